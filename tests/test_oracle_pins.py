@@ -1,0 +1,279 @@
+"""Pins for the FP64 oracle: each check is fixed by the paper or by mathematics,
+not by the oracle itself (closed forms, library routines, invariants, the
+paper's logged decompositions)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+from scipy.sparse import coo_matrix
+from scipy.sparse.csgraph import shortest_path
+
+import workloads as W
+from oracle import brute, stad_literal as L
+from oracle.kernels import quantise, grid_table
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_decompositions.json")
+
+
+def _rand_tree(n, seed, lo=1, hi=4):
+    rng = np.random.default_rng(seed)
+    t = W.random_recursive(n, rng)
+    return t.with_weights(W.trees.integer_weights(t.m, lo, hi, rng))
+
+
+def test_f_constant_gives_column_sums():
+    # f == 1: every output is the sum of the field (Eq. integration with f = 1)
+    t = _rand_tree(300, 1)
+    x = np.random.default_rng(2).standard_normal((300, 4))
+    y = brute.integrate(t, 1.0, W.KernelSpec.exp(0.0), x)
+    np.testing.assert_allclose(y, np.broadcast_to(x.sum(0), y.shape), rtol=1e-12, atol=1e-10)
+
+
+def test_unit_path_is_toeplitz():
+    # Path with the whole path as backbone: G_0[s] = sum_t f(|s-t|) x_t (Appendix "Complexity Analysis for Paths")
+    n = 257
+    spec = W.KernelSpec.rational(1.0)  # 1/(1+x)
+    x = np.random.default_rng(3).standard_normal(n)
+    y = brute.integrate(W.path(n), 1.0, spec, x)
+    c = 1.0 / (1.0 + np.arange(n))
+    np.testing.assert_allclose(y, scipy.linalg.toeplitz(c) @ x, rtol=1e-12)
+
+
+def test_star_closed_form():
+    n = 50
+    spec = W.KernelSpec.gauss(0.3)
+    f = lambda k: math.exp(-0.3 * k * k)
+    x = np.random.default_rng(4).standard_normal(n)
+    y = brute.integrate(W.star(n), 1.0, spec, x)
+    leaves = x[1:].sum()
+    assert abs(y[0] - (f(0) * x[0] + f(1) * leaves)) < 1e-12
+    exp_leaf = f(0) * x[1:] + f(1) * x[0] + f(2) * (leaves - x[1:])
+    np.testing.assert_allclose(y[1:], exp_leaf, rtol=1e-12, atol=1e-12)
+
+
+def test_uniform_path_exponential_closed_form():
+    # sum_j lambda^{|i-j|} = (1 + lambda - lambda^{i+1} - lambda^{N-i}) / (1 - lambda)
+    n, lam = 400, 0.97
+    t = W.path(n).with_weights(np.full(n - 1, 2.0))  # q = 2 at delta = 1
+    spec = W.KernelSpec.exp(-math.log(lam) / 2.0)     # f(2k) = lam^k
+    y = brute.integrate(t, 1.0, spec, np.ones(n))
+    i = np.arange(n)
+    closed = (1 + lam - lam ** (i + 1) - lam ** (n - i)) / (1 - lam)
+    np.testing.assert_allclose(y, closed, rtol=1e-11)
+
+
+def test_weighted_path_exponential_two_sweeps():
+    # f(x) = lambda^x on a weighted path: left and right exponential recurrences
+    rng = np.random.default_rng(5)
+    n = 300
+    q = rng.integers(1, 9, size=n - 1)
+    t = W.path(n).with_weights(q.astype(float) / 4.0)
+    spec = W.KernelSpec.exp(0.7)
+    x = rng.standard_normal(n)
+    y = brute.integrate(t, 0.25, spec, x)
+    g = np.exp(-0.7 * 0.25 * q)
+    left = np.zeros(n)
+    right = np.zeros(n)
+    left[0] = x[0]
+    for i in range(1, n):
+        left[i] = x[i] + g[i - 1] * left[i - 1]
+    right[-1] = x[-1]
+    for i in range(n - 2, -1, -1):
+        right[i] = x[i] + g[i] * right[i + 1]
+    np.testing.assert_allclose(y, left + right - x, rtol=1e-11)
+
+
+def test_matches_scipy_all_pairs_shortest_paths():
+    for seed, delta in [(6, 1.0), (7, 1 / 64)]:
+        rng = np.random.default_rng(seed)
+        t = W.random_recursive(400, rng)
+        t = t.with_weights(W.trees.snapped_uniform_weights(t.m, 0.5, 2.0, 1 / 64, rng))
+        q = quantise(t.w, delta).astype(float)
+        D = shortest_path(coo_matrix((q, (t.u, t.v)), shape=(t.n, t.n)), directed=False)
+        spec = W.KernelSpec.rational(0.05, e=2.0)
+        M = grid_table(spec, delta, int(D.max()))[D.astype(np.int64)]
+        x = rng.standard_normal((t.n, 3))
+        np.testing.assert_allclose(brute.integrate(t, delta, spec, x), M @ x, rtol=1e-12, atol=1e-12)
+
+
+def test_forest_has_no_cross_tree_terms():
+    a, b = _rand_tree(40, 8), _rand_tree(25, 9)
+    f, offs = W.forest([a, b])
+    spec = W.KernelSpec.exp(0.2)
+    x = np.random.default_rng(10).standard_normal((f.n, 2))
+    y = brute.integrate(f, 1.0, spec, x)
+    np.testing.assert_allclose(y[:40], brute.integrate(a, 1.0, spec, x[:40]), rtol=1e-13)
+    np.testing.assert_allclose(y[40:], brute.integrate(b, 1.0, spec, x[40:]), rtol=1e-13)
+
+
+def test_operator_symmetry_and_linearity():
+    t = _rand_tree(200, 11)
+    spec = W.KernelSpec.rational(0.1, e=1.0, p=2.0)
+    rng = np.random.default_rng(12)
+    x, z = rng.standard_normal((2, 200, 3))
+    Kx, Kz = brute.integrate(t, 1.0, spec, x), brute.integrate(t, 1.0, spec, z)
+    assert abs(np.sum(z * Kx) - np.sum(Kz * x)) < 1e-10 * np.abs(Kx).sum()
+    np.testing.assert_allclose(brute.integrate(t, 1.0, spec, 2 * x - 3 * z), 2 * Kx - 3 * Kz, rtol=1e-11, atol=1e-11)
+
+
+def test_quantisation_error_bound():
+    # |d_Q - d_T| <= l_ij * delta and exp(-l/B) <= K_Q/K_T <= exp(l/B) (Appendix, quantization error)
+    rng = np.random.default_rng(13)
+    t = W.random_recursive(120, rng).with_weights(rng.uniform(0.001, 0.2, size=119))
+    eps, B = 0.05, 64
+    delta = eps / B
+    q = quantise(t.w, delta).astype(float)
+    DQ = delta * shortest_path(coo_matrix((q, (t.u, t.v)), shape=(120, 120)), directed=False)
+    DT = shortest_path(coo_matrix((t.w, (t.u, t.v)), shape=(120, 120)), directed=False)
+    hops = shortest_path(coo_matrix((np.ones(119), (t.u, t.v)), shape=(120, 120)), directed=False)
+    assert np.all(np.abs(DQ - DT) <= hops * delta * (1 + 1e-12))
+    ratio = np.exp(-DQ / eps) / np.exp(-DT / eps)
+    assert np.all(ratio <= np.exp(hops / B) * (1 + 1e-12)) and np.all(ratio >= np.exp(-hops / B) * (1 - 1e-12))
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_literal_stad_equals_brute_on_all_labelled_trees(n):
+    rng = np.random.default_rng(100 + n)
+    spec = W.KernelSpec.rational(0.3, e=2.0, p=1.0)
+    for t in W.prufer_trees(n):
+        t = t.with_weights(W.trees.integer_weights(t.m, 1, 5, rng))
+        x = rng.standard_normal((n, 2))
+        y = brute.integrate(t, 1.0, spec, x)
+        for policy in ("adaptive", "diameter", "centroid"):
+            w, _ = L.solve(t, 1.0, spec, x, policy=policy)
+            assert np.abs(w - y).max() <= 1e-12 * max(1.0, np.abs(y).max())
+
+
+def test_literal_stad_equals_brute_on_labelled_trees_n7():
+    rng = np.random.default_rng(107)
+    spec = W.KernelSpec.exp(0.4)
+    for t in W.prufer_trees(7):  # all 16,807 labelled trees
+        t = t.with_weights(W.trees.integer_weights(t.m, 1, 5, rng))
+        x = rng.standard_normal(7)
+        w, _ = L.solve(t, 1.0, spec, x, policy="adaptive")
+        assert np.abs(w - brute.integrate(t, 1.0, spec, x)).max() <= 1e-12
+
+
+def test_g_evaluators_agree_with_quadruple_loop():
+    # Eq. sumofFFTterms: direct loop (proof of the 1D-FFT proposition) vs Algorithm 2 vs Algorithm 3
+    rng = np.random.default_rng(14)
+    for H1, Wd in [(1, 1), (1, 7), (4, 1), (3, 5), (6, 9)]:
+        A = rng.standard_normal((H1, Wd, 2))
+        fv = 1.0 / (1.0 + np.arange(3 * (H1 + Wd) + 4) ** 2 / 9.0)
+        Gd = L.compute_g_direct(A, fv)
+        np.testing.assert_allclose(L.compute_g_1d(A, fv), Gd, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(L.compute_g_2dfft(A, fv), Gd, rtol=1e-12, atol=1e-12)
+
+
+def test_caterpillar_closed_form():
+    # w_u = G_1[a(alpha)] + (f(0) - f(2)) x_u for leaves (Proposition "Caterpillars")
+    t = W.caterpillar_leaves(20, leaves=3)
+    spec = W.KernelSpec.rational(1.0)
+    fv = lambda k: 1.0 / (1.0 + k)
+    x = np.random.default_rng(15).standard_normal((t.n, 1))
+    y = brute.integrate(t, 1.0, spec, x)
+    w, res = L.solve(t, 1.0, spec, x, policy="diameter")
+    root = [c for c in res.calls if c["level"] == 0][0]
+    assert root["H"] == 1
+    G = root["inter"]["G"]
+    for u, (r, col, comp) in root["rec"].items():
+        if r == 1:
+            assert abs(y[u, 0] - (G[1, col, 0] + (fv(0) - fv(2)) * x[u, 0])) < 1e-12
+    np.testing.assert_allclose(w, y, rtol=1e-12, atol=1e-12)
+
+
+def test_exponential_sweeps_algorithm7():
+    # Algorithm 7 (two sweeps) equals brute force for an exponential sum, weighted tree
+    rng = np.random.default_rng(16)
+    t = W.random_recursive(150, rng)
+    t = t.with_weights(W.trees.integer_weights(t.m, 1, 6, rng))
+    spec = W.KernelSpec.expsum([0.7, -0.2], [0.3, 0.05])
+    terms = [(0.7, math.exp(-0.3)), (-0.2, math.exp(-0.05))]
+    x = rng.standard_normal((150, 2))
+    for policy in ("adaptive", "diameter"):
+        w, _ = L.solve(t, 1.0, spec, x, policy=policy, exp_terms=terms)
+        np.testing.assert_allclose(w, brute.integrate(t, 1.0, spec, x), rtol=1e-11, atol=1e-12)
+
+
+def test_kernel_parameter_gradient_by_finite_differences():
+    t = W.grid_spanning_tree(5, 5, np.random.default_rng(17))
+    rng = np.random.default_rng(18)
+    a, b = rng.normal(0, 0.1, 3), rng.uniform(0.1, 2.0, 3)
+    x, g = rng.standard_normal((2, t.n, 4))
+    grad = brute.kernel_param_grad(t, 1.0, W.KernelSpec.expsum(a, b), g, x)
+    theta = W.KernelSpec.expsum(a, b).params
+    for k in range(len(theta)):
+        h = 1e-6
+        tp, tm = list(theta), list(theta)
+        tp[k] += h
+        tm[k] -= h
+        lp = np.sum(g * brute.integrate(t, 1.0, W.KernelSpec("expsum", tp), x))
+        lm = np.sum(g * brute.integrate(t, 1.0, W.KernelSpec("expsum", tm), x))
+        assert abs((lp - lm) / (2 * h) - grad[k]) < 1e-6 * max(1.0, abs(grad[k]))
+
+
+# --- the paper's logged decompositions --------------------------------------
+
+def _golden():
+    with open(GOLDEN) as fh:
+        return json.load(fh)
+
+
+def test_spider_4001_root_choice():
+    gd = _golden()["long_arm_spider_4001"]
+    t = W.spider(gd["arms"], gd["arm_len"])
+    g = L.Graph(t, 1.0)
+    S = set(range(t.n))
+    Pd = L.diameter_path(g, S)
+    dd = L.decompose_off_path_components(g, S, Pd)
+    assert (len(Pd), dd["H"], (dd["H"] + 1) * len(Pd)) == (gd["diameter_root"]["m"], gd["diameter_root"]["H"],
+                                                           gd["diameter_root"]["table"])
+    P, dec, kind = L.choose_backbone(g, S, "adaptive")
+    assert kind == "centroid" and P == [0]
+    assert (len(P), dec["H"], dec["H"] + 1) == (1, gd["adaptive_root"]["H"], gd["adaptive_root"]["table"])
+    assert sorted(len(c["verts"]) for c in dec["comps"]) == gd["adaptive_root"]["children"]
+    # each remaining arm is processed with its whole path as backbone (Corollary on equal-arm spiders)
+    for c in dec["comps"]:
+        P2, d2, _ = L.choose_backbone(g, set(c["verts"]), "adaptive")
+        assert len(P2) == len(c["verts"]) and d2["H"] == 0
+
+
+def test_caterpillar_hanging_paths_1056_root_choice():
+    gd = _golden()["caterpillar_hanging_1056"]
+    t = W.caterpillar_hanging_paths(gd["ell"])
+    assert t.n == 1056
+    g = L.Graph(t, 1.0)
+    S = set(range(t.n))
+    Pd = L.diameter_path(g, S)
+    dd = L.decompose_off_path_components(g, S, Pd)
+    assert (len(Pd), dd["H"]) == (gd["diameter_root"]["m"], gd["diameter_root"]["H"])
+    sizes = [len(c["verts"]) for c in dd["comps"]]
+    assert sizes.count(32) == gd["diameter_root"]["children"]["32"] and len(sizes) == 30
+    P, dec, kind = L.choose_backbone(g, S, "adaptive")
+    assert kind == "centroid"
+    assert (len(P), dec["H"]) == (gd["adaptive_root"]["m"], gd["adaptive_root"]["H"])
+    assert sorted(len(c["verts"]) for c in dec["comps"]) == gd["adaptive_root"]["children"]
+
+
+def test_path_800_keeps_full_diameter():
+    gd = _golden()["path_800"]
+    t = W.path(gd["n"])
+    g = L.Graph(t, 1.0)
+    P, dec, kind = L.choose_backbone(g, set(range(t.n)), "adaptive")
+    assert kind == "diameter" and len(P) == gd["adaptive_root"]["m"] and dec["H"] == 0 and not dec["comps"]
+
+
+def test_figure1_projection_and_depth():
+    gd = _golden()["figure1"]
+    # backbone p1..p6 = 0..5; B1 = p2-6-7; B2 = p2-8, 8-9, 8-10; B3 = p3-11, 11-12, 11-u(13); B4 = p4-14-15
+    edges = [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (1, 6), (6, 7), (1, 8), (8, 9), (8, 10),
+             (2, 11), (11, 12), (11, 13), (3, 14), (14, 15)]
+    t = W.trees._from_edges(16, edges)
+    g = L.Graph(t, 1.0)
+    dec = L.decompose_off_path_components(g, set(range(16)), [0, 1, 2, 3, 4, 5])
+    assert dec["pi"][13] == gd["u_pi_backbone_index"] and dec["d"][13] == gd["u_depth"]
+    anchors = [c["anchor"] for c in dec["comps"]]
+    assert anchors.count(gd["shared_anchor_backbone_index"]) == 2 and len(anchors) == 4
