@@ -1,0 +1,371 @@
+"""Benchmark: StAd-TFI forward + backward (adjoint) throughput on one B300.
+
+Default workload: a random recursive tree with N = 2^20 vertices, edge lengths
+U[0.5, 2] snapped to a 1/64 grid, grid step 1/64, f(x) = exp(-0.1 x), an
+N x 16 FP32 N(0,1) field. One step = one forward apply and one backward apply
+(the adjoint, on a second field), i.e. N*d vertex-channel integrations in each
+direction. Metric: N*d / step time (vertex.channel integrations per second,
+fwd+bwd). Inputs are resident in HBM; L2 is flushed (512 MB write) between
+timed steps. Prints one JSON line on rank 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle (plain definition, one
+traversal per target) on the host cores on a bounded sample of target
+vertices per step of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "vertex.channel integrations/s (N*d/s), fwd+bwd, N=2^20"
+UNIT = "vertex.channel/s"
+
+
+def workload_args(a):
+    return dict(shape=a.shape, n=a.n, d=a.d, kernel=a.kernel)
+
+
+def workload_name(a):
+    return f"sweep_{a.shape}_n{a.n}_d{a.d}_{a.kernel}_delta1/64"
+
+
+def config_block(a, extra=None):
+    c = {"workload": workload_name(a), "shape": a.shape, "n": a.n, "d": a.d,
+         "kernel": {"exp": "exp(-0.1x)", "cauchy": "1/(1+x^2)", "gauss": "exp(-x^2/8)"}[a.kernel],
+         "delta": 1.0 / 64, "weights": "U[0.5,2] snapped to 1/64", "policy": a.policy, "leaf_max": a.leaf_max,
+         "l2": "flushed between timed steps (512 MB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return pk, "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def ncu_traffic(kernel_stage: str):
+    """DRAM bytes per apply for a stage from a committed ncu summary, if it was
+    taken on the current kernel sources; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except OSError:
+        return None
+    import hashlib
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2609_34025_b300", "csrc", "kernels.cuh"), "rb").read())
+    ent = rec.get(kernel_stage)
+    if not ent or ent.get("kernels_sha256") != h.hexdigest()[:16]:
+        return None
+    return ent.get("bytes_per_apply")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(cfg, F, G, targets, threads=0):
+    from oracle import brute
+
+    adj = getattr(oracle_sample, "_adj", None)
+    if adj is None:
+        adj = brute.Adjacency(cfg["tree"], cfg["delta"])
+        adj.max_dist()
+        oracle_sample._adj = adj
+    t0 = time.perf_counter()
+    brute.integrate(cfg["tree"], cfg["delta"], cfg["kernel"], F, targets=targets, threads=threads, adj=adj)
+    brute.integrate(cfg["tree"], cfg["delta"], cfg["kernel"], G, targets=targets, threads=threads, adj=adj)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(cfg, F, G, budget_s=15.0):
+    rng = np.random.default_rng(1)
+    n, d = F.shape
+    cores = os.cpu_count() or 1
+    s = 16
+    t = oracle_sample(cfg, F, G, rng.choice(n, s, replace=False).astype(np.int32))
+    reps, total_t, total_s = 0, 0.0, 0
+    s = int(np.clip(s * (budget_s / 3) / max(t, 1e-3), 16, 4096))
+    while total_t < budget_s and reps < 3:
+        tgt = rng.choice(n, s, replace=False).astype(np.int32)
+        total_t += oracle_sample(cfg, F, G, tgt)
+        total_s += s
+        reps += 1
+    return {"value": total_s * d / total_t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{total_s} target vertices (fwd+bwd, all {d} channels) of the full N={n} workload, "
+                      f"FP64 brute force, {total_t:.1f} s"}
+
+
+def run_reference(a):
+    import workloads as W
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = W.configs.sweep(**workload_args(a))
+    n, d = cfg["tree"].n, cfg["d"]
+    F = W.normal_field(n, d, seed=123).astype(np.float64)
+    G = W.normal_field(n, d, seed=124).astype(np.float64)
+    rng = np.random.default_rng(2)
+    cores = os.cpu_count() or 1
+    # size the per-step sample so the whole run stays within a few minutes
+    t = oracle_sample(cfg, F, G, rng.choice(n, 16, replace=False).astype(np.int32))
+    budget_per_step = 120.0 / max(1, a.steps + a.warmup)
+    s = int(np.clip(16 * budget_per_step / max(t, 1e-3), 4, 4096))
+    for _ in range(a.warmup):
+        oracle_sample(cfg, F, G, rng.choice(n, s, replace=False).astype(np.int32))
+    times = []
+    for _ in range(a.steps):
+        times.append(oracle_sample(cfg, F, G, rng.choice(n, s, replace=False).astype(np.int32)))
+    tot = sum(times)
+    value = a.steps * s * d / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_block(a, {"sample_targets_per_step": s}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{s} target vertices per step (fwd+bwd, {d} channels) of the N={n} tree"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(a):
+    import torch
+
+    import paper_2609_34025_b300 as tfi
+    from paper_2609_34025_b300 import build as tbuild
+    import workloads as W
+
+    tbuild.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfg = W.configs.sweep(**workload_args(a))
+    n, d = cfg["tree"].n, cfg["d"]
+    t0 = time.perf_counter()
+    plan = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=a.policy, leaf_max=a.leaf_max,
+                              max_channels=d)
+    plan_s = time.perf_counter() - t0
+    # weak scaling over ranks: each rank integrates its own block of d channels on the same tree
+    F = torch.from_numpy(W.normal_field(n, d, seed=123 + 2 * rank)).cuda()
+    G = torch.from_numpy(W.normal_field(n, d, seed=124 + 2 * rank)).cuda()
+    out = torch.empty_like(F)
+    gF = torch.empty_like(F)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.apply(F, out)
+        plan.apply_backward(G, gF)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    plan.profile(True)
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for i in range(a.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    prof = plan.profile_read()
+    plan.profile(False)
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    value = world * n * d * a.steps / (total_ms / 1e3)
+    # forward only
+    evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    for i in range(a.steps):
+        flush.zero_()
+        evf[i][0].record(stream)
+        plan.apply(F, out)
+        evf[i][1].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = sum(s.elapsed_time(e) for s, e in evf) / a.steps
+    # end to end through the C ABI with pinned host buffers (copies in the timed region)
+    Fh = torch.from_numpy(W.normal_field(n, d, seed=123 + 2 * rank)).pin_memory()
+    Gh = torch.from_numpy(W.normal_field(n, d, seed=124 + 2 * rank)).pin_memory()
+    Oh = torch.empty_like(Fh).pin_memory()
+    Qh = torch.empty_like(Fh).pin_memory()
+    for _ in range(2):
+        plan.apply_host_ptr(Fh.data_ptr(), Oh.data_ptr(), d)
+    e2e_t0 = time.perf_counter()
+    for _ in range(a.steps):
+        plan.apply_host_ptr(Fh.data_ptr(), Oh.data_ptr(), d)
+        plan.apply_host_ptr(Gh.data_ptr(), Qh.data_ptr(), d)
+    e2e_s = time.perf_counter() - e2e_t0
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    # roofline of the dominant stage
+    model = plan.stage_model(d)
+    applies = 2 * a.steps
+    per_apply_ms = {k: v[0] / applies for k, v in prof.items()}
+    launches = {k: v[1] / applies for k, v in prof.items()}
+    dom = max(per_apply_ms, key=per_apply_ms.get)
+    pk, src = measured_peaks()
+    clk = clk.summary()
+    bytes_dom, flops_dom = model[dom]
+    t_dom = per_apply_ms[dom] / 1e3
+    gbs = bytes_dom / t_dom / 1e9
+    sm_mhz = pk.get("sm_max_mhz", 2032.0)
+    fp32_peak_tflops = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    tflops = flops_dom / t_dom / 1e12
+    frac_hbm = gbs / pk["hbm_gbs"]
+    frac_alu = tflops / fp32_peak_tflops
+    traffic = ncu_traffic(dom)
+    if frac_hbm >= frac_alu:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": frac_hbm,
+                "traffic": traffic, "kernel_stage": dom, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roof = {"bound": "alu", "achieved": tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": frac_alu,
+                "traffic": traffic, "kernel_stage": dom,
+                "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x sm_max_mhz"}
+    roof["stage_ms_per_apply"] = {k: round(v, 4) for k, v in per_apply_ms.items()}
+    roof["stage_model_per_apply"] = {k: {"bytes": b, "flops": f} for k, (b, f) in model.items()}
+    F_np = F.cpu().numpy().astype(np.float64)
+    G_np = G.cpu().numpy().astype(np.float64)
+    cpu = cpu_baseline(cfg, F_np, G_np, budget_s=a.cpu_budget) if a.cpu_budget > 0 else None
+    info = plan.info()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": config_block(a, {"parallelism": f"channel blocks, {world} rank(s), no collective on the data path",
+                                   "plan_seconds": round(plan_s, 3), "plan_calls": info["n_calls"],
+                                   "plan_leaves": info["n_leaves"], "plan_levels": info["n_levels"]}),
+        "fwd_value": world * n * d / (fwd_ms / 1e3), "fwd_ms": fwd_ms,
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": world * n * d * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * n * d * 4,
+                "d2h_bytes_per_step": 2 * n * d * 4},
+        "gpu_launches": int(round(sum(launches.values()) * 2 * a.steps)),
+        "gpu_launches_per_step": sum(launches.values()) * 2,
+        "clocks": clk, "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--shape", default="rrt", choices=["rrt", "binary", "caterpillar"])
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--d", type=int, default=16)
+    ap.add_argument("--kernel", default="exp", choices=["exp", "cauchy", "gauss"])
+    ap.add_argument("--policy", default="adaptive")
+    ap.add_argument("--leaf-max", dest="leaf_max", type=int, default=64)
+    ap.add_argument("--cpu-budget", dest="cpu_budget", type=float, default=15.0)
+    a = ap.parse_args()
+    if a.warmup < 3:
+        a.warmup = 3
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * tfi.h — C ABI of libtfi: Structure-Adaptive Tree Field Integration (StAd-TFI)
+ * on one B300 GPU (sm_103a).
+ *
+ * The operation (paper Eq. "integration", specialised to trees in Eq.
+ * "stad-target"; weighted trees on the quantised metric of Appendix
+ * "Distance quantization for FFT-Based Integrators"):
+ *
+ *     out[u, c] = sum_v f(delta * dhat(u, v)) * F[v, c]      for every vertex u
+ *
+ * where q_e = max(1, round(w_e / delta)) is the integer length of edge e
+ * (round half to even) and dhat(u, v) is the sum of q_e on the tree path.
+ * Vertices in different trees of a forest do not interact.
+ *
+ * The plan holds the paper's recursive decomposition (Section 2.1, Algorithm
+ * 1 "DecomposeOffPathComponents", Algorithm 6 "ChooseBackbone", Eq.
+ * "stad-score") flattened into arrays, the grid samples of f and the cached
+ * kernel spectra. An apply evaluates every call's cross term (Eq.
+ * "stad-split", Eq. "sumofFFTterms", Eq. "stad-E", Lemma "Cross-component
+ * correction") with GPU kernels and adds the leaf terms.
+ *
+ * Conventions
+ *   - No function throws; every function returns a tfi_status. A message for
+ *     the last error of the calling thread is available from tfi_last_error().
+ *   - Device pointers are CUDA device addresses on the current device; the
+ *     caller owns them. Host pointers are read during the call only.
+ *   - Applies are stream-ordered and asynchronous with respect to the host. A
+ *     plan may be used by one stream at a time (it owns one workspace).
+ *   - Fields are row-major N x d arrays (row stride d elements), dtype
+ *     TFI_DTYPE_F32 (float) or TFI_DTYPE_BF16 (bfloat16); accumulation is
+ *     FP32. Results are deterministic: no floating-point atomics.
+ */
+#ifndef TFI_H
+#define TFI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tfi_status;
+#define TFI_OK                 0
+#define TFI_ERR_ARG            1  /* null pointer, bad size, bad enum, d > max_channels, ... */
+#define TFI_ERR_NOT_TREE       2  /* edge list has a cycle, a self loop or an out-of-range vertex */
+#define TFI_ERR_WEIGHT         3  /* an edge weight is not finite or not > 0 */
+#define TFI_ERR_GRID_OVERFLOW  4  /* a grid distance exceeds 2^30, or a sampled table is too short */
+#define TFI_ERR_OOM            5  /* host or device allocation failed */
+#define TFI_ERR_CUDA           6  /* a CUDA runtime call failed (message in tfi_last_error) */
+#define TFI_ERR_TIMEOUT        7  /* a bounded device wait gave up */
+#define TFI_ERR_UNSUPPORTED    8  /* the plan needs an evaluator this build does not have */
+#define TFI_ERR_NO_DEVICE      9  /* no CUDA device, or the plan was built host-only */
+
+typedef struct tfi_plan_s *tfi_plan_t;
+typedef void *tfi_stream_t;       /* a cudaStream_t; NULL = the legacy default stream */
+
+/* A forest on vertices 0..n-1: n_edges undirected edges (u[i], v[i]) of
+ * length w[i] > 0. A tree has n_edges = n - 1. Host memory, read only. */
+typedef struct {
+    int32_t n;
+    int32_t n_edges;
+    const int32_t *u;
+    const int32_t *v;
+    const double *w;
+} tfi_tree;
+
+/* Kernel f(x) of a distance x in original units. The plan samples it on the
+ * grid, f(k * delta), in FP64 and rounds the samples once to FP32.
+ *   TFI_F_EXPSUM   f(x) = sum_k a_k exp(-b_k x)   params = [a_1, b_1, a_2, b_2, ...]
+ *   TFI_F_GAUSS    f(x) = a exp(-c x^2)           params = [a, c]
+ *   TFI_F_RATIONAL f(x) = a / (1 + c x^e)^p       params = [a, c, e, p]
+ *   TFI_F_TABLE    f(k delta) = table[k] for k < table_len; a plan that needs a
+ *                  longer table fails with TFI_ERR_GRID_OVERFLOW. */
+#define TFI_F_TABLE    0
+#define TFI_F_EXPSUM   1
+#define TFI_F_GAUSS    2
+#define TFI_F_RATIONAL 3
+typedef struct {
+    int32_t kind;
+    int32_t n_params;
+    const double *params;   /* host */
+    int64_t table_len;
+    const double *table;    /* host; TFI_F_TABLE only */
+} tfi_kernel;
+
+/* Backbone policy per recursive call (Section 2.4, Algorithm 6):
+ *   ADAPTIVE  diameter path vs single centroid by Eq. "stad-score" (grid units)
+ *   DIAMETER  always the (weighted) diameter path
+ *   CENTROID  always a single centroid vertex */
+#define TFI_POLICY_ADAPTIVE 0
+#define TFI_POLICY_DIAMETER 1
+#define TFI_POLICY_CENTROID 2
+
+#define TFI_PLAN_HOST_ONLY  1   /* build the decomposition on the host only (no GPU use) */
+
+typedef struct {
+    double delta;           /* grid step > 0 */
+    int32_t policy;         /* TFI_POLICY_* */
+    int32_t leaf_max;       /* s0 >= 1: a call with <= s0 vertices is summed densely (s0 = 1: base case f(0) x_u) */
+    int32_t max_channels;   /* largest d any apply will use (sizes the workspace) */
+    int32_t flags;          /* TFI_PLAN_* */
+} tfi_options;
+
+#define TFI_DTYPE_F32  0
+#define TFI_DTYPE_BF16 1
+
+/* Build a plan: validate and quantise the forest, run the decomposition on the
+ * host (Algorithms 1 and 6 per call, iteratively), flatten it, sample f,
+ * compute the kernel spectra in FP64, and (unless TFI_PLAN_HOST_ONLY) upload
+ * everything and allocate the workspace on the current device. On success
+ * *out owns host and device memory until tfi_destroy. */
+tfi_status tfi_plan(const tfi_tree *tree, const tfi_kernel *kernel, const tfi_options *opt, tfi_plan_t *out);
+
+/* out = K F (the operator above). F, out: device, n x d, dtype; out is
+ * overwritten and must not alias F. 1 <= d <= max_channels. */
+tfi_status tfi_apply(tfi_plan_t plan, const void *F, void *out, int32_t d, int32_t dtype, tfi_stream_t stream);
+
+/* grad_F = K^T grad_out. K is symmetric (f(dhat(u,v)) = f(dhat(v,u)); the
+ * paper uses the same operator for K and K^T in its Sinkhorn updates), so this
+ * is one more apply on grad_out. Same layout rules as tfi_apply. */
+tfi_status tfi_apply_backward(tfi_plan_t plan, const void *grad_out, void *grad_F, int32_t d, int32_t dtype,
+                              tfi_stream_t stream);
+
+/* As tfi_apply, with F and out in HOST memory (pinned memory gives
+ * asynchronous copies). Copies F in, applies, copies out, and synchronises the
+ * stream before returning. Uses plan-owned device staging buffers. */
+tfi_status tfi_apply_host(tfi_plan_t plan, const void *F_host, void *out_host, int32_t d, int32_t dtype,
+                          tfi_stream_t stream);
+
+/* Release everything the plan owns. NULL is accepted and ignored. */
+tfi_status tfi_destroy(tfi_plan_t plan);
+
+/* Plan statistics. */
+typedef struct {
+    int64_t n;              /* vertices */
+    int64_t n_calls;        /* non-leaf recursive calls */
+    int64_t n_leaves;       /* leaf calls (|V(S)| <= s0) */
+    int64_t n_levels;       /* recursion depth + 1 */
+    int64_t n_records;      /* sum over non-leaf calls of |V(S)| */
+    int64_t n_keys;         /* distinct (call, depth, coordinate) and (component, depth) bins */
+    int64_t n_jobs_fft;     /* cross / correction tables evaluated by FFT */
+    int64_t n_jobs_direct;  /* tables evaluated by direct summation */
+    int64_t n_centroid;     /* calls whose backbone is a single centroid */
+    int64_t sum_table;      /* sum over non-leaf calls of (H+1)(L+1), grid units */
+    int64_t sum_fft_points; /* sum over FFT jobs of P1*P2 */
+    int64_t sum_leaf_pairs; /* sum over leaves of |V(S)|^2 */
+    int64_t ftab_len;       /* grid samples of f held on the device */
+    int64_t device_bytes;   /* device memory owned by the plan (without per-d work lists) */
+    double plan_seconds;    /* host wall time of tfi_plan */
+} tfi_plan_info;
+tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
+
+/* Export the decomposition for inspection and tests (host copies, int64).
+ *   TFI_EXPORT_CALLS    7 per non-leaf call: level, min vertex, |V(S)|, kind (0 diameter, 1 centroid),
+ *                       m = |V(P)|, H (grid), L = X_m (grid)
+ *   TFI_EXPORT_BACKBONE backbone vertices p_1..p_m of every call, concatenated in call order
+ *   TFI_EXPORT_RECORDS  5 per (call, vertex): call index, vertex, depth d(u) (grid),
+ *                       coordinate X(pi(u)) (grid), component id = min vertex of the component (-1 on P)
+ *   TFI_EXPORT_LEAVES   3 per leaf call: level, min vertex, |V(S)|
+ * If dst is NULL (or cap too small) only *len (number of int64 values) is set. */
+#define TFI_EXPORT_CALLS    0
+#define TFI_EXPORT_BACKBONE 1
+#define TFI_EXPORT_RECORDS  2
+#define TFI_EXPORT_LEAVES   3
+tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t cap, int64_t *len);
+
+/* Stages of an apply, in launch order, for profiling and the roofline model:
+ *   LEAF    dense leaf calls f(D_S) x_S
+ *   BUCKET  segmented bin sums of field rows (A_r[t] and b_alpha[r])
+ *   FFT     cross tables / corrections by shared-memory FFT correlation
+ *   DIRECT  cross tables / corrections by direct summation over occupied bins
+ *   GATHER  per-vertex sum over calls of G - E, plus the leaf term, one write per row */
+#define TFI_STAGE_LEAF   0
+#define TFI_STAGE_BUCKET 1
+#define TFI_STAGE_FFT    2
+#define TFI_STAGE_DIRECT 3
+#define TFI_STAGE_GATHER 4
+#define TFI_N_STAGES     5
+
+/* Per-stage timing with CUDA events recorded on the apply's stream. enable != 0
+ * starts recording (and clears previous totals); 0 stops. Adds two event
+ * records per stage per apply. */
+tfi_status tfi_profile_enable(tfi_plan_t plan, int32_t enable);
+
+/* Synchronise the recorded events and return, per stage, the summed device time
+ * in milliseconds and the number of kernel launches since profiling was
+ * enabled. ms and launches each hold TFI_N_STAGES values. */
+tfi_status tfi_profile_read(tfi_plan_t plan, double *ms, int64_t *launches);
+
+/* Algorithmic DRAM bytes and floating-point operations of one apply, per stage,
+ * for d channels of the given dtype, from the plan's exact counts (bins, records,
+ * leaf pairs, FFT sizes). bytes and flops each hold TFI_N_STAGES values. */
+tfi_status tfi_stage_model(tfi_plan_t plan, int32_t d, int32_t dtype, double *bytes, double *flops);
+
+/* Message describing the last error returned on the calling thread ("" if none). */
+const char *tfi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TFI_H */

@@ -316,9 +316,10 @@ class Result:
 
 
 def solve(tree, delta: float, spec, x, policy: str = "adaptive", leaf_max: int = 1,
-          evaluator: str = "fft2d", exp_terms=None):
+          evaluator: str = "fft2d", exp_terms=None, evaluate: bool = True):
     """Returns (w, Result). x: (n,) or (n, d). With exp_terms = [(c, lambda)]
-    per grid unit, the cross terms use Algorithm 7 instead of FFTs."""
+    per grid unit, the cross terms use Algorithm 7 instead of FFTs. With
+    evaluate=False only the decomposition is recorded (w stays zero)."""
     g = Graph(tree, delta)
     x = np.asarray(x, dtype=np.float64)
     squeeze = x.ndim == 1
@@ -327,7 +328,7 @@ def solve(tree, delta: float, spec, x, policy: str = "adaptive", leaf_max: int =
     n, d = x.shape
     # f on the grid, long enough for every lookup the algorithms make
     from .brute import Adjacency
-    kmax = 3 * Adjacency(tree, delta).max_dist() + 4
+    kmax = 3 * Adjacency(tree, delta).max_dist() + 4 if evaluate else 0
     fv = grid_table(spec, delta, kmax) if spec.kind != "table" else _padded_table(spec, kmax)
     w = np.zeros((n, d))
     res = Result()
@@ -344,13 +345,15 @@ def solve(tree, delta: float, spec, x, policy: str = "adaptive", leaf_max: int =
         level, S = stack.pop()
         if len(S) <= leaf_max:
             verts = sorted(S)
-            for u in verts:
+            for u in (verts if evaluate else []):
                 du, _ = g.distances(u, S)
                 w[u] += sum(fv[du[v]] * x[v] for v in verts)
             res.leaves.append(dict(level=level, minv=verts[0], size=len(S), verts=verts))
             continue
         P, dec, kind = choose_backbone(g, S, policy)
-        if exp_terms is not None:
+        if not evaluate:
+            cross, inter = {u: 0.0 for u in S}, None
+        elif exp_terms is not None:
             cross = cross_subroutine_exp(dec, x, exp_terms)
             inter = None
         else:

@@ -1,0 +1,252 @@
+"""StAd-TFI (structure-adaptive tree field integration) on one B300.
+
+A thin Python binding over ``libtfi.so`` (C ABI in ``include/tfi.h``): it
+marshals arguments only. Every step of the apply runs in the library's CUDA
+kernels; there is no CPU fallback, and importing the binding fails loudly when
+the library has not been built.
+
+    plan = Plan(n, u, v, w, delta=1/64, kernel=("expsum", [1.0, 0.1]), leaf_max=64, max_channels=16)
+    out = plan.apply(F)                 # F: CUDA tensor (n, d), float32 or bfloat16
+    y = integrate(F, plan)              # autograd: backward is the same symmetric operator
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtfi.so")
+
+TFI_OK = 0
+_STATUS = {0: "OK", 1: "ARG", 2: "NOT_TREE", 3: "WEIGHT", 4: "GRID_OVERFLOW", 5: "OOM", 6: "CUDA", 7: "TIMEOUT",
+           8: "UNSUPPORTED", 9: "NO_DEVICE"}
+KERNEL_KINDS = {"table": 0, "expsum": 1, "gauss": 2, "rational": 3}
+POLICIES = {"adaptive": 0, "diameter": 1, "centroid": 2}
+DTYPE_F32, DTYPE_BF16 = 0, 1
+EXPORTS = {"calls": (0, 7), "backbone": (1, 1), "records": (2, 5), "leaves": (3, 3)}
+
+
+class TfiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tfi error {_STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = _STATUS.get(code, str(code))
+
+
+class _Tree(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("u", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+class _Kernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_params", ctypes.c_int32), ("params", ctypes.c_void_p),
+                ("table_len", ctypes.c_int64), ("table", ctypes.c_void_p)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("policy", ctypes.c_int32), ("leaf_max", ctypes.c_int32),
+                ("max_channels", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "n", "n_calls", "n_leaves", "n_levels", "n_records", "n_keys", "n_jobs_fft", "n_jobs_direct",
+        "n_centroid", "sum_table", "sum_fft_points", "sum_leaf_pairs", "ftab_len", "device_bytes")] + [
+        ("plan_seconds", ctypes.c_double)]
+
+
+EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_host", "tfi_destroy",
+                    "tfi_plan_get_info", "tfi_plan_export", "tfi_profile_enable", "tfi_profile_read",
+                    "tfi_stage_model", "tfi_last_error")
+STAGES = ("leaf", "bucket", "fft", "direct", "gather")
+
+_lib = None
+
+
+def lib():
+    """The loaded libtfi (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2609_34025_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.tfi_plan.argtypes = [ctypes.POINTER(_Tree), ctypes.POINTER(_Kernel), ctypes.POINTER(_Options),
+                               ctypes.POINTER(vp)]
+        L.tfi_apply.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.tfi_apply_backward.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.tfi_apply_host.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.tfi_destroy.argtypes = [vp]
+        L.tfi_plan_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
+        L.tfi_plan_export.argtypes = [vp, i32, vp, i64, ctypes.POINTER(i64)]
+        L.tfi_profile_enable.argtypes = [vp, i32]
+        L.tfi_profile_read.argtypes = [vp, vp, vp]
+        L.tfi_stage_model.argtypes = [vp, i32, i32, vp, vp]
+        L.tfi_last_error.restype = ctypes.c_char_p
+        for name in EXPORTED_SYMBOLS[:-1]:
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != TFI_OK:
+        raise TfiError(code, lib().tfi_last_error().decode())
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+
+    if t.dtype == torch.float32:
+        return DTYPE_F32
+    if t.dtype == torch.bfloat16:
+        return DTYPE_BF16
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+class Plan:
+    """A planned tree (or forest): the decomposition, f samples and spectra on the device."""
+
+    def __init__(self, n, u, v, w, delta=1.0, kernel=("expsum", [1.0, 1.0]), table=None, policy="adaptive",
+                 leaf_max=64, max_channels=16, host_only=False):
+        u = np.ascontiguousarray(u, dtype=np.int32)
+        v = np.ascontiguousarray(v, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        kind, params = kernel
+        params = np.ascontiguousarray(params, dtype=np.float64)
+        tab = None if table is None else np.ascontiguousarray(table, dtype=np.float64)
+        tree = _Tree(int(n), int(u.shape[0]), u.ctypes.data, v.ctypes.data, w.ctypes.data)
+        ker = _Kernel(KERNEL_KINDS[kind], int(params.shape[0]), params.ctypes.data if params.size else None,
+                      0 if tab is None else int(tab.shape[0]), None if tab is None else tab.ctypes.data)
+        opt = _Options(float(delta), POLICIES[policy], int(leaf_max), int(max_channels), 1 if host_only else 0)
+        h = ctypes.c_void_p()
+        _check(lib().tfi_plan(ctypes.byref(tree), ctypes.byref(ker), ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+        self.n = int(n)
+        self.max_channels = int(max_channels)
+        self.host_only = host_only
+
+    @classmethod
+    def from_spec(cls, tree, delta, spec, **kw):
+        """Build from any tree with (n, u, v, w) and a kernel spec with (kind, params, table)."""
+        return cls(tree.n, tree.u, tree.v, tree.w, delta=delta, kernel=(spec.kind, list(spec.params)),
+                   table=getattr(spec, "table", None), **kw)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tfi_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _apply(self, fn, F, out, stream):
+        import torch
+
+        if not F.is_cuda or F.dim() != 2 or F.shape[0] != self.n or not F.is_contiguous():
+            raise ValueError("F must be a contiguous CUDA tensor of shape (n, d)")
+        if out is None:
+            out = torch.empty_like(F)
+        if out.shape != F.shape or out.dtype != F.dtype or not out.is_contiguous():
+            raise ValueError("out must match F")
+        _check(fn(self._h, ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(F.shape[1]),
+                  _dtype_code(F), _stream_handle(stream)))
+        return out
+
+    def apply(self, F, out=None, stream=None):
+        """out = K F on the device (stream-ordered)."""
+        return self._apply(lib().tfi_apply, F, out, stream)
+
+    def apply_backward(self, grad_out, out=None, stream=None):
+        """grad_F = K^T grad_out (= K grad_out: the operator is symmetric)."""
+        return self._apply(lib().tfi_apply_backward, grad_out, out, stream)
+
+    def apply_host(self, F: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """Host arrays in and out: copies, apply, copies back, synchronised."""
+        if F.dtype != np.float32 or F.ndim != 2 or F.shape[0] != self.n:
+            raise ValueError("F must be float32 of shape (n, d)")
+        F = np.ascontiguousarray(F)
+        if out is None:
+            out = np.empty_like(F)
+        _check(lib().tfi_apply_host(self._h, ctypes.c_void_p(F.ctypes.data), ctypes.c_void_p(out.ctypes.data),
+                                    int(F.shape[1]), DTYPE_F32, _stream_handle(stream)))
+        return out
+
+    def apply_host_ptr(self, f_ptr: int, out_ptr: int, d: int, dtype: int = DTYPE_F32, stream=None):
+        """Host pointers (e.g. pinned torch tensors) in and out, synchronised."""
+        _check(lib().tfi_apply_host(self._h, ctypes.c_void_p(f_ptr), ctypes.c_void_p(out_ptr), int(d), int(dtype),
+                                    _stream_handle(stream)))
+
+    def info(self) -> dict:
+        inf = _Info()
+        _check(lib().tfi_plan_get_info(self._h, ctypes.byref(inf)))
+        return {name: getattr(inf, name) for name, _ in _Info._fields_}
+
+    def profile(self, enable: bool = True):
+        """Start (clearing totals) or stop per-stage CUDA-event timing."""
+        _check(lib().tfi_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{stage: (milliseconds, launches)} summed since profiling was enabled (synchronises)."""
+        ms = np.zeros(len(STAGES), dtype=np.float64)
+        ln = np.zeros(len(STAGES), dtype=np.int64)
+        _check(lib().tfi_profile_read(self._h, ms.ctypes.data, ln.ctypes.data))
+        return {k: (float(ms[i]), int(ln[i])) for i, k in enumerate(STAGES)}
+
+    def stage_model(self, d: int, dtype: int = DTYPE_F32) -> dict:
+        """{stage: (algorithmic bytes, flops)} for one apply with d channels."""
+        b = np.zeros(len(STAGES), dtype=np.float64)
+        f = np.zeros(len(STAGES), dtype=np.float64)
+        _check(lib().tfi_stage_model(self._h, int(d), int(dtype), b.ctypes.data, f.ctypes.data))
+        return {k: (float(b[i]), float(f[i])) for i, k in enumerate(STAGES)}
+
+    def export(self, what: str) -> np.ndarray:
+        code, width = EXPORTS[what]
+        ln = ctypes.c_int64()
+        _check(lib().tfi_plan_export(self._h, code, None, 0, ctypes.byref(ln)))
+        buf = np.empty(ln.value, dtype=np.int64)
+        _check(lib().tfi_plan_export(self._h, code, buf.ctypes.data if ln.value else None, ln.value,
+                                     ctypes.byref(ln)))
+        return buf.reshape(-1, width) if width > 1 else buf
+
+
+def _autograd_fn():
+    import torch
+
+    class TreeFieldIntegral(torch.autograd.Function):
+        """y = K F with dL/dF = K dL/dy (K symmetric)."""
+
+        @staticmethod
+        def forward(ctx, F, plan):
+            ctx.plan = plan
+            return plan.apply(F.contiguous())
+
+        @staticmethod
+        def backward(ctx, g):
+            return ctx.plan.apply_backward(g.contiguous()), None
+
+    return TreeFieldIntegral
+
+
+_TFI = None
+
+
+def integrate(F, plan: Plan):
+    """Differentiable out = K F (autograd through the hand-written adjoint)."""
+    global _TFI
+    if _TFI is None:
+        _TFI = _autograd_fn()
+    return _TFI.apply(F, plan)

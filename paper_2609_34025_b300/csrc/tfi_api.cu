@@ -1,0 +1,561 @@
+// C ABI of libtfi (include/tfi.h): plan upload, apply orchestration, export.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "planner.hpp"
+#include "tfi.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+tfi_status fail(tfi_status code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define TFI_CUDA(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(TFI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+struct WorkLists {
+    // FFT items grouped by log2(P1 P2): one launch per class
+    std::vector<int> fft_lnp;
+    std::vector<int> fft_count;
+    std::vector<int> fft_npair;
+    std::vector<int64_t> fft_off;
+    tfi::dev::FftItem *d_fft = nullptr;
+    tfi::dev::DirItem *d_dir = nullptr;
+    int n_dir = 0;
+};
+
+}  // namespace
+
+struct tfi_plan_s {
+    tfi::HostPlan hp;
+    bool on_device = false;
+    int device = -1;
+    int64_t dev_bytes = 0;
+    std::vector<void *> allocs;
+    // device arrays
+    int32_t *key_r = nullptr, *key_x = nullptr, *key_ptr = nullptr, *key_vtx = nullptr;
+    tfi::dev::JobDev *jobs = nullptr;
+    int32_t *vrec_ptr = nullptr, *vrec_akey = nullptr, *vrec_bkey = nullptr;
+    int32_t *lgrp_ptr = nullptr, *leaf_vtx = nullptr, *leaf_dist = nullptr, *leaf_pdist = nullptr;
+    int32_t *leaf_lo = nullptr, *leaf_hi = nullptr;
+    uint8_t *in_leaf = nullptr;
+    int32_t max_gs = 0, n_groups = 0;
+    float *ftab = nullptr;
+    float2 *spectra = nullptr, *twiddle = nullptr;
+    float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
+    void *stage_in = nullptr, *stage_out = nullptr;
+    std::map<int, WorkLists> work;  // per channel count d
+    // stage profiling (CUDA events on the apply stream)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct StageRec {
+        int stage;
+        int launches;
+        cudaEvent_t a, b;
+    };
+    std::vector<StageRec> prof;
+    cudaEvent_t next_event() {
+        if (ev_used == ev_pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            ev_pool.push_back(e);
+        }
+        return ev_pool[ev_used++];
+    }
+
+    template <typename T>
+    tfi_status upload(T **dst, const std::vector<T> &src) {
+        if (src.empty()) {
+            *dst = nullptr;
+            return TFI_OK;
+        }
+        void *p = nullptr;
+        if (cudaMalloc(&p, src.size() * sizeof(T)) != cudaSuccess)
+            return fail(TFI_ERR_OOM, "cudaMalloc failed while uploading the plan");
+        allocs.push_back(p);
+        dev_bytes += int64_t(src.size() * sizeof(T));
+        TFI_CUDA(cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+        *dst = static_cast<T *>(p);
+        return TFI_OK;
+    }
+    tfi_status alloc(void **dst, size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        if (cudaMalloc(dst, bytes) != cudaSuccess) return fail(TFI_ERR_OOM, "cudaMalloc failed for the workspace");
+        allocs.push_back(*dst);
+        dev_bytes += int64_t(bytes);
+        return TFI_OK;
+    }
+    ~tfi_plan_s() {
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        for (auto &kv : work) {
+            cudaFree(kv.second.d_fft);
+            cudaFree(kv.second.d_dir);
+        }
+        for (void *p : allocs) cudaFree(p);
+    }
+};
+
+namespace {
+
+constexpr int kFftThreads = 256;
+constexpr int kFftSmemPairPoints = 1 << 13;  // points x pairs per CTA (64 KB) for classes below 2^14
+
+int fft_pairs_per_cta(int lnp, int pairs) {
+    const int cap = lnp >= 13 ? 1 : (kFftSmemPairPoints >> lnp);
+    return std::max(1, std::min(pairs, cap));
+}
+
+tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
+    auto it = p->work.find(d);
+    if (it != p->work.end()) {
+        *out = &it->second;
+        return TFI_OK;
+    }
+    WorkLists wl;
+    const int pairs = (d + 1) / 2;
+    std::map<int, std::vector<tfi::dev::FftItem>> by_class;
+    std::vector<tfi::dev::DirItem> dir;
+    const auto &jobs = p->hp.jobs;
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        const tfi::Job &jb = jobs[j];
+        if (jb.ke == jb.kb) continue;
+        if (jb.mode == 0) {
+            const int lnp = jb.lp1 + jb.lp2;
+            const int np = fft_pairs_per_cta(lnp, pairs);
+            for (int p0 = 0; p0 < pairs; p0 += np)
+                by_class[lnp].push_back(tfi::dev::FftItem{int32_t(j), p0, std::min(np, pairs - p0)});
+        } else {
+            for (int64_t q = jb.kb; q < jb.ke; q += 32) dir.push_back(tfi::dev::DirItem{int32_t(j), int32_t(q)});
+        }
+    }
+    std::vector<tfi::dev::FftItem> all;
+    for (auto &kv : by_class) {
+        wl.fft_lnp.push_back(kv.first);
+        wl.fft_count.push_back(int(kv.second.size()));
+        wl.fft_npair.push_back(fft_pairs_per_cta(kv.first, pairs));
+        wl.fft_off.push_back(int64_t(all.size()));
+        all.insert(all.end(), kv.second.begin(), kv.second.end());
+    }
+    if (!all.empty()) {
+        TFI_CUDA(cudaMalloc(&wl.d_fft, all.size() * sizeof(all[0])));
+        TFI_CUDA(cudaMemcpy(wl.d_fft, all.data(), all.size() * sizeof(all[0]), cudaMemcpyHostToDevice));
+    }
+    wl.n_dir = int(dir.size());
+    if (!dir.empty()) {
+        TFI_CUDA(cudaMalloc(&wl.d_dir, dir.size() * sizeof(dir[0])));
+        TFI_CUDA(cudaMemcpy(wl.d_dir, dir.data(), dir.size() * sizeof(dir[0]), cudaMemcpyHostToDevice));
+    }
+    auto res = p->work.emplace(d, wl);
+    *out = &res.first->second;
+    return TFI_OK;
+}
+
+int grid_for(int64_t work, int threads) {
+    const int64_t b = (work + threads - 1) / threads;
+    return int(std::max<int64_t>(1, std::min<int64_t>(b, 148 * 32)));
+}
+
+template <int CH, typename T>
+void launch_leaf(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
+    if (p->n_groups == 0) return;
+    int levels = 1;
+    while ((2 << (levels - 1)) <= p->max_gs) ++levels;
+    const size_t smem = size_t(p->max_gs) * (1 + levels) * 4 + size_t(p->max_gs) * CH * 4;
+    dim3 grid(p->n_groups, (d + CH - 1) / CH);
+    tfi::dev::leaf_kernel<T, CH><<<grid, 256, smem, s>>>(p->lgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist,
+                                                         p->leaf_lo, p->leaf_hi, F, d, p->ftab, p->lbuf, p->max_gs);
+}
+
+template <int CH>
+void launch_direct(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
+    if (wl.n_dir == 0) return;
+    constexpr int WARPS = 4;
+    dim3 grid((wl.n_dir + WARPS - 1) / WARPS, (d + CH - 1) / CH);
+    tfi::dev::direct_kernel<CH, WARPS><<<grid, 32 * WARPS, 0, s>>>(wl.d_dir, wl.n_dir, p->jobs, p->key_r, p->key_x,
+                                                                   d, p->kbuf, p->vbuf, p->ftab);
+}
+
+bool g_attr_done = false;
+
+tfi_status set_attributes() {
+    if (g_attr_done) return TFI_OK;
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 129 * 1024));
+#define LEAF_ATTR(T, CH)                                                                                      \
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::leaf_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  200 * 1024));
+    LEAF_ATTR(float, 1) LEAF_ATTR(float, 2) LEAF_ATTR(float, 4) LEAF_ATTR(float, 8) LEAF_ATTR(float, 16)
+    LEAF_ATTR(__nv_bfloat16, 1) LEAF_ATTR(__nv_bfloat16, 2) LEAF_ATTR(__nv_bfloat16, 4)
+    LEAF_ATTR(__nv_bfloat16, 8) LEAF_ATTR(__nv_bfloat16, 16)
+#undef LEAF_ATTR
+    g_attr_done = true;
+    return TFI_OK;
+}
+
+struct StageMark {
+    tfi_plan_t p;
+    cudaStream_t s;
+    int stage;
+    cudaEvent_t a = nullptr;
+    StageMark(tfi_plan_t p_, cudaStream_t s_, int st) : p(p_), s(s_), stage(st) {
+        if (p->profiling && (a = p->next_event())) cudaEventRecord(a, s);
+    }
+    void done(int launches) {
+        if (!a) return;
+        cudaEvent_t b = p->next_event();
+        if (!b) return;
+        cudaEventRecord(b, s);
+        p->prof.push_back({stage, launches, a, b});
+    }
+};
+
+template <typename T>
+tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
+    WorkLists *wl = nullptr;
+    if (tfi_status rc = build_work(p, d, &wl)) return rc;
+    if (tfi_status rc = set_attributes()) return rc;
+    const int n = p->hp.n;
+    // (a7) dense leaves -> lbuf
+    StageMark m_leaf(p, s, TFI_STAGE_LEAF);
+    if (d >= 16) launch_leaf<16>(p, F, d, s);
+    else if (d > 4) launch_leaf<8>(p, F, d, s);
+    else if (d > 2) launch_leaf<4>(p, F, d, s);
+    else if (d == 2) launch_leaf<2>(p, F, d, s);
+    else launch_leaf<1>(p, F, d, s);
+    m_leaf.done(p->n_groups > 0 ? 1 : 0);
+    // (a3) bin sums
+    const int64_t n_keys = int64_t(p->hp.key_r.size());
+    if (n_keys > 0) {
+        StageMark m_bucket(p, s, TFI_STAGE_BUCKET);
+        if (d % 4 == 0)
+            tfi::dev::bucket_kernel<T, 4><<<grid_for(n_keys * (d / 4), 256), 256, 0, s>>>(n_keys, p->key_ptr,
+                                                                                          p->key_vtx, F, d, p->kbuf);
+        else
+            tfi::dev::bucket_kernel<T, 1><<<grid_for(n_keys * d, 256), 256, 0, s>>>(n_keys, p->key_ptr, p->key_vtx,
+                                                                                    F, d, p->kbuf);
+        m_bucket.done(1);
+        // (a4, a5) tables by FFT, one launch per size class, then the direct jobs
+        StageMark m_fft(p, s, TFI_STAGE_FFT);
+        for (size_t c = 0; c < wl->fft_lnp.size(); ++c) {
+            const size_t smem = size_t(wl->fft_npair[c]) * (size_t(1) << wl->fft_lnp[c]) * sizeof(float2);
+            tfi::dev::fft_kernel<<<wl->fft_count[c], kFftThreads, smem, s>>>(
+                wl->d_fft + wl->fft_off[c], p->jobs, p->key_r, p->key_x, d, p->kbuf, p->vbuf, p->spectra, p->twiddle);
+        }
+        m_fft.done(int(wl->fft_lnp.size()));
+        StageMark m_dir(p, s, TFI_STAGE_DIRECT);
+        if (d >= 16) launch_direct<16>(p, *wl, d, s);
+        else if (d > 4) launch_direct<8>(p, *wl, d, s);
+        else if (d > 2) launch_direct<4>(p, *wl, d, s);
+        else if (d == 2) launch_direct<2>(p, *wl, d, s);
+        else launch_direct<1>(p, *wl, d, s);
+        m_dir.done(wl->n_dir > 0 ? 1 : 0);
+    }
+    // (a6) gather
+    StageMark m_gather(p, s, TFI_STAGE_GATHER);
+    if (d % 4 == 0)
+        tfi::dev::gather_kernel<T, 4><<<grid_for(int64_t(n) * (d / 4), 256), 256, 0, s>>>(
+            n, p->vrec_ptr, p->vrec_akey, p->vrec_bkey, p->vbuf, p->lbuf, p->in_leaf, d, out);
+    else
+        tfi::dev::gather_kernel<T, 1><<<grid_for(int64_t(n) * d, 256), 256, 0, s>>>(
+            n, p->vrec_ptr, p->vrec_akey, p->vrec_bkey, p->vbuf, p->lbuf, p->in_leaf, d, out);
+    m_gather.done(1);
+    TFI_CUDA(cudaGetLastError());
+    return TFI_OK;
+}
+
+tfi_status upload_plan(tfi_plan_t p) {
+    tfi::HostPlan &hp = p->hp;
+    TFI_CUDA(cudaGetDevice(&p->device));
+    if (tfi_status rc = p->upload(&p->key_r, hp.key_r)) return rc;
+    if (tfi_status rc = p->upload(&p->key_x, hp.key_x)) return rc;
+    if (tfi_status rc = p->upload(&p->key_ptr, hp.key_ptr)) return rc;
+    if (tfi_status rc = p->upload(&p->key_vtx, hp.key_vtx)) return rc;
+    std::vector<tfi::dev::JobDev> jd(hp.jobs.size());
+    for (size_t j = 0; j < hp.jobs.size(); ++j) {
+        const tfi::Job &jb = hp.jobs[j];
+        jd[j].kb = int32_t(jb.kb);
+        jd[j].ke = int32_t(jb.ke);
+        jd[j].lp1 = jb.lp1;
+        jd[j].lp2 = jb.lp2;
+        jd[j].spec_off = jb.mode == 0 ? hp.spec_class_off[size_t(jb.lp1 * 16 + jb.lp2)] / 2 : 0;
+        jd[j].pad = 0;
+    }
+    if (tfi_status rc = p->upload(&p->jobs, jd)) return rc;
+    if (tfi_status rc = p->upload(&p->vrec_ptr, hp.vrec_ptr)) return rc;
+    if (tfi_status rc = p->upload(&p->vrec_akey, hp.vrec_akey)) return rc;
+    if (tfi_status rc = p->upload(&p->vrec_bkey, hp.vrec_bkey)) return rc;
+    if (tfi_status rc = p->upload(&p->lgrp_ptr, hp.lgrp_ptr)) return rc;
+    if (tfi_status rc = p->upload(&p->leaf_vtx, hp.leaf_vtx)) return rc;
+    if (tfi_status rc = p->upload(&p->leaf_dist, hp.leaf_dist)) return rc;
+    if (tfi_status rc = p->upload(&p->leaf_pdist, hp.leaf_pdist)) return rc;
+    if (tfi_status rc = p->upload(&p->leaf_lo, hp.leaf_lo)) return rc;
+    if (tfi_status rc = p->upload(&p->leaf_hi, hp.leaf_hi)) return rc;
+    if (tfi_status rc = p->upload(&p->in_leaf, hp.in_leaf)) return rc;
+    p->n_groups = int32_t(hp.lgrp_ptr.size()) - 1;
+    p->max_gs = 1;
+    for (int g = 0; g < p->n_groups; ++g)
+        p->max_gs = std::max(p->max_gs, hp.lgrp_ptr[size_t(g) + 1] - hp.lgrp_ptr[size_t(g)]);
+    if (tfi_status rc = p->upload(&p->ftab, hp.ftab)) return rc;
+    std::vector<float2> spec(hp.spectra.size() / 2), tw(hp.twiddle.size() / 2);
+    std::memcpy(spec.data(), hp.spectra.data(), hp.spectra.size() * sizeof(float));
+    std::memcpy(tw.data(), hp.twiddle.data(), hp.twiddle.size() * sizeof(float));
+    if (tfi_status rc = p->upload(&p->spectra, spec)) return rc;
+    if (tfi_status rc = p->upload(&p->twiddle, tw)) return rc;
+    const size_t K = hp.key_r.size(), dm = size_t(hp.max_channels);
+    if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->kbuf), K * dm * sizeof(float))) return rc;
+    if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->vbuf), K * dm * sizeof(float))) return rc;
+    if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->lbuf), size_t(hp.n) * dm * sizeof(float))) return rc;
+    p->on_device = true;
+    return TFI_OK;
+}
+
+tfi_status check_apply_args(tfi_plan_t p, const void *a, const void *b, int32_t d, int32_t dtype) {
+    if (!p || !a || !b) return fail(TFI_ERR_ARG, "null plan or field pointer");
+    if (!p->on_device) return fail(TFI_ERR_NO_DEVICE, "plan was built host-only");
+    if (d < 1 || d > p->hp.max_channels) return fail(TFI_ERR_ARG, "d must be in [1, max_channels]");
+    if (dtype != TFI_DTYPE_F32 && dtype != TFI_DTYPE_BF16) return fail(TFI_ERR_ARG, "unknown dtype");
+    if (a == b) return fail(TFI_ERR_ARG, "out must not alias F");
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != p->device)
+        return fail(TFI_ERR_ARG, "the current device is not the plan's device");
+    return TFI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tfi_last_error(void) { return g_err.c_str(); }
+
+tfi_status tfi_plan(const tfi_tree *tree, const tfi_kernel *kernel, const tfi_options *opt, tfi_plan_t *out) {
+    g_err.clear();
+    if (!tree || !kernel || !opt || !out) return fail(TFI_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (tree->n < 1 || tree->n_edges < 0 || tree->n_edges > tree->n - 1)
+        return fail(TFI_ERR_ARG, "need n >= 1 and 0 <= n_edges <= n - 1");
+    if (tree->n_edges > 0 && (!tree->u || !tree->v || !tree->w)) return fail(TFI_ERR_ARG, "null edge array");
+    if (!(opt->delta > 0.0) || !std::isfinite(opt->delta)) return fail(TFI_ERR_ARG, "delta must be finite and > 0");
+    if (opt->policy < 0 || opt->policy > 2) return fail(TFI_ERR_ARG, "unknown policy");
+    if (opt->leaf_max < 1 || opt->leaf_max > tfi::kLeafMax)
+        return fail(TFI_ERR_ARG, "leaf_max must be in [1, " + std::to_string(tfi::kLeafMax) + "]");
+    if (opt->max_channels < 1) return fail(TFI_ERR_ARG, "max_channels must be >= 1");
+    if (kernel->kind < 0 || kernel->kind > 3) return fail(TFI_ERR_ARG, "unknown kernel kind");
+    if (kernel->n_params < 0 || (kernel->n_params > 0 && !kernel->params)) return fail(TFI_ERR_ARG, "bad kernel params");
+    const int need[4] = {0, 2, 2, 4};
+    if (kernel->kind == TFI_F_EXPSUM ? (kernel->n_params < 2 || kernel->n_params % 2)
+                                     : kernel->n_params != need[kernel->kind])
+        return fail(TFI_ERR_ARG, "wrong number of kernel parameters");
+    if (kernel->kind == TFI_F_TABLE && (kernel->table_len < 1 || !kernel->table))
+        return fail(TFI_ERR_ARG, "sampled kernel needs a table");
+    std::unique_ptr<tfi_plan_s> p(new (std::nothrow) tfi_plan_s());
+    if (!p) return fail(TFI_ERR_OOM, "host allocation failed");
+    tfi::HostPlan &hp = p->hp;
+    hp.delta = opt->delta;
+    hp.policy = opt->policy;
+    hp.leaf_max = opt->leaf_max;
+    hp.max_channels = opt->max_channels;
+    hp.f.kind = kernel->kind;
+    hp.f.params.assign(kernel->params, kernel->params + kernel->n_params);
+    if (kernel->kind == TFI_F_TABLE) hp.f.table.assign(kernel->table, kernel->table + kernel->table_len);
+    std::string err;
+    int rc;
+    try {
+        rc = tfi::build_plan(hp, tree->n, tree->n_edges, tree->u, tree->v, tree->w, err);
+    } catch (const std::bad_alloc &) {
+        return fail(TFI_ERR_OOM, "host allocation failed while planning");
+    }
+    if (rc) return fail(rc, err);
+    if (!(opt->flags & TFI_PLAN_HOST_ONLY)) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+            return fail(TFI_ERR_NO_DEVICE, "no CUDA device (build with TFI_PLAN_HOST_ONLY to plan on the host)");
+        if (tfi_status r2 = upload_plan(p.get())) return r2;
+    }
+    *out = p.release();
+    return TFI_OK;
+}
+
+tfi_status tfi_apply(tfi_plan_t plan, const void *F, void *out, int32_t d, int32_t dtype, tfi_stream_t stream) {
+    if (tfi_status rc = check_apply_args(plan, F, out, d, dtype)) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dtype == TFI_DTYPE_F32)
+        return apply_impl<float>(plan, static_cast<const float *>(F), static_cast<float *>(out), d, s);
+    return apply_impl<__nv_bfloat16>(plan, static_cast<const __nv_bfloat16 *>(F), static_cast<__nv_bfloat16 *>(out),
+                                     d, s);
+}
+
+tfi_status tfi_apply_backward(tfi_plan_t plan, const void *grad_out, void *grad_F, int32_t d, int32_t dtype,
+                              tfi_stream_t stream) {
+    // K is symmetric: the adjoint is the same integrator applied to grad_out
+    return tfi_apply(plan, grad_out, grad_F, d, dtype, stream);
+}
+
+tfi_status tfi_apply_host(tfi_plan_t plan, const void *F_host, void *out_host, int32_t d, int32_t dtype,
+                          tfi_stream_t stream) {
+    if (!plan || !F_host || !out_host) return fail(TFI_ERR_ARG, "null argument");
+    if (!plan->on_device) return fail(TFI_ERR_NO_DEVICE, "plan was built host-only");
+    const size_t esz = dtype == TFI_DTYPE_BF16 ? 2 : 4;
+    const size_t bytes = size_t(plan->hp.n) * size_t(d) * esz;
+    if (!plan->stage_in) {
+        const size_t cap = size_t(plan->hp.n) * size_t(plan->hp.max_channels) * 4;
+        if (tfi_status rc = plan->alloc(&plan->stage_in, cap)) return rc;
+        if (tfi_status rc = plan->alloc(&plan->stage_out, cap)) return rc;
+    }
+    if (tfi_status rc = check_apply_args(plan, plan->stage_in, plan->stage_out, d, dtype)) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TFI_CUDA(cudaMemcpyAsync(plan->stage_in, F_host, bytes, cudaMemcpyHostToDevice, s));
+    if (tfi_status rc = tfi_apply(plan, plan->stage_in, plan->stage_out, d, dtype, stream)) return rc;
+    TFI_CUDA(cudaMemcpyAsync(out_host, plan->stage_out, bytes, cudaMemcpyDeviceToHost, s));
+    TFI_CUDA(cudaStreamSynchronize(s));
+    return TFI_OK;
+}
+
+tfi_status tfi_destroy(tfi_plan_t plan) {
+    delete plan;
+    return TFI_OK;
+}
+
+tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info) {
+    if (!plan || !info) return fail(TFI_ERR_ARG, "null argument");
+    const tfi::HostPlan &hp = plan->hp;
+    std::memset(info, 0, sizeof(*info));
+    info->n = hp.n;
+    info->n_calls = int64_t(hp.calls.size());
+    info->n_leaves = int64_t(hp.leaves.size());
+    info->n_levels = hp.n_levels;
+    info->n_records = int64_t(hp.recs.size());
+    info->n_keys = int64_t(hp.key_r.size());
+    for (const tfi::Job &j : hp.jobs) {
+        if (j.mode == 0) {
+            info->n_jobs_fft++;
+            info->sum_fft_points += int64_t(1) << (j.lp1 + j.lp2);
+        } else {
+            info->n_jobs_direct++;
+        }
+    }
+    for (const tfi::Call &c : hp.calls) {
+        info->n_centroid += c.kind;
+        info->sum_table += (c.H + 1) * (c.L + 1);
+    }
+    for (const tfi::Leaf &l : hp.leaves) info->sum_leaf_pairs += (l.end - l.begin) * (l.end - l.begin);
+    info->ftab_len = hp.ftab_len;
+    info->device_bytes = plan->dev_bytes;
+    info->plan_seconds = hp.plan_seconds;
+    return TFI_OK;
+}
+
+tfi_status tfi_profile_enable(tfi_plan_t plan, int32_t enable) {
+    if (!plan) return fail(TFI_ERR_ARG, "null plan");
+    plan->profiling = enable != 0;
+    plan->prof.clear();
+    plan->ev_used = 0;
+    return TFI_OK;
+}
+
+tfi_status tfi_profile_read(tfi_plan_t plan, double *ms, int64_t *launches) {
+    if (!plan || !ms || !launches) return fail(TFI_ERR_ARG, "null argument");
+    for (int i = 0; i < TFI_N_STAGES; ++i) {
+        ms[i] = 0.0;
+        launches[i] = 0;
+    }
+    for (const auto &r : plan->prof) {
+        TFI_CUDA(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        TFI_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.stage] += double(t);
+        launches[r.stage] += r.launches;
+    }
+    return TFI_OK;
+}
+
+tfi_status tfi_stage_model(tfi_plan_t plan, int32_t d, int32_t dtype, double *bytes, double *flops) {
+    if (!plan || !bytes || !flops || d < 1) return fail(TFI_ERR_ARG, "bad argument");
+    const tfi::HostPlan &hp = plan->hp;
+    const double sin = dtype == TFI_DTYPE_BF16 ? 2.0 : 4.0, D = double(d);
+    for (int i = 0; i < TFI_N_STAGES; ++i) bytes[i] = flops[i] = 0.0;
+    const double nleaf = double(hp.leaf_vtx.size());
+    double pairs = 0;
+    for (const tfi::Leaf &l : hp.leaves) pairs += double(l.end - l.begin) * double(l.end - l.begin);
+    bytes[TFI_STAGE_LEAF] = nleaf * (D * sin + 5 * 4) + nleaf * D * 4;
+    flops[TFI_STAGE_LEAF] = 2.0 * D * pairs;
+    const double K = double(hp.key_r.size()), KV = double(hp.key_vtx.size());
+    bytes[TFI_STAGE_BUCKET] = KV * (D * sin + 4) + K * 4 + K * D * 4;
+    double kf = 0, kd = 0;
+    for (const tfi::Job &j : hp.jobs) {
+        const double nk = double(j.ke - j.kb);
+        if (j.mode == 0) {
+            const double np = std::ldexp(1.0, j.lp1 + j.lp2);
+            const double lg = double(j.lp1 + j.lp2);
+            kf += nk;
+            // two complex transforms and one complex product per channel pair
+            flops[TFI_STAGE_FFT] += std::ceil(D / 2) * (2 * 5 * np * lg + 6 * np);
+        } else {
+            kd += nk;
+            flops[TFI_STAGE_DIRECT] += 2.0 * nk * nk * D;
+        }
+    }
+    bytes[TFI_STAGE_FFT] = kf * (2 * D * 4 + 8);
+    bytes[TFI_STAGE_DIRECT] = kd * (2 * D * 4 + 8);
+    const double R = double(hp.recs.size());
+    double nb = 0;
+    for (int32_t b : hp.vrec_bkey) nb += b >= 0;
+    (void)nb;
+    bytes[TFI_STAGE_GATHER] = R * 8 + double(hp.n) * (4 + 1) + K * D * 4 + nleaf * D * 4 + double(hp.n) * D * sin;
+    return TFI_OK;
+}
+
+tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t cap, int64_t *len) {
+    if (!plan || !len) return fail(TFI_ERR_ARG, "null argument");
+    const tfi::HostPlan &hp = plan->hp;
+    std::vector<int64_t> v;
+    switch (what) {
+        case TFI_EXPORT_CALLS:
+            for (const tfi::Call &c : hp.calls) {
+                const int64_t row[7] = {c.level, c.minv, c.size, c.kind, c.bb_end - c.bb_begin, c.H, c.L};
+                v.insert(v.end(), row, row + 7);
+            }
+            break;
+        case TFI_EXPORT_BACKBONE:
+            v.assign(hp.bb.begin(), hp.bb.end());
+            break;
+        case TFI_EXPORT_RECORDS:
+            for (size_t c = 0; c < hp.calls.size(); ++c) {
+                for (int64_t i = hp.calls[c].rec_begin; i < hp.calls[c].rec_end; ++i) {
+                    const tfi::Rec &r = hp.recs[size_t(i)];
+                    const int64_t row[5] = {int64_t(c), r.v, r.r, r.x, r.comp >= 0 ? hp.comps[size_t(r.comp)].minv : -1};
+                    v.insert(v.end(), row, row + 5);
+                }
+            }
+            break;
+        case TFI_EXPORT_LEAVES:
+            for (const tfi::Leaf &l : hp.leaves) {
+                const int64_t row[3] = {l.level, l.minv, l.end - l.begin};
+                v.insert(v.end(), row, row + 3);
+            }
+            break;
+        default:
+            return fail(TFI_ERR_ARG, "unknown export");
+    }
+    *len = int64_t(v.size());
+    if (dst && cap >= int64_t(v.size())) std::memcpy(dst, v.data(), v.size() * sizeof(int64_t));
+    return TFI_OK;
+}
+
+}  // extern "C"

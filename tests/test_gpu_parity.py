@@ -1,0 +1,186 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance (per channel, normwise): max_u |y_gpu - y| / max_u |y| <= 1e-4 for
+FP32 fields and <= 1e-2 for BF16 fields (the bf16 case compares against the
+oracle applied to the bf16-rounded input).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import brute
+
+from ._lib import tfi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-4, "bf16": 1e-2}
+
+
+def _err(y, ref):
+    y = np.asarray(y, dtype=np.float64).reshape(ref.shape[0], -1)
+    ref = ref.reshape(ref.shape[0], -1)
+    scale = np.maximum(np.abs(ref).max(axis=0), 1e-300)
+    return float((np.abs(y - ref).max(axis=0) / scale).max())
+
+
+def _run(t, delta, spec, F, policy="adaptive", leaf_max=64, dtype="f32", targets=None):
+    p = tfi.Plan.from_spec(t, delta, spec, policy=policy, leaf_max=leaf_max, max_channels=F.shape[1])
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    Fd = torch.from_numpy(F).to("cuda", tdt)
+    y = p.apply(Fd)
+    torch.cuda.synchronize()
+    Fin = Fd.float().cpu().numpy().astype(np.float64)
+    ref = brute.integrate(t, delta, spec, Fin, targets=targets)
+    yv = y.float().cpu().numpy()
+    if targets is not None:
+        yv = yv[targets]
+    return p, yv, ref
+
+
+def _rrt(n, seed, lo=1, hi=4):
+    rng = np.random.default_rng(seed)
+    t = W.random_recursive(n, rng)
+    return t.with_weights(W.trees.integer_weights(t.m, lo, hi, rng))
+
+
+@pytest.mark.parametrize("policy", ["adaptive", "diameter", "centroid"])
+@pytest.mark.parametrize("leaf_max", [1, 16, 64, 256])
+def test_rrt_n2000_config(policy, leaf_max):
+    cfg = W.configs.rrt_n2000()
+    F = W.normal_field(cfg["tree"].n, cfg["d"], seed=123)
+    _, y, ref = _run(cfg["tree"], cfg["delta"], cfg["kernel"], F, policy=policy, leaf_max=leaf_max)
+    assert _err(y, ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("shape", ["rrt", "binary", "caterpillar"])
+@pytest.mark.parametrize("kernel", ["exp", "cauchy", "gauss"])
+@pytest.mark.parametrize("d", [1, 16, 64])
+def test_sweep_shapes_small(shape, kernel, d):
+    cfg = W.configs.sweep(shape=shape, n=4096 if shape != "caterpillar" else 2048, d=d, kernel=kernel)
+    F = W.normal_field(cfg["tree"].n, d, seed=123)
+    _, y, ref = _run(cfg["tree"], cfg["delta"], cfg["kernel"], F, leaf_max=64)
+    assert _err(y, ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("make", [lambda: W.spider(8, 200), lambda: W.caterpillar_hanging_paths(24),
+                                  lambda: W.path(3000), lambda: W.star(500), lambda: W.complete_kary(3, 6),
+                                  lambda: W.caterpillar_leaves(300), lambda: W.broom(400),
+                                  lambda: W.preferential_attachment(3000, np.random.default_rng(3))])
+@pytest.mark.parametrize("policy", ["adaptive", "diameter"])
+def test_paper_families_unit_weights(make, policy):
+    t = make()
+    F = W.normal_field(t.n, 3, seed=7)
+    _, y, ref = _run(t, 1.0, W.KernelSpec.rational(1.0), F, policy=policy, leaf_max=8)
+    assert _err(y, ref) <= TOL["f32"]
+
+
+def test_forest_uneven_batch_small():
+    cfg = W.configs.uneven_batch(count=40, lo=8, hi=3000, d=16)
+    F = W.normal_field(cfg["tree"].n, 16, seed=123)
+    _, y, ref = _run(cfg["tree"], cfg["delta"], cfg["kernel"], F, leaf_max=64)
+    assert _err(y, ref) <= TOL["f32"]
+
+
+def test_torus_mst_small():
+    cfg = W.configs.torus_sinkhorn(n=4000, pairs=8)
+    a, _ = W.dirichlet_pairs(cfg["tree"].n, 8, seed=1)
+    _, y, ref = _run(cfg["tree"], cfg["delta"], cfg["kernel"], a.astype(np.float32), leaf_max=64)
+    assert _err(y, ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_attention_grid_trees(dtype):
+    cfg = W.configs.attention(heads=2)
+    for h in cfg["heads"]:
+        F = W.normal_field(h["tree"].n, 64, seed=11)
+        _, y, ref = _run(h["tree"], 1.0, h["kernel"], F, leaf_max=64, dtype=dtype)
+        assert _err(y, ref) <= TOL[dtype]
+
+
+def test_full_size_sampled_rrt_2p20():
+    # the benchmark workload at full size, checked on sampled outputs the oracle computes one by one
+    cfg = W.configs.sweep(shape="rrt", n=1 << 20, d=16, kernel="exp")
+    F = W.normal_field(cfg["tree"].n, 16, seed=123)
+    rng = np.random.default_rng(0)
+    targets = np.sort(rng.choice(cfg["tree"].n, size=48, replace=False)).astype(np.int32)
+    _, y, ref = _run(cfg["tree"], cfg["delta"], cfg["kernel"], F, leaf_max=64, targets=targets)
+    assert _err(y, ref) <= TOL["f32"]
+
+
+def test_deterministic_and_adjoint():
+    t = _rrt(3000, 5)
+    spec = W.KernelSpec.gauss(0.02)
+    p = tfi.Plan.from_spec(t, 1.0, spec, leaf_max=32, max_channels=8)
+    x = torch.randn(t.n, 8, device="cuda")
+    z = torch.randn(t.n, 8, device="cuda")
+    y1 = p.apply(x)
+    y2 = p.apply(x)
+    assert torch.equal(y1, y2)
+    kz = p.apply_backward(z)
+    lhs = float((z.double() * y1.double()).sum())
+    rhs = float((kz.double() * x.double()).sum())
+    assert abs(lhs - rhs) <= 1e-4 * (abs(lhs) + abs(rhs) + 1.0)
+    assert torch.equal(kz, p.apply(z))
+
+
+def test_autograd_function():
+    t = _rrt(500, 6)
+    spec = W.KernelSpec.exp(0.3)
+    p = tfi.Plan.from_spec(t, 1.0, spec, leaf_max=16, max_channels=4)
+    x = torch.randn(t.n, 4, device="cuda", requires_grad=True)
+    g = torch.randn(t.n, 4, device="cuda")
+    y = tfi.integrate(x, p)
+    (y * g).sum().backward()
+    ref = brute.integrate(t, 1.0, spec, g.cpu().numpy())
+    assert _err(x.grad.cpu().numpy(), ref) <= TOL["f32"]
+
+
+def test_apply_host_matches_device():
+    t = _rrt(2500, 8)
+    p = tfi.Plan.from_spec(t, 1.0, W.KernelSpec.exp(0.2), leaf_max=64, max_channels=16)
+    F = W.normal_field(t.n, 16, seed=3)
+    yd = p.apply(torch.from_numpy(F).cuda()).cpu().numpy()
+    yh = p.apply_host(F)
+    assert np.array_equal(yd, yh)
+
+
+@pytest.mark.parametrize("n,edges", [(1, []), (2, [(0, 1)]), (5, [(0, 1), (3, 4)]), (7, [])])
+def test_degenerate_trees(n, edges):
+    u = [a for a, _ in edges]
+    v = [b for _, b in edges]
+    w = [1.5] * len(edges)
+    t = W.trees.Tree(n, np.array(u, np.int32), np.array(v, np.int32), np.array(w))
+    F = W.normal_field(n, 5, seed=1)
+    for s0 in (1, 4):
+        _, y, ref = _run(t, 0.5, W.KernelSpec.exp(0.7), F, leaf_max=s0)
+        assert _err(y, ref) <= TOL["f32"]
+
+
+def test_largest_leaf_and_odd_channels():
+    t = _rrt(3000, 9, 1, 3)
+    F = W.normal_field(t.n, 7, seed=2)
+    _, y, ref = _run(t, 1.0, W.KernelSpec.rational(0.5, e=2.0), F, leaf_max=1024)
+    assert _err(y, ref) <= TOL["f32"]
+
+
+def test_sampled_table_kernel():
+    t = _rrt(1500, 10)
+    tab = 1.0 / (1.0 + np.arange(400) ** 1.5 / 10.0)
+    F = W.normal_field(t.n, 4, seed=4)
+    _, y, ref = _run(t, 1.0, W.KernelSpec.samples(tab), F, leaf_max=32)
+    assert _err(y, ref) <= TOL["f32"]
+
+
+def test_stage_profile_and_model():
+    t = _rrt(20000, 12)
+    p = tfi.Plan.from_spec(t, 1.0, W.KernelSpec.exp(0.1), leaf_max=64, max_channels=16)
+    x = torch.randn(t.n, 16, device="cuda")
+    p.profile(True)
+    p.apply(x)
+    prof = p.profile_read()
+    p.profile(False)
+    assert prof["gather"][1] == 1 and prof["gather"][0] > 0
+    model = p.stage_model(16)
+    assert model["bucket"][0] > 0 and model["leaf"][1] > 0
