@@ -15,6 +15,6 @@ def dirichlet_pairs(n: int, pairs: int, seed: int = 0, dtype=np.float32):
     """`pairs` source/target marginals, each Dirichlet(1) on n vertices.
     Returns (a, b) of shape (n, pairs)."""
     rng = np.random.default_rng(seed)
-    a = rng.dirichlet(np.ones(n), size=pairs).T
-    b = rng.dirichlet(np.ones(n), size=pairs).T
+    a = np.ascontiguousarray(rng.dirichlet(np.ones(n), size=pairs).T)
+    b = np.ascontiguousarray(rng.dirichlet(np.ones(n), size=pairs).T)
     return a.astype(dtype), b.astype(dtype)
