@@ -127,6 +127,31 @@ tfi_status tfi_apply_backward(tfi_plan_t plan, const void *grad_out, void *grad_
 tfi_status tfi_apply_host(tfi_plan_t plan, const void *F_host, void *out_host, int32_t d, int32_t dtype,
                           tfi_stream_t stream);
 
+/* Allocation-free apply: the same result as tfi_apply, for callers that must not
+ * allocate device memory while they run. That includes hosts that own all
+ * device memory through their own allocator or a fixed budget and forbid
+ * libraries from calling cudaMalloc, and latency-critical loops that cannot
+ * absorb cudaMalloc's implicit synchronisation. The paper has no counterpart:
+ * this is a deployment variant of the apply.
+ *
+ * Instead of the plan's workspace and per-d work lists, this call uses one
+ * file-scope device array of TFI_STATIC_SCRATCH_BYTES (32 MiB) that every GPU
+ * loading libtfi holds until the process exits. It calls no cudaMalloc,
+ * cudaFree or other allocating routine; it only copies this d's work lists
+ * from host memory into that array (cudaMemcpyAsync on `stream`).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Plans whose workspace at this d (bin sums, table values, leaf terms and
+ *     work lists) exceeds TFI_STATIC_SCRATCH_BYTES are rejected with
+ *     TFI_ERR_ARG; use tfi_apply for them.
+ *   - All calls share the one array and each call overwrites what it reads, so
+ *     no state carries over; but calls that overlap on the GPU (other streams,
+ *     other plans, other threads) race on it. Serialise them.
+ * F, out, d, dtype and stream follow tfi_apply. */
+#define TFI_STATIC_SCRATCH_BYTES (32u << 20)
+tfi_status tfi_apply_static(tfi_plan_t plan, const void *F, void *out, int32_t d, int32_t dtype, tfi_stream_t stream);
+
 /* Release everything the plan owns. NULL is accepted and ignored. */
 tfi_status tfi_destroy(tfi_plan_t plan);
 

@@ -59,7 +59,7 @@ class _Info(ctypes.Structure):
 
 EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_host", "tfi_destroy",
                     "tfi_plan_get_info", "tfi_plan_export", "tfi_profile_enable", "tfi_profile_read",
-                    "tfi_stage_model", "tfi_last_error")
+                    "tfi_stage_model", "tfi_apply_static", "tfi_last_error")
 STAGES = ("leaf", "bucket", "fft", "direct", "gather")
 
 _lib = None

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -338,6 +339,123 @@ tfi_status check_apply_args(tfi_plan_t p, const void *a, const void *b, int32_t 
     return TFI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free apply (tfi_apply_static): the workspace and the per-d work
+// lists live in one file-scope device array instead of plan-owned cudaMalloc
+// memory. Every GPU that loads this library holds the array until exit.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = size_t(TFI_STATIC_SCRATCH_BYTES);
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxStaticDevices = 256;
+std::mutex g_static_mu;
+void *g_static_addr[kMaxStaticDevices] = {};
+
+// Device address of g_static_scratch on device `dev` (which must be current).
+// In host code the symbol names a host-side stand-in, so the address is looked
+// up once per device with cudaGetSymbolAddress and cached.
+tfi_status static_scratch_address(int dev, unsigned char **out) {
+    if (dev < 0 || dev >= kMaxStaticDevices) return fail(TFI_ERR_ARG, "device ordinal out of range for the static workspace");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(TFI_ERR_CUDA, std::string("cudaGetSymbolAddress(static workspace): ") + cudaGetErrorString(e));
+        g_static_addr[dev] = ptr;
+    }
+    *out = static_cast<unsigned char *>(g_static_addr[dev]);
+    return TFI_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+template <typename T>
+tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
+    if (tfi_status rc = set_attributes()) return rc;
+    // work lists for d, built on the host (same grouping as the plan-owned path)
+    const int pairs = (d + 1) / 2;
+    std::map<int, std::vector<tfi::dev::FftItem>> by_class;
+    std::vector<tfi::dev::DirItem> dir;
+    for (size_t j = 0; j < p->hp.jobs.size(); ++j) {
+        const tfi::Job &jb = p->hp.jobs[j];
+        if (jb.ke == jb.kb) continue;
+        if (jb.mode == 0) {
+            const int lnp = jb.lp1 + jb.lp2;
+            const int np = fft_pairs_per_cta(lnp, pairs);
+            for (int p0 = 0; p0 < pairs; p0 += np)
+                by_class[lnp].push_back(tfi::dev::FftItem{int32_t(j), p0, std::min(np, pairs - p0)});
+        } else {
+            for (int64_t q = jb.kb; q < jb.ke; q += 32) dir.push_back(tfi::dev::DirItem{int32_t(j), int32_t(q)});
+        }
+    }
+    std::vector<tfi::dev::FftItem> fft_all;
+    std::vector<int> cls_lnp, cls_count, cls_npair;
+    std::vector<size_t> cls_off;
+    for (auto &kv : by_class) {
+        cls_lnp.push_back(kv.first);
+        cls_count.push_back(int(kv.second.size()));
+        cls_npair.push_back(fft_pairs_per_cta(kv.first, pairs));
+        cls_off.push_back(fft_all.size());
+        fft_all.insert(fft_all.end(), kv.second.begin(), kv.second.end());
+    }
+    // carve the static array: bin sums, table values, leaf terms, work lists
+    const size_t K = p->hp.key_r.size(), n = size_t(p->hp.n);
+    const size_t o_k = 0;
+    const size_t o_v = o_k + align256(K * size_t(d) * sizeof(float));
+    const size_t o_l = o_v + align256(K * size_t(d) * sizeof(float));
+    const size_t o_f = o_l + align256(n * size_t(d) * sizeof(float));
+    const size_t o_d = o_f + align256(fft_all.size() * sizeof(tfi::dev::FftItem));
+    const size_t total = o_d + align256(dir.size() * sizeof(tfi::dev::DirItem));
+    if (total > kStaticScratchBytes)
+        return fail(TFI_ERR_ARG, "plan needs " + std::to_string(total) + " bytes of workspace at d=" + std::to_string(d) +
+                                     ", more than the static workspace of " + std::to_string(kStaticScratchBytes) +
+                                     " bytes; use tfi_apply");
+    unsigned char *base = nullptr;
+    if (tfi_status rc = static_scratch_address(p->device, &base)) return rc;
+    float *kbuf = reinterpret_cast<float *>(base + o_k);
+    float *vbuf = reinterpret_cast<float *>(base + o_v);
+    float *lbuf = reinterpret_cast<float *>(base + o_l);
+    auto *d_fft = reinterpret_cast<tfi::dev::FftItem *>(base + o_f);
+    auto *d_dir = reinterpret_cast<tfi::dev::DirItem *>(base + o_d);
+    // pageable sources: each copy returns once the host data has been staged
+    if (!fft_all.empty())
+        TFI_CUDA(cudaMemcpyAsync(d_fft, fft_all.data(), fft_all.size() * sizeof(fft_all[0]), cudaMemcpyHostToDevice, s));
+    if (!dir.empty())
+        TFI_CUDA(cudaMemcpyAsync(d_dir, dir.data(), dir.size() * sizeof(dir[0]), cudaMemcpyHostToDevice, s));
+    // every workspace value an apply reads is written earlier in the same apply,
+    // so nothing needs clearing between calls
+    if (p->n_groups > 0) {
+        int levels = 1;
+        while ((2 << (levels - 1)) <= p->max_gs) ++levels;
+        const int CH = 16;
+        const size_t smem = size_t(p->max_gs) * (1 + levels) * 4 + size_t(p->max_gs) * CH * 4;
+        dim3 grid(p->n_groups, (d + CH - 1) / CH);
+        tfi::dev::leaf_kernel<T, 16><<<grid, 256, smem, s>>>(p->lgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist,
+                                                             p->leaf_lo, p->leaf_hi, F, d, p->ftab, lbuf, p->max_gs);
+    }
+    if (K > 0) {
+        tfi::dev::bucket_kernel<T, 1><<<grid_for(int64_t(K) * d, 256), 256, 0, s>>>(int64_t(K), p->key_ptr, p->key_vtx,
+                                                                                   F, d, kbuf);
+        for (size_t c = 0; c < cls_lnp.size(); ++c) {
+            const size_t smem = size_t(cls_npair[c]) * (size_t(1) << cls_lnp[c]) * sizeof(float2);
+            tfi::dev::fft_kernel<<<cls_count[c], kFftThreads, smem, s>>>(d_fft + cls_off[c], p->jobs, p->key_r,
+                                                                        p->key_x, d, kbuf, vbuf, p->spectra,
+                                                                        p->twiddle);
+        }
+        if (!dir.empty()) {
+            constexpr int WARPS = 4;
+            dim3 grid((unsigned(dir.size()) + WARPS - 1) / WARPS, (d + 15) / 16);
+            tfi::dev::direct_kernel<16, WARPS><<<grid, 32 * WARPS, 0, s>>>(d_dir, int(dir.size()), p->jobs, p->key_r,
+                                                                           p->key_x, d, kbuf, vbuf, p->ftab);
+        }
+    }
+    tfi::dev::gather_kernel<T, 1><<<grid_for(int64_t(n) * d, 256), 256, 0, s>>>(
+        int(n), p->vrec_ptr, p->vrec_akey, p->vrec_bkey, vbuf, lbuf, p->in_leaf, d, out);
+    TFI_CUDA(cudaGetLastError());
+    return TFI_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -405,6 +523,16 @@ tfi_status tfi_apply_backward(tfi_plan_t plan, const void *grad_out, void *grad_
                               tfi_stream_t stream) {
     // K is symmetric: the adjoint is the same integrator applied to grad_out
     return tfi_apply(plan, grad_out, grad_F, d, dtype, stream);
+}
+
+tfi_status tfi_apply_static(tfi_plan_t plan, const void *F, void *out, int32_t d, int32_t dtype,
+                            tfi_stream_t stream) {
+    if (tfi_status rc = check_apply_args(plan, F, out, d, dtype)) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dtype == TFI_DTYPE_F32)
+        return apply_static_impl<float>(plan, static_cast<const float *>(F), static_cast<float *>(out), d, s);
+    return apply_static_impl<__nv_bfloat16>(plan, static_cast<const __nv_bfloat16 *>(F),
+                                            static_cast<__nv_bfloat16 *>(out), d, s);
 }
 
 tfi_status tfi_apply_host(tfi_plan_t plan, const void *F_host, void *out_host, int32_t d, int32_t dtype,
