@@ -99,50 +99,162 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
-// Radix-2 passes along one axis of npair arrays of NP points each.
-// Axis of length n = 2^ln with element stride `stride`; the other axis has
-// `lines` lines with stride `lstride`. rows: stride 1, lstride n. cols: stride
-// lines, lstride 1 (consecutive threads take consecutive columns).
-template <bool INVERSE>
-__device__ __forceinline__ void fft_axis(float2 *Z, int npair, int lnp, int ln, int stride, int lines, int lstride,
-                                         bool cols, const float2 *__restrict__ tw) {
-    if (ln == 0) return;
-    const int NP = 1 << lnp;
-    const int half_np = NP >> 1;
-    const int nb = npair * half_np;
-    const int hn = 1 << (ln - 1);  // butterflies per line
-    for (int s = 0; s < ln; ++s) {
-        const int lh = INVERSE ? s : (ln - 1 - s);  // log2(half)
-        const int half = 1 << lh;
-        const int twshift = kTwLogDev - 1 - lh;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            const int p = b >> (lnp - 1);
-            const int bb = b & (half_np - 1);
-            int line, k;
-            if (cols) {
-                line = bb & (lines - 1);
-                k = bb / lines;
-            } else {
-                line = bb >> (ln - 1);
-                k = bb & (hn - 1);
+// Shared-memory layout of one FFT array: element e lives at e + (e >> 5), one
+// pad slot per 32 elements, so that the strided 8-byte accesses of the
+// small-span passes spread over all banks.
+__device__ __forceinline__ int padded(int e) { return e + (e >> 5); }
+__host__ __device__ constexpr int padded_size(int np) { return np + (np >> 5); }
+
+template <int RL>
+__device__ __forceinline__ constexpr int brev_c(int q) {
+    return RL == 1 ? q : RL == 2 ? (((q & 1) << 1) | (q >> 1)) : (((q & 1) << 2) | (q & 2) | ((q >> 2) & 1));
+}
+
+// Multiply by the constant twiddle exp(-2 pi i j / (2 dt)) (CONJ: its conjugate)
+// for dt <= 4, without general complex products where the value is trivial.
+template <int DT, int J, bool CONJ>
+__device__ __forceinline__ float2 mul_c(float2 a) {
+    constexpr float c = 0.70710678118654752f;
+    if (J == 0) return a;
+    if (DT == 2 || (DT == 4 && J == 2))  // -i (conjugate: +i)
+        return CONJ ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    if (J == 1)  // (1 - i)/sqrt2 (conjugate: (1 + i)/sqrt2)
+        return CONJ ? make_float2(c * (a.x - a.y), c * (a.x + a.y)) : make_float2(c * (a.x + a.y), c * (a.y - a.x));
+    // J == 3: (-1 - i)/sqrt2 (conjugate: (-1 + i)/sqrt2)
+    return CONJ ? make_float2(-c * (a.x + a.y), c * (a.x - a.y)) : make_float2(c * (a.y - a.x), -c * (a.x + a.y));
+}
+
+// In-register 2^RL-point DFT, natural order in, bit-reversed order out (radix-2
+// decimation in frequency with constant twiddles).
+template <int RL>
+__device__ __forceinline__ void dft_dif(float2 *v) {
+    constexpr int R = 1 << RL;
+#pragma unroll
+    for (int st = RL - 1; st >= 0; --st) {
+        const int dt = 1 << st;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            if (t & dt) continue;
+            const float2 a = v[t], b = v[t + dt];
+            v[t] = make_float2(a.x + b.x, a.y + b.y);
+            const float2 d = make_float2(a.x - b.x, a.y - b.y);
+            const int j = t & (dt - 1);
+            if (dt == 4) v[t + dt] = j == 0 ? d : j == 1 ? mul_c<4, 1, false>(d) : j == 2 ? mul_c<4, 2, false>(d) : mul_c<4, 3, false>(d);
+            else if (dt == 2) v[t + dt] = j == 0 ? d : mul_c<2, 1, false>(d);
+            else v[t + dt] = d;
+        }
+    }
+}
+
+// Inverse of dft_dif up to the factor 2^RL: bit-reversed in, natural out
+// (radix-2 decimation in time with conjugate constant twiddles).
+template <int RL>
+__device__ __forceinline__ void idft_dit(float2 *v) {
+    constexpr int R = 1 << RL;
+#pragma unroll
+    for (int st = 0; st < RL; ++st) {
+        const int dt = 1 << st;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            if (t & dt) continue;
+            const int j = t & (dt - 1);
+            const float2 b = v[t + dt];
+            float2 x;
+            if (dt == 4) x = j == 0 ? b : j == 1 ? mul_c<4, 1, true>(b) : j == 2 ? mul_c<4, 2, true>(b) : mul_c<4, 3, true>(b);
+            else if (dt == 2) x = j == 0 ? b : mul_c<2, 1, true>(b);
+            else x = b;
+            const float2 a = v[t];
+            v[t] = make_float2(a.x + x.x, a.y + x.y);
+            v[t + dt] = make_float2(a.x - x.x, a.y - x.y);
+        }
+    }
+}
+
+// One radix-2^RL pass over RL consecutive radix-2 stages. Each thread takes
+// groups of R = 2^RL elements of one axis at positions base + o + t h
+// (h = 2^lh_lo, o < h, t < R), which are closed under the stages with
+// half-spans h .. h R/2. Forward (decimation in frequency): an R-point DFT of
+// the group, output k multiplied by w^k with w = exp(-2 pi i o / (R h)), stored
+// at slot brev(k); this equals the RL radix-2 stages and keeps the overall
+// natural -> bit-reversed order. INV is its exact inverse up to the factor R.
+// The axis has length 2^ln and element stride es; 2^llog lines of stride ls;
+// line_fast puts consecutive threads on consecutive lines.
+template <bool INV, int RL>
+__device__ __forceinline__ void fft_pass(float2 *Z, int padnp, int npair, int ln, int lh_lo, int es, int llog, int ls,
+                                         bool line_fast, const float2 *__restrict__ tw) {
+    constexpr int R = 1 << RL;
+    const int glog = ln - RL;
+    const int total = npair << (llog + glog);
+    const int hmask = (1 << lh_lo) - 1;
+    const int lmask = (1 << llog) - 1, gmask = (1 << glog) - 1;
+    const int sh = kTwLogDev - RL - lh_lo;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        int line, g;
+        if (line_fast) {
+            line = w & lmask;
+            g = (w >> llog) & gmask;
+        } else {
+            g = w & gmask;
+            line = (w >> glog) & lmask;
+        }
+        const int p = w >> (llog + glog);
+        const int o = g & hmask;
+        const int base = ((g >> lh_lo) << (lh_lo + RL)) + o;
+        float2 *Zp = Z + p * padnp;
+        const int lb = line * ls;
+        float2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = Zp[padded(lb + (base + (t << lh_lo)) * es)];
+        float2 tws[R];
+        if (lh_lo > 0) {
+            tws[1] = __ldg(tw + (o << sh));
+            if (RL >= 2) {
+                tws[2 % R] = __ldg(tw + ((2 * o) << sh));
+                tws[3 % R] = cmul(tws[1], tws[2 % R]);
             }
-            const int j = k & (half - 1);
-            const int i0 = ((k >> lh) << (lh + 1)) + j;
-            float2 *base = Z + p * NP + line * lstride;
-            float2 *a0 = base + i0 * stride;
-            float2 *a1 = a0 + half * stride;
-            const float2 w = __ldg(tw + (j << twshift));
-            const float2 u = *a0, v = *a1;
-            if (!INVERSE) {
-                *a0 = make_float2(u.x + v.x, u.y + v.y);
-                *a1 = cmul(make_float2(u.x - v.x, u.y - v.y), w);
-            } else {
-                const float2 t = cmulc(v, w);
-                *a0 = make_float2(u.x + t.x, u.y + t.y);
-                *a1 = make_float2(u.x - t.x, u.y - t.y);
+            if (RL >= 3) {
+                tws[4 % R] = __ldg(tw + ((4 * o) << sh));
+                tws[5 % R] = cmul(tws[1], tws[4 % R]);
+                tws[6 % R] = cmul(tws[2 % R], tws[4 % R]);
+                tws[7 % R] = cmul(tws[3 % R], tws[4 % R]);
             }
         }
-        __syncthreads();
+        if (!INV) {
+            dft_dif<RL>(v);
+            if (lh_lo > 0) {
+#pragma unroll
+                for (int q = 1; q < R; ++q) v[q] = cmul(v[q], tws[brev_c<RL>(q)]);
+            }
+        } else {
+            if (lh_lo > 0) {
+#pragma unroll
+                for (int q = 1; q < R; ++q) v[q] = cmulc(v[q], tws[brev_c<RL>(q)]);
+            }
+            idft_dit<RL>(v);
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) Zp[padded(lb + (base + (t << lh_lo)) * es)] = v[t];
+    }
+    __syncthreads();
+}
+
+// All stages of one axis: radix-8 passes, the remaining 1 or 2 stages in one
+// smaller pass at the small-span end.
+template <bool INV>
+__device__ __forceinline__ void fft_axis(float2 *Z, int padnp, int npair, int ln, int es, int llog, int ls,
+                                         bool line_fast, const float2 *__restrict__ tw) {
+    if (ln == 0) return;
+    const int full = ln / 3, rem = ln - 3 * full;
+    if (!INV) {
+        for (int k = 0; k < full; ++k)
+            fft_pass<false, 3>(Z, padnp, npair, ln, ln - 3 * (k + 1), es, llog, ls, line_fast, tw);
+        if (rem == 2) fft_pass<false, 2>(Z, padnp, npair, ln, 0, es, llog, ls, line_fast, tw);
+        if (rem == 1) fft_pass<false, 1>(Z, padnp, npair, ln, 0, es, llog, ls, line_fast, tw);
+    } else {
+        if (rem == 2) fft_pass<true, 2>(Z, padnp, npair, ln, 0, es, llog, ls, line_fast, tw);
+        if (rem == 1) fft_pass<true, 1>(Z, padnp, npair, ln, 0, es, llog, ls, line_fast, tw);
+        for (int k = full - 1; k >= 0; --k)
+            fft_pass<true, 3>(Z, padnp, npair, ln, ln - 3 * (k + 1), es, llog, ls, line_fast, tw);
     }
 }
 
@@ -155,8 +267,9 @@ __global__ void fft_kernel(const FftItem *__restrict__ items, const JobDev *__re
     const JobDev jb = jobs[it.job];
     const int lp1 = jb.lp1, lp2 = jb.lp2, lnp = lp1 + lp2;
     const int NP = 1 << lnp, P1 = 1 << lp1, P2 = 1 << lp2;
+    const int padnp = padded_size(NP);
     const int npair = it.npair;
-    for (int i = threadIdx.x; i < npair * NP; i += blockDim.x) Z[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < npair * padnp; i += blockDim.x) Z[i] = make_float2(0.f, 0.f);
     __syncthreads();
     const int nk = jb.ke - jb.kb;
     // scatter bin sums; depth reversed so the depth correlation becomes a convolution
@@ -167,70 +280,122 @@ __global__ void fft_kernel(const FftItem *__restrict__ items, const JobDev *__re
         const float re = kbuf[int64_t(k) * d + ch];
         const float im = (ch + 1 < d) ? kbuf[int64_t(k) * d + ch + 1] : 0.f;
         const int pos = ((P1 - key_r[k]) & (P1 - 1)) * P2 + key_x[k];
-        Z[p * NP + pos] = make_float2(re, im);
+        Z[p * padnp + padded(pos)] = make_float2(re, im);
     }
     __syncthreads();
-    fft_axis<false>(Z, npair, lnp, lp2, 1, P1, P2, false, tw);   // rows: backbone axis
-    fft_axis<false>(Z, npair, lnp, lp1, P2, P2, 1, true, tw);    // columns: depth axis
+    fft_axis<false>(Z, padnp, npair, lp2, 1, lp1, P2, false, tw);   // rows: backbone axis
+    fft_axis<false>(Z, padnp, npair, lp1, P2, lp2, 1, true, tw);    // columns: depth axis
     const float2 *S = spectra + jb.spec_off;
-    for (int i = threadIdx.x; i < npair * NP; i += blockDim.x) Z[i] = cmul(Z[i], __ldg(S + (i & (NP - 1))));
+    for (int i = threadIdx.x; i < npair * NP; i += blockDim.x) {
+        const int p = i >> lnp, e = i & (NP - 1);
+        float2 *z = Z + p * padnp + padded(e);
+        *z = cmul(*z, __ldg(S + e));
+    }
     __syncthreads();
-    fft_axis<true>(Z, npair, lnp, lp1, P2, P2, 1, true, tw);
-    fft_axis<true>(Z, npair, lnp, lp2, 1, P1, P2, false, tw);
+    fft_axis<true>(Z, padnp, npair, lp1, P2, lp2, 1, true, tw);
+    fft_axis<true>(Z, padnp, npair, lp2, 1, lp1, P2, false, tw);
     for (int t = threadIdx.x; t < nk * npair; t += blockDim.x) {
         const int kk = t / npair, p = t - kk * npair;
         const int k = jb.kb + kk;
         const int ch = 2 * (it.pair0 + p);
-        const float2 v = Z[p * NP + key_r[k] * P2 + key_x[k]];
+        const float2 v = Z[p * padnp + padded(key_r[k] * P2 + key_x[k])];
         vbuf[int64_t(k) * d + ch] = v.x;
         if (ch + 1 < d) vbuf[int64_t(k) * d + ch + 1] = v.y;
     }
 }
 
 // ---------------------------------------------------------------------------
-// direct job kernel: one warp per (job, 32 query bins), CH channels per pass
+// direct job kernel: one warp per (job, 64 query bins), two queries per lane,
+// CH channels per pass; source bins staged through shared memory in chunks of
+// 32 with a padded row stride so the row stores are conflict-free
 // ---------------------------------------------------------------------------
-template <int CH, int WARPS>
+template <int CH>
+struct SvStride {
+    static constexpr int v = CH >= 8 ? CH + 4 : CH;
+};
+
+template <int CH, int WARPS, bool VEC>
 __global__ void direct_kernel(const DirItem *__restrict__ items, int n_items, const JobDev *__restrict__ jobs,
                               const int32_t *__restrict__ key_r, const int32_t *__restrict__ key_x, int d,
                               const float *__restrict__ kbuf, float *__restrict__ vbuf, const float *__restrict__ ftab) {
+    constexpr int SV = SvStride<CH>::v;
     __shared__ int sr[WARPS][32];
     __shared__ int sx[WARPS][32];
-    __shared__ float sv[WARPS][32][CH];
+    __shared__ __align__(16) float sv[WARPS][32 * SV];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = blockIdx.x * WARPS + warp;
     if (w >= n_items) return;
     const int c0 = blockIdx.y * CH;
     const DirItem it = items[w];
     const JobDev jb = jobs[it.job];
-    const int i = it.q0 + lane;
-    const bool valid = i < jb.ke;
-    const int ri = valid ? key_r[i] : 0;
-    const int xi = valid ? key_x[i] : 0;
-    float acc[CH];
+    const int i0 = it.q0 + lane, i1 = i0 + 32;
+    const bool v0 = i0 < jb.ke, v1 = i1 < jb.ke;
+    const int r0 = v0 ? key_r[i0] : 0, x0 = v0 ? key_x[i0] : 0;
+    const int r1 = v1 ? key_r[i1] : 0, x1 = v1 ? key_x[i1] : 0;
+    float a0[CH], a1[CH];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) acc[c] = 0.f;
+    for (int c = 0; c < CH; ++c) a0[c] = a1[c] = 0.f;
+    float *my = sv[warp];
     for (int s0 = jb.kb; s0 < jb.ke; s0 += 32) {
         const int j = s0 + lane;
         if (j < jb.ke) {
             sr[warp][lane] = key_r[j];
             sx[warp][lane] = key_x[j];
+            const float *src = kbuf + int64_t(j) * d + c0;
+            if (VEC) {
 #pragma unroll
-            for (int c = 0; c < CH; ++c) sv[warp][lane][c] = (c0 + c < d) ? kbuf[int64_t(j) * d + c0 + c] : 0.f;
+                for (int c = 0; c < CH; c += 4)
+                    *reinterpret_cast<float4 *>(my + lane * SV + c) = *reinterpret_cast<const float4 *>(src + c);
+            } else {
+#pragma unroll
+                for (int c = 0; c < CH; ++c) my[lane * SV + c] = (c0 + c < d) ? src[c] : 0.f;
+            }
         }
         __syncwarp();
         const int cnt = min(32, jb.ke - s0);
         for (int t = 0; t < cnt; ++t) {
-            const float f = __ldg(ftab + ri + sr[warp][t] + abs(xi - sx[warp][t]));
+            const int rt = sr[warp][t], xt = sx[warp][t];
+            const float f0 = __ldg(ftab + r0 + rt + abs(x0 - xt));
+            const float f1 = __ldg(ftab + r1 + rt + abs(x1 - xt));
+            if (VEC) {
 #pragma unroll
-            for (int c = 0; c < CH; ++c) acc[c] = fmaf(f, sv[warp][t][c], acc[c]);
+                for (int c = 0; c < CH; c += 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(my + t * SV + c);
+                    a0[c] = fmaf(f0, q.x, a0[c]); a0[c + 1] = fmaf(f0, q.y, a0[c + 1]);
+                    a0[c + 2] = fmaf(f0, q.z, a0[c + 2]); a0[c + 3] = fmaf(f0, q.w, a0[c + 3]);
+                    a1[c] = fmaf(f1, q.x, a1[c]); a1[c + 1] = fmaf(f1, q.y, a1[c + 1]);
+                    a1[c + 2] = fmaf(f1, q.z, a1[c + 2]); a1[c + 3] = fmaf(f1, q.w, a1[c + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const float q = my[t * SV + c];
+                    a0[c] = fmaf(f0, q, a0[c]);
+                    a1[c] = fmaf(f1, q, a1[c]);
+                }
+            }
         }
         __syncwarp();
     }
-    if (valid) {
+    if (VEC) {
+        if (v0) {
 #pragma unroll
-        for (int c = 0; c < CH; ++c)
-            if (c0 + c < d) vbuf[int64_t(i) * d + c0 + c] = acc[c];
+            for (int c = 0; c < CH; c += 4)
+                *reinterpret_cast<float4 *>(vbuf + int64_t(i0) * d + c0 + c) = make_float4(a0[c], a0[c + 1], a0[c + 2], a0[c + 3]);
+        }
+        if (v1) {
+#pragma unroll
+            for (int c = 0; c < CH; c += 4)
+                *reinterpret_cast<float4 *>(vbuf + int64_t(i1) * d + c0 + c) = make_float4(a1[c], a1[c + 1], a1[c + 2], a1[c + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            if (c0 + c < d) {
+                if (v0) vbuf[int64_t(i0) * d + c0 + c] = a0[c];
+                if (v1) vbuf[int64_t(i1) * d + c0 + c] = a1[c];
+            }
+        }
     }
 }
 

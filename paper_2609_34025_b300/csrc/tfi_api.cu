@@ -144,7 +144,7 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
             for (int p0 = 0; p0 < pairs; p0 += np)
                 by_class[lnp].push_back(tfi::dev::FftItem{int32_t(j), p0, std::min(np, pairs - p0)});
         } else {
-            for (int64_t q = jb.kb; q < jb.ke; q += 32) dir.push_back(tfi::dev::DirItem{int32_t(j), int32_t(q)});
+            for (int64_t q = jb.kb; q < jb.ke; q += 64) dir.push_back(tfi::dev::DirItem{int32_t(j), int32_t(q)});
         }
     }
     std::vector<tfi::dev::FftItem> all;
@@ -190,15 +190,19 @@ void launch_direct(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
     if (wl.n_dir == 0) return;
     constexpr int WARPS = 4;
     dim3 grid((wl.n_dir + WARPS - 1) / WARPS, (d + CH - 1) / CH);
-    tfi::dev::direct_kernel<CH, WARPS><<<grid, 32 * WARPS, 0, s>>>(wl.d_dir, wl.n_dir, p->jobs, p->key_r, p->key_x,
-                                                                   d, p->kbuf, p->vbuf, p->ftab);
+    if (CH % 4 == 0 && d % CH == 0)
+        tfi::dev::direct_kernel<CH, WARPS, (CH % 4 == 0)><<<grid, 32 * WARPS, 0, s>>>(
+            wl.d_dir, wl.n_dir, p->jobs, p->key_r, p->key_x, d, p->kbuf, p->vbuf, p->ftab);
+    else
+        tfi::dev::direct_kernel<CH, WARPS, false><<<grid, 32 * WARPS, 0, s>>>(wl.d_dir, wl.n_dir, p->jobs, p->key_r,
+                                                                              p->key_x, d, p->kbuf, p->vbuf, p->ftab);
 }
 
 bool g_attr_done = false;
 
 tfi_status set_attributes() {
     if (g_attr_done) return TFI_OK;
-    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 129 * 1024));
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
 #define LEAF_ATTR(T, CH)                                                                                      \
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::leaf_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   200 * 1024));
@@ -255,7 +259,8 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
         // (a4, a5) tables by FFT, one launch per size class, then the direct jobs
         StageMark m_fft(p, s, TFI_STAGE_FFT);
         for (size_t c = 0; c < wl->fft_lnp.size(); ++c) {
-            const size_t smem = size_t(wl->fft_npair[c]) * (size_t(1) << wl->fft_lnp[c]) * sizeof(float2);
+            const size_t smem = size_t(wl->fft_npair[c]) * size_t(tfi::dev::padded_size(1 << wl->fft_lnp[c])) *
+                                sizeof(float2);
             tfi::dev::fft_kernel<<<wl->fft_count[c], kFftThreads, smem, s>>>(
                 wl->d_fft + wl->fft_off[c], p->jobs, p->key_r, p->key_x, d, p->kbuf, p->vbuf, p->spectra, p->twiddle);
         }
@@ -386,7 +391,7 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
             for (int p0 = 0; p0 < pairs; p0 += np)
                 by_class[lnp].push_back(tfi::dev::FftItem{int32_t(j), p0, std::min(np, pairs - p0)});
         } else {
-            for (int64_t q = jb.kb; q < jb.ke; q += 32) dir.push_back(tfi::dev::DirItem{int32_t(j), int32_t(q)});
+            for (int64_t q = jb.kb; q < jb.ke; q += 64) dir.push_back(tfi::dev::DirItem{int32_t(j), int32_t(q)});
         }
     }
     std::vector<tfi::dev::FftItem> fft_all;
@@ -438,7 +443,8 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
         tfi::dev::bucket_kernel<T, 1><<<grid_for(int64_t(K) * d, 256), 256, 0, s>>>(int64_t(K), p->key_ptr, p->key_vtx,
                                                                                    F, d, kbuf);
         for (size_t c = 0; c < cls_lnp.size(); ++c) {
-            const size_t smem = size_t(cls_npair[c]) * (size_t(1) << cls_lnp[c]) * sizeof(float2);
+            const size_t smem =
+                size_t(cls_npair[c]) * size_t(tfi::dev::padded_size(1 << cls_lnp[c])) * sizeof(float2);
             tfi::dev::fft_kernel<<<cls_count[c], kFftThreads, smem, s>>>(d_fft + cls_off[c], p->jobs, p->key_r,
                                                                         p->key_x, d, kbuf, vbuf, p->spectra,
                                                                         p->twiddle);
@@ -446,8 +452,9 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
         if (!dir.empty()) {
             constexpr int WARPS = 4;
             dim3 grid((unsigned(dir.size()) + WARPS - 1) / WARPS, (d + 15) / 16);
-            tfi::dev::direct_kernel<16, WARPS><<<grid, 32 * WARPS, 0, s>>>(d_dir, int(dir.size()), p->jobs, p->key_r,
-                                                                           p->key_x, d, kbuf, vbuf, p->ftab);
+            tfi::dev::direct_kernel<16, WARPS, false><<<grid, 32 * WARPS, 0, s>>>(d_dir, int(dir.size()), p->jobs,
+                                                                                  p->key_r, p->key_x, d, kbuf, vbuf,
+                                                                                  p->ftab);
         }
     }
     tfi::dev::gather_kernel<T, 1><<<grid_for(int64_t(n) * d, 256), 256, 0, s>>>(
