@@ -356,7 +356,7 @@ def main():
     ap.add_argument("--d", type=int, default=16)
     ap.add_argument("--kernel", default="exp", choices=["exp", "cauchy", "gauss"])
     ap.add_argument("--policy", default="adaptive")
-    ap.add_argument("--leaf-max", dest="leaf_max", type=int, default=64)
+    ap.add_argument("--leaf-max", dest="leaf_max", type=int, default=512)
     ap.add_argument("--cpu-budget", dest="cpu_budget", type=float, default=15.0)
     a = ap.parse_args()
     if a.warmup < 3:

@@ -187,7 +187,6 @@ __device__ __forceinline__ void fft_pass(float2 *Z, int padnp, int npair, int ln
     const int total = npair << (llog + glog);
     const int hmask = (1 << lh_lo) - 1;
     const int lmask = (1 << llog) - 1, gmask = (1 << glog) - 1;
-    const int sh = kTwLogDev - RL - lh_lo;
     for (int w = threadIdx.x; w < total; w += blockDim.x) {
         int line, g;
         if (line_fast) {
@@ -205,18 +204,26 @@ __device__ __forceinline__ void fft_pass(float2 *Z, int padnp, int npair, int ln
         float2 v[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) v[t] = Zp[padded(lb + (base + (t << lh_lo)) * es)];
+        // w^k with w = exp(-2 pi i o / (R h)), from the per-level entry
+        // exp(-2 pi i o / (8 h)) by squaring
         float2 tws[R];
         if (lh_lo > 0) {
-            tws[1] = __ldg(tw + (o << sh));
-            if (RL >= 2) {
-                tws[2 % R] = __ldg(tw + ((2 * o) << sh));
+            const float2 w8 = __ldg(tw + (1 << lh_lo) + o);
+            if (RL == 3) {
+                tws[1] = w8;
+                tws[2 % R] = cmul(w8, w8);
                 tws[3 % R] = cmul(tws[1], tws[2 % R]);
-            }
-            if (RL >= 3) {
-                tws[4 % R] = __ldg(tw + ((4 * o) << sh));
+                tws[4 % R] = cmul(tws[2 % R], tws[2 % R]);
                 tws[5 % R] = cmul(tws[1], tws[4 % R]);
                 tws[6 % R] = cmul(tws[2 % R], tws[4 % R]);
                 tws[7 % R] = cmul(tws[3 % R], tws[4 % R]);
+            } else if (RL == 2) {
+                tws[1] = cmul(w8, w8);
+                tws[2 % R] = cmul(tws[1], tws[1]);
+                tws[3 % R] = cmul(tws[1], tws[2 % R]);
+            } else {
+                const float2 w4 = cmul(w8, w8);
+                tws[1] = cmul(w4, w4);
             }
         }
         if (!INV) {
@@ -238,24 +245,82 @@ __device__ __forceinline__ void fft_pass(float2 *Z, int padnp, int npair, int ln
     __syncthreads();
 }
 
-// All stages of one axis: radix-8 passes, the remaining 1 or 2 stages in one
-// smaller pass at the small-span end.
+// All passes of one axis. Forward order runs from the largest span down: the
+// 1- or 2-stage remainder pass first, then radix-8 passes ending at span 1;
+// the inverse runs the mirror image. With skip_bottom the span-1 pass is left
+// out (fused_bottom does it together with the spectrum product).
 template <bool INV>
 __device__ __forceinline__ void fft_axis(float2 *Z, int padnp, int npair, int ln, int es, int llog, int ls,
-                                         bool line_fast, const float2 *__restrict__ tw) {
+                                         bool line_fast, const float2 *__restrict__ tw, bool skip_bottom) {
     if (ln == 0) return;
     const int full = ln / 3, rem = ln - 3 * full;
+    const bool do_rem = rem && !(skip_bottom && full == 0);
     if (!INV) {
-        for (int k = 0; k < full; ++k)
-            fft_pass<false, 3>(Z, padnp, npair, ln, ln - 3 * (k + 1), es, llog, ls, line_fast, tw);
-        if (rem == 2) fft_pass<false, 2>(Z, padnp, npair, ln, 0, es, llog, ls, line_fast, tw);
-        if (rem == 1) fft_pass<false, 1>(Z, padnp, npair, ln, 0, es, llog, ls, line_fast, tw);
+        if (do_rem) {
+            if (rem == 2) fft_pass<false, 2>(Z, padnp, npair, ln, ln - 2, es, llog, ls, line_fast, tw);
+            else fft_pass<false, 1>(Z, padnp, npair, ln, ln - 1, es, llog, ls, line_fast, tw);
+        }
+        for (int k = 0; k < full; ++k) {
+            const int lh = ln - rem - 3 * (k + 1);
+            if (skip_bottom && lh == 0) break;
+            fft_pass<false, 3>(Z, padnp, npair, ln, lh, es, llog, ls, line_fast, tw);
+        }
     } else {
-        if (rem == 2) fft_pass<true, 2>(Z, padnp, npair, ln, 0, es, llog, ls, line_fast, tw);
-        if (rem == 1) fft_pass<true, 1>(Z, padnp, npair, ln, 0, es, llog, ls, line_fast, tw);
-        for (int k = full - 1; k >= 0; --k)
-            fft_pass<true, 3>(Z, padnp, npair, ln, ln - 3 * (k + 1), es, llog, ls, line_fast, tw);
+        for (int k = full - 1; k >= 0; --k) {
+            const int lh = ln - rem - 3 * (k + 1);
+            if (skip_bottom && lh == 0) continue;
+            fft_pass<true, 3>(Z, padnp, npair, ln, lh, es, llog, ls, line_fast, tw);
+        }
+        if (do_rem) {
+            if (rem == 2) fft_pass<true, 2>(Z, padnp, npair, ln, ln - 2, es, llog, ls, line_fast, tw);
+            else fft_pass<true, 1>(Z, padnp, npair, ln, ln - 1, es, llog, ls, line_fast, tw);
+        }
     }
+}
+
+// The span-1 pass of the innermost axis, forward and inverse, with the product
+// by the kernel spectrum in between, all in registers (no twiddles at span 1).
+template <int RL>
+__device__ __forceinline__ void fused_bottom_pass(float2 *Z, int padnp, int npair, int ln, int es, int llog, int ls,
+                                                  bool line_fast, const float2 *__restrict__ S) {
+    constexpr int R = 1 << RL;
+    const int glog = ln - RL;
+    const int total = npair << (llog + glog);
+    const int lmask = (1 << llog) - 1, gmask = (1 << glog) - 1;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        int line, g;
+        if (line_fast) {
+            line = w & lmask;
+            g = (w >> llog) & gmask;
+        } else {
+            g = w & gmask;
+            line = (w >> glog) & lmask;
+        }
+        const int p = w >> (llog + glog);
+        float2 *Zp = Z + p * padnp;
+        const int e0 = line * ls + (g << RL) * es;
+        float2 sp[R], v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) sp[q] = __ldg(S + e0 + q * es);
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = Zp[padded(e0 + t * es)];
+        dft_dif<RL>(v);
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = cmul(v[q], sp[q]);
+        idft_dit<RL>(v);
+#pragma unroll
+        for (int t = 0; t < R; ++t) Zp[padded(e0 + t * es)] = v[t];
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void fused_bottom(float2 *Z, int padnp, int npair, int ln, int es, int llog, int ls,
+                                             bool line_fast, const float2 *__restrict__ S) {
+    const int full = ln / 3, rem = ln - 3 * full;
+    const int rl = full > 0 ? 3 : rem;
+    if (rl == 3) fused_bottom_pass<3>(Z, padnp, npair, ln, es, llog, ls, line_fast, S);
+    else if (rl == 2) fused_bottom_pass<2>(Z, padnp, npair, ln, es, llog, ls, line_fast, S);
+    else fused_bottom_pass<1>(Z, padnp, npair, ln, es, llog, ls, line_fast, S);
 }
 
 __global__ void fft_kernel(const FftItem *__restrict__ items, const JobDev *__restrict__ jobs,
@@ -283,17 +348,22 @@ __global__ void fft_kernel(const FftItem *__restrict__ items, const JobDev *__re
         Z[p * padnp + padded(pos)] = make_float2(re, im);
     }
     __syncthreads();
-    fft_axis<false>(Z, padnp, npair, lp2, 1, lp1, P2, false, tw);   // rows: backbone axis
-    fft_axis<false>(Z, padnp, npair, lp1, P2, lp2, 1, true, tw);    // columns: depth axis
     const float2 *S = spectra + jb.spec_off;
-    for (int i = threadIdx.x; i < npair * NP; i += blockDim.x) {
-        const int p = i >> lnp, e = i & (NP - 1);
-        float2 *z = Z + p * padnp + padded(e);
-        *z = cmul(*z, __ldg(S + e));
+    if (lp1 > 0) {
+        // rows (backbone axis) are the outer axis, columns (depth axis) the inner one
+        fft_axis<false>(Z, padnp, npair, lp2, 1, lp1, P2, false, tw, false);
+        fft_axis<false>(Z, padnp, npair, lp1, P2, lp2, 1, true, tw, true);
+        fused_bottom(Z, padnp, npair, lp1, P2, lp2, 1, true, S);
+        fft_axis<true>(Z, padnp, npair, lp1, P2, lp2, 1, true, tw, true);
+        fft_axis<true>(Z, padnp, npair, lp2, 1, lp1, P2, false, tw, false);
+    } else if (lp2 > 0) {
+        fft_axis<false>(Z, padnp, npair, lp2, 1, 0, P2, false, tw, true);
+        fused_bottom(Z, padnp, npair, lp2, 1, 0, P2, false, S);
+        fft_axis<true>(Z, padnp, npair, lp2, 1, 0, P2, false, tw, true);
+    } else {
+        for (int p = threadIdx.x; p < npair; p += blockDim.x) Z[p * padnp] = cmul(Z[p * padnp], __ldg(S));
+        __syncthreads();
     }
-    __syncthreads();
-    fft_axis<true>(Z, padnp, npair, lp1, P2, lp2, 1, true, tw);
-    fft_axis<true>(Z, padnp, npair, lp2, 1, lp1, P2, false, tw);
     for (int t = threadIdx.x; t < nk * npair; t += blockDim.x) {
         const int kk = t / npair, p = t - kk * npair;
         const int k = jb.kb + kk;
@@ -437,6 +507,13 @@ __global__ void gather_kernel(int n, const int32_t *__restrict__ vrec_ptr, const
 // dense leaves: one CTA per leaf group, CH channels per pass
 // dhat(i, j) = D(i) + D(j) - 2 min_{w in (i, j]} D(parent(w)) in preorder
 // ---------------------------------------------------------------------------
+// Shared-memory layout of leaf_kernel, in 4-byte words: distances, sparse
+// table (levels x max_gs), then the field rows at a 16-byte aligned offset.
+__host__ __device__ inline int leaf_sx_offset(int max_gs, int levels) { return ((max_gs * (1 + levels)) + 3) & ~3; }
+__host__ __device__ inline size_t leaf_smem_bytes(int max_gs, int levels, int ch) {
+    return size_t(leaf_sx_offset(max_gs, levels)) * 4 + size_t(max_gs) * ch * 4;
+}
+
 template <typename T, int CH>
 __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__restrict__ leaf_vtx,
                             const int32_t *__restrict__ leaf_dist, const int32_t *__restrict__ leaf_pdist,
@@ -450,7 +527,8 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
     while ((2 << (levels - 1)) <= max_gs) ++levels;
     int *sdist = smem_i;
     int *st = sdist + max_gs;                                   // levels x max_gs
-    float *sx = reinterpret_cast<float *>(st + levels * max_gs);  // max_gs x CH
+    // max_gs x CH field rows, 16-byte aligned for vector loads
+    float *sx = reinterpret_cast<float *>(smem_i + leaf_sx_offset(max_gs, levels));
     for (int i = threadIdx.x; i < gs; i += blockDim.x) {
         sdist[i] = leaf_dist[gb + i];
         st[i] = leaf_pdist[gb + i];
@@ -480,8 +558,19 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
                 dist = di + sdist[j] - 2 * m;
             }
             const float f = __ldg(ftab + dist);
+            if (CH % 4 == 0) {
 #pragma unroll
-            for (int c = 0; c < CH; ++c) acc[c] = fmaf(f, sx[j * CH + c], acc[c]);
+                for (int c = 0; c < CH; c += 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(sx + j * CH + c);
+                    acc[c] = fmaf(f, q.x, acc[c]);
+                    acc[c + 1] = fmaf(f, q.y, acc[c + 1]);
+                    acc[c + 2] = fmaf(f, q.z, acc[c + 2]);
+                    acc[c + 3] = fmaf(f, q.w, acc[c + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < CH; ++c) acc[c] = fmaf(f, sx[j * CH + c], acc[c]);
+            }
         }
         const int64_t v = leaf_vtx[gb + i];
 #pragma unroll

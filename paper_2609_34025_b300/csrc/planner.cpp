@@ -542,12 +542,15 @@ int flatten(HostPlan &hp, std::string &err) {
             }
         }
     }
-    const int64_t tw = int64_t(1) << (kTwLog - 1);
-    hp.twiddle.resize(size_t(2 * tw));
-    for (int64_t k = 0; k < tw; ++k) {
-        const double ang = -2.0 * M_PI * double(k) / double(int64_t(1) << kTwLog);
-        hp.twiddle[size_t(2 * k)] = float(std::cos(ang));
-        hp.twiddle[size_t(2 * k + 1)] = float(std::sin(ang));
+    // compact per-level twiddles: twiddle[h + o] = exp(-2 pi i o / (8 h)) for h = 2^L, o < h
+    const int64_t tw = int64_t(1) << kTwLog;
+    hp.twiddle.assign(size_t(2 * tw), 0.f);
+    for (int64_t h = 1; h < tw; h <<= 1) {
+        for (int64_t o = 0; o < h; ++o) {
+            const double ang = -2.0 * M_PI * double(o) / double(8 * h);
+            hp.twiddle[size_t(2 * (h + o))] = float(std::cos(ang));
+            hp.twiddle[size_t(2 * (h + o) + 1)] = float(std::sin(ang));
+        }
     }
     return TFI_OK;
 }

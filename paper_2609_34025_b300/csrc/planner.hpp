@@ -92,7 +92,7 @@ struct HostPlan {
     // FFT spectra per (lp1, lp2) class, bit-reversed order, scaled by 1/(P1 P2), interleaved re/im
     std::vector<int32_t> spec_class_off;                   // [lp1 * 16 + lp2] -> offset in floats (complex = 2)
     std::vector<float> spectra;
-    std::vector<float> twiddle;                            // exp(-2 pi i k / 2^TW_LOG), k < 2^(TW_LOG-1)
+    std::vector<float> twiddle;                            // [h + o] = exp(-2 pi i o / (8 h)), h = 2^L < 2^kTwLog
     double plan_seconds = 0;
 };
 

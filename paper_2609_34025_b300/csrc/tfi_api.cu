@@ -63,6 +63,10 @@ struct tfi_plan_s {
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
     void *stage_in = nullptr, *stage_out = nullptr;
     std::map<int, WorkLists> work;  // per channel count d
+    // fork/join inside an apply: leaf terms and direct jobs run on their own
+    // streams, concurrently with the bin sums and FFT jobs
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_leaf = nullptr, ev_bucket = nullptr, ev_dir = nullptr;
     // stage profiling (CUDA events on the apply stream)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -105,6 +109,10 @@ struct tfi_plan_s {
         return TFI_OK;
     }
     ~tfi_plan_s() {
+        for (cudaEvent_t e : {ev_fork, ev_leaf, ev_bucket, ev_dir})
+            if (e) cudaEventDestroy(e);
+        for (cudaStream_t st : aux)
+            if (st) cudaStreamDestroy(st);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         for (auto &kv : work) {
             cudaFree(kv.second.d_fft);
@@ -179,7 +187,7 @@ void launch_leaf(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
     if (p->n_groups == 0) return;
     int levels = 1;
     while ((2 << (levels - 1)) <= p->max_gs) ++levels;
-    const size_t smem = size_t(p->max_gs) * (1 + levels) * 4 + size_t(p->max_gs) * CH * 4;
+    const size_t smem = tfi::dev::leaf_smem_bytes(p->max_gs, levels, CH);
     dim3 grid(p->n_groups, (d + CH - 1) / CH);
     tfi::dev::leaf_kernel<T, CH><<<grid, 256, smem, s>>>(p->lgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist,
                                                          p->leaf_lo, p->leaf_hi, F, d, p->ftab, p->lbuf, p->max_gs);
@@ -237,14 +245,19 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     if (tfi_status rc = build_work(p, d, &wl)) return rc;
     if (tfi_status rc = set_attributes()) return rc;
     const int n = p->hp.n;
-    // (a7) dense leaves -> lbuf
-    StageMark m_leaf(p, s, TFI_STAGE_LEAF);
-    if (d >= 16) launch_leaf<16>(p, F, d, s);
-    else if (d > 4) launch_leaf<8>(p, F, d, s);
-    else if (d > 2) launch_leaf<4>(p, F, d, s);
-    else if (d == 2) launch_leaf<2>(p, F, d, s);
-    else launch_leaf<1>(p, F, d, s);
+    cudaStream_t s_leaf = p->aux[0], s_dir = p->aux[1];
+    // fork: everything on the side streams starts after the work already queued on s
+    TFI_CUDA(cudaEventRecord(p->ev_fork, s));
+    TFI_CUDA(cudaStreamWaitEvent(s_leaf, p->ev_fork, 0));
+    // (a7) dense leaves -> lbuf, on the leaf stream
+    StageMark m_leaf(p, s_leaf, TFI_STAGE_LEAF);
+    if (d >= 16) launch_leaf<16>(p, F, d, s_leaf);
+    else if (d > 4) launch_leaf<8>(p, F, d, s_leaf);
+    else if (d > 2) launch_leaf<4>(p, F, d, s_leaf);
+    else if (d == 2) launch_leaf<2>(p, F, d, s_leaf);
+    else launch_leaf<1>(p, F, d, s_leaf);
     m_leaf.done(p->n_groups > 0 ? 1 : 0);
+    TFI_CUDA(cudaEventRecord(p->ev_leaf, s_leaf));
     // (a3) bin sums
     const int64_t n_keys = int64_t(p->hp.key_r.size());
     if (n_keys > 0) {
@@ -256,7 +269,17 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
             tfi::dev::bucket_kernel<T, 1><<<grid_for(n_keys * d, 256), 256, 0, s>>>(n_keys, p->key_ptr, p->key_vtx,
                                                                                     F, d, p->kbuf);
         m_bucket.done(1);
-        // (a4, a5) tables by FFT, one launch per size class, then the direct jobs
+        TFI_CUDA(cudaEventRecord(p->ev_bucket, s));
+        TFI_CUDA(cudaStreamWaitEvent(s_dir, p->ev_bucket, 0));
+        // (a4, a5) tables: direct jobs on their stream, FFT jobs (one launch per size class) on s
+        StageMark m_dir(p, s_dir, TFI_STAGE_DIRECT);
+        if (d >= 16) launch_direct<16>(p, *wl, d, s_dir);
+        else if (d > 4) launch_direct<8>(p, *wl, d, s_dir);
+        else if (d > 2) launch_direct<4>(p, *wl, d, s_dir);
+        else if (d == 2) launch_direct<2>(p, *wl, d, s_dir);
+        else launch_direct<1>(p, *wl, d, s_dir);
+        m_dir.done(wl->n_dir > 0 ? 1 : 0);
+        TFI_CUDA(cudaEventRecord(p->ev_dir, s_dir));
         StageMark m_fft(p, s, TFI_STAGE_FFT);
         for (size_t c = 0; c < wl->fft_lnp.size(); ++c) {
             const size_t smem = size_t(wl->fft_npair[c]) * size_t(tfi::dev::padded_size(1 << wl->fft_lnp[c])) *
@@ -265,15 +288,10 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
                 wl->d_fft + wl->fft_off[c], p->jobs, p->key_r, p->key_x, d, p->kbuf, p->vbuf, p->spectra, p->twiddle);
         }
         m_fft.done(int(wl->fft_lnp.size()));
-        StageMark m_dir(p, s, TFI_STAGE_DIRECT);
-        if (d >= 16) launch_direct<16>(p, *wl, d, s);
-        else if (d > 4) launch_direct<8>(p, *wl, d, s);
-        else if (d > 2) launch_direct<4>(p, *wl, d, s);
-        else if (d == 2) launch_direct<2>(p, *wl, d, s);
-        else launch_direct<1>(p, *wl, d, s);
-        m_dir.done(wl->n_dir > 0 ? 1 : 0);
+        TFI_CUDA(cudaStreamWaitEvent(s, p->ev_dir, 0));
     }
-    // (a6) gather
+    // join, then (a6) gather
+    TFI_CUDA(cudaStreamWaitEvent(s, p->ev_leaf, 0));
     StageMark m_gather(p, s, TFI_STAGE_GATHER);
     if (d % 4 == 0)
         tfi::dev::gather_kernel<T, 4><<<grid_for(int64_t(n) * (d / 4), 256), 256, 0, s>>>(
@@ -328,6 +346,9 @@ tfi_status upload_plan(tfi_plan_t p) {
     if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->kbuf), K * dm * sizeof(float))) return rc;
     if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->vbuf), K * dm * sizeof(float))) return rc;
     if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->lbuf), size_t(hp.n) * dm * sizeof(float))) return rc;
+    for (cudaStream_t &st : p->aux) TFI_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&p->ev_fork, &p->ev_leaf, &p->ev_bucket, &p->ev_dir})
+        TFI_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     p->on_device = true;
     return TFI_OK;
 }
@@ -434,7 +455,7 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
         int levels = 1;
         while ((2 << (levels - 1)) <= p->max_gs) ++levels;
         const int CH = 16;
-        const size_t smem = size_t(p->max_gs) * (1 + levels) * 4 + size_t(p->max_gs) * CH * 4;
+        const size_t smem = tfi::dev::leaf_smem_bytes(p->max_gs, levels, CH);
         dim3 grid(p->n_groups, (d + CH - 1) / CH);
         tfi::dev::leaf_kernel<T, 16><<<grid, 256, smem, s>>>(p->lgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist,
                                                              p->leaf_lo, p->leaf_hi, F, d, p->ftab, lbuf, p->max_gs);
