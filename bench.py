@@ -330,7 +330,7 @@ def run_ours(a):
         "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": config_block(a, {"parallelism": f"channel blocks, {world} rank(s), no collective on the data path",
-                                   "plan_seconds": round(plan_s, 3), "plan_calls": info["n_calls"],
+                                   "plan_seconds": round(plan_s, 3), "device_keys_ms": round(info["device_keys_ms"], 3), "plan_calls": info["n_calls"],
                                    "plan_leaves": info["n_leaves"], "plan_levels": info["n_levels"]}),
         "fwd_value": world * n * d / (fwd_ms / 1e3), "fwd_ms": fwd_ms,
         "roofline": roof, "cpu_baseline": cpu,

@@ -172,6 +172,7 @@ typedef struct {
     int64_t ftab_len;       /* grid samples of f held on the device */
     int64_t device_bytes;   /* device memory owned by the plan (without per-d work lists) */
     double plan_seconds;    /* host wall time of tfi_plan */
+    double device_keys_ms;  /* device time of the plan-time distance / bin-key pass (0 host-only) */
 } tfi_plan_info;
 tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
 
@@ -182,11 +183,19 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
  *   TFI_EXPORT_RECORDS  5 per (call, vertex): call index, vertex, depth d(u) (grid),
  *                       coordinate X(pi(u)) (grid), component id = min vertex of the component (-1 on P)
  *   TFI_EXPORT_LEAVES   3 per leaf call: level, min vertex, |V(S)|
+ *   TFI_EXPORT_DEVICE_KEYS 4 per (call, vertex), in RECORDS order: call index, vertex, and the
+ *                       depth d(u) and coordinate X(pi(u)) as computed on the device at plan time
+ *                       from root distances (pointer doubling over the rooted forest) and
+ *                       lowest common ancestors: d(u) = D(u) + D(pi u) - 2 D(lca(u, pi u)),
+ *                       X = D(p_1) + D(pi u) - 2 D(lca(p_1, pi u)) (Eq. "stad-depth",
+ *                       Eq. "projection"); they must equal the host planner's bit for bit.
+ *                       Needs a device plan.
  * If dst is NULL (or cap too small) only *len (number of int64 values) is set. */
 #define TFI_EXPORT_CALLS    0
 #define TFI_EXPORT_BACKBONE 1
 #define TFI_EXPORT_RECORDS  2
 #define TFI_EXPORT_LEAVES   3
+#define TFI_EXPORT_DEVICE_KEYS 4
 tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t cap, int64_t *len);
 
 /* Stages of an apply, in launch order, for profiling and the roofline model:

@@ -25,7 +25,7 @@ _STATUS = {0: "OK", 1: "ARG", 2: "NOT_TREE", 3: "WEIGHT", 4: "GRID_OVERFLOW", 5:
 KERNEL_KINDS = {"table": 0, "expsum": 1, "gauss": 2, "rational": 3}
 POLICIES = {"adaptive": 0, "diameter": 1, "centroid": 2}
 DTYPE_F32, DTYPE_BF16 = 0, 1
-EXPORTS = {"calls": (0, 7), "backbone": (1, 1), "records": (2, 5), "leaves": (3, 3)}
+EXPORTS = {"calls": (0, 7), "backbone": (1, 1), "records": (2, 5), "leaves": (3, 3), "device_keys": (4, 4)}
 
 
 class TfiError(RuntimeError):
@@ -54,7 +54,7 @@ class _Info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "n", "n_calls", "n_leaves", "n_levels", "n_records", "n_keys", "n_jobs_fft", "n_jobs_direct",
         "n_centroid", "sum_table", "sum_fft_points", "sum_leaf_pairs", "ftab_len", "device_bytes")] + [
-        ("plan_seconds", ctypes.c_double)]
+        ("plan_seconds", ctypes.c_double), ("device_keys_ms", ctypes.c_double)]
 
 
 EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_host", "tfi_destroy",

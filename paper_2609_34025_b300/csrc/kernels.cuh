@@ -579,5 +579,68 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
     }
 }
 
+// ---------------------------------------------------------------------------
+// (a2) distances and bin keys on the device, at plan time.
+// Root grid distances D and hop depths by pointer doubling over the rooted
+// parent array (a prefix sum along every root path: D_{k+1}[v] = D_k[v] +
+// D_k[J_k[v]], J_{k+1} = J_k o J_k, with D = 0 and J = itself at a root); the
+// jump tables J_k double as binary-lifting ancestor tables for the LCA. Then per
+// record (v in call S, anchor a = pi(v), backbone start p_1):
+//   d(v)     = D(v)   + D(a) - 2 D(lca(v, a))      (Eq. "stad-depth")
+//   X(pi v)  = D(p_1) + D(a) - 2 D(lca(p_1, a))    (backbone coordinate)
+// ---------------------------------------------------------------------------
+__global__ void k1_init(int n, const int32_t *__restrict__ parent, const int32_t *__restrict__ qpar,
+                        int64_t *__restrict__ D, int32_t *__restrict__ hop, int32_t *__restrict__ anc0) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int p = parent[v];
+        anc0[v] = p;
+        D[v] = p == v ? 0 : qpar[v];
+        hop[v] = p == v ? 0 : 1;
+    }
+}
+
+__global__ void k1_jump(int n, const int32_t *__restrict__ anc_k, const int64_t *__restrict__ Din,
+                        const int32_t *__restrict__ hin, int32_t *__restrict__ anc_k1, int64_t *__restrict__ Dout,
+                        int32_t *__restrict__ hout) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int a = anc_k[v];
+        anc_k1[v] = anc_k[a];
+        Dout[v] = Din[v] + Din[a];
+        hout[v] = hin[v] + hin[a];
+    }
+}
+
+__device__ __forceinline__ int k1_lca(int u, int v, const int32_t *__restrict__ anc, int n, int K,
+                                      const int32_t *__restrict__ hop) {
+    if (hop[u] < hop[v]) {
+        const int t = u;
+        u = v;
+        v = t;
+    }
+    int diff = hop[u] - hop[v];
+    for (int k = 0; diff; ++k, diff >>= 1)
+        if (diff & 1) u = anc[int64_t(k) * n + u];
+    if (u == v) return u;
+    for (int k = K - 1; k >= 0; --k) {
+        const int au = anc[int64_t(k) * n + u], av = anc[int64_t(k) * n + v];
+        if (au != av) {
+            u = au;
+            v = av;
+        }
+    }
+    return anc[u];
+}
+
+__global__ void k1_records(int64_t R, const int32_t *__restrict__ rec_v, const int32_t *__restrict__ rec_a,
+                           const int32_t *__restrict__ rec_p1, const int64_t *__restrict__ D,
+                           const int32_t *__restrict__ hop, const int32_t *__restrict__ anc, int n, int K,
+                           int32_t *__restrict__ out_r, int32_t *__restrict__ out_x) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < R; i += int64_t(gridDim.x) * blockDim.x) {
+        const int v = rec_v[i], a = rec_a[i], p1 = rec_p1[i];
+        out_r[i] = int32_t(D[v] + D[a] - 2 * D[k1_lca(v, a, anc, n, K, hop)]);
+        out_x[i] = int32_t(D[p1] + D[a] - 2 * D[k1_lca(p1, a, anc, n, K, hop)]);
+    }
+}
+
 }  // namespace dev
 }  // namespace tfi

@@ -471,6 +471,42 @@ int flatten(HostPlan &hp, std::string &err) {
             hp.vrec_bkey[size_t(slot)] = rec_bkey[size_t(i)];
         }
     }
+    // rooted forest for the device distance pass: each tree rooted at its smallest vertex
+    {
+        hp.k1_parent.assign(size_t(hp.n), -1);
+        hp.k1_qpar.assign(size_t(hp.n), 0);
+        std::vector<int32_t> hop(size_t(hp.n), 0), queue;
+        queue.reserve(size_t(hp.n));
+        for (int32_t s0 = 0; s0 < hp.n; ++s0) {
+            if (hp.k1_parent[size_t(s0)] >= 0) continue;
+            hp.k1_parent[size_t(s0)] = s0;
+            queue.clear();
+            queue.push_back(s0);
+            for (size_t h = 0; h < queue.size(); ++h) {
+                const int32_t a = queue[h];
+                for (int64_t e = hp.ptr[size_t(a)]; e < hp.ptr[size_t(a) + 1]; ++e) {
+                    const int32_t b = hp.adj[size_t(e)];
+                    if (hp.k1_parent[size_t(b)] >= 0) continue;
+                    hp.k1_parent[size_t(b)] = a;
+                    hp.k1_qpar[size_t(b)] = int32_t(hp.qlen[size_t(e)]);
+                    hop[size_t(b)] = hop[size_t(a)] + 1;
+                    hp.k1_maxhop = std::max(hp.k1_maxhop, hop[size_t(b)]);
+                    queue.push_back(b);
+                }
+            }
+        }
+        hp.rec_anchor.resize(hp.recs.size());
+        hp.rec_p1.resize(hp.recs.size());
+        for (const Call &c : hp.calls) {
+            const int32_t p1 = hp.bb[size_t(c.bb_begin)];
+            for (int64_t i = c.rec_begin; i < c.rec_end; ++i) {
+                const Rec &rc = hp.recs[size_t(i)];
+                hp.rec_anchor[size_t(i)] =
+                    rc.comp >= 0 ? hp.bb[size_t(c.bb_begin + hp.comps[size_t(rc.comp)].anchor_idx)] : rc.v;
+                hp.rec_p1[size_t(i)] = p1;
+            }
+        }
+    }
     hp.in_leaf.assign(size_t(hp.n), 0);
     for (int32_t v : hp.leaf_vtx) hp.in_leaf[size_t(v)] = 1;
     // leaf groups

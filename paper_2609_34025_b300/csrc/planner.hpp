@@ -87,6 +87,10 @@ struct HostPlan {
     std::vector<int32_t> leaf_lo, leaf_hi;                 // per leaf vertex: its leaf's range (absolute)
     std::vector<uint8_t> in_leaf;                          // per vertex: 1 if it lies in a leaf call (backbone
                                                            // vertices of non-leaf calls are complete there)
+    // device distance pass (rooted forest + per-record anchor and backbone start)
+    std::vector<int32_t> k1_parent, k1_qpar;               // parent (self at a root) and edge length to it
+    int32_t k1_maxhop = 0;                                 // largest hop depth below a root
+    std::vector<int32_t> rec_anchor, rec_p1;               // per record: pi(v) and the call's p_1
     int64_t ftab_len = 0;
     std::vector<float> ftab;
     // FFT spectra per (lp1, lp2) class, bit-reversed order, scaled by 1/(P1 P2), interleaved re/im

@@ -62,6 +62,8 @@ struct tfi_plan_s {
     float2 *spectra = nullptr, *twiddle = nullptr;
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
     void *stage_in = nullptr, *stage_out = nullptr;
+    int32_t *dev_rec_r = nullptr, *dev_rec_x = nullptr;  // record keys computed on the device at plan time
+    double device_keys_ms = 0.0;
     std::map<int, WorkLists> work;  // per channel count d
     // fork/join inside an apply: leaf terms and direct jobs run on their own
     // streams, concurrently with the bin sums and FFT jobs
@@ -304,6 +306,78 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     return TFI_OK;
 }
 
+// Device allocations that live for one plan-time pass.
+struct DeviceTemps {
+    std::vector<void *> ptrs;
+    ~DeviceTemps() {
+        for (void *q : ptrs) cudaFree(q);
+    }
+    template <typename T>
+    tfi_status get(T **dst, size_t count) {
+        void *q = nullptr;
+        if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return fail(TFI_ERR_OOM, "cudaMalloc failed (device keys)");
+        ptrs.push_back(q);
+        *dst = static_cast<T *>(q);
+        return TFI_OK;
+    }
+};
+
+// (a2) device distances and bin keys at plan time; temporaries are freed here.
+tfi_status run_device_keys(tfi_plan_t p) {
+    const tfi::HostPlan &hp = p->hp;
+    const int n = hp.n;
+    const int64_t R = int64_t(hp.recs.size());
+    if (R == 0) return TFI_OK;
+    DeviceTemps tmp;
+    int K = 1;
+    while ((1 << K) <= hp.k1_maxhop) ++K;  // 2^K > largest hop depth
+    int32_t *parent, *qpar, *rv, *ra, *rp, *hop0, *hop1, *anc;
+    int64_t *D0, *D1;
+    if (tfi_status rc = tmp.get(&parent, size_t(n))) return rc;
+    if (tfi_status rc = tmp.get(&qpar, size_t(n))) return rc;
+    if (tfi_status rc = tmp.get(&rv, size_t(R))) return rc;
+    if (tfi_status rc = tmp.get(&ra, size_t(R))) return rc;
+    if (tfi_status rc = tmp.get(&rp, size_t(R))) return rc;
+    if (tfi_status rc = tmp.get(&hop0, size_t(n))) return rc;
+    if (tfi_status rc = tmp.get(&hop1, size_t(n))) return rc;
+    if (tfi_status rc = tmp.get(&D0, size_t(n))) return rc;
+    if (tfi_status rc = tmp.get(&D1, size_t(n))) return rc;
+    if (tfi_status rc = tmp.get(&anc, size_t(K + 1) * size_t(n))) return rc;
+    std::vector<int32_t> rec_v(static_cast<size_t>(R));
+    for (int64_t i = 0; i < R; ++i) rec_v[size_t(i)] = hp.recs[size_t(i)].v;
+    TFI_CUDA(cudaMemcpy(parent, hp.k1_parent.data(), size_t(n) * 4, cudaMemcpyHostToDevice));
+    TFI_CUDA(cudaMemcpy(qpar, hp.k1_qpar.data(), size_t(n) * 4, cudaMemcpyHostToDevice));
+    TFI_CUDA(cudaMemcpy(rv, rec_v.data(), size_t(R) * 4, cudaMemcpyHostToDevice));
+    TFI_CUDA(cudaMemcpy(ra, hp.rec_anchor.data(), size_t(R) * 4, cudaMemcpyHostToDevice));
+    TFI_CUDA(cudaMemcpy(rp, hp.rec_p1.data(), size_t(R) * 4, cudaMemcpyHostToDevice));
+    void *outr = nullptr, *outx = nullptr;
+    if (tfi_status rc = p->alloc(&outr, size_t(R) * 4)) return rc;
+    if (tfi_status rc = p->alloc(&outx, size_t(R) * 4)) return rc;
+    p->dev_rec_r = static_cast<int32_t *>(outr);
+    p->dev_rec_x = static_cast<int32_t *>(outx);
+    cudaEvent_t e0, e1;
+    TFI_CUDA(cudaEventCreate(&e0));
+    TFI_CUDA(cudaEventCreate(&e1));
+    TFI_CUDA(cudaEventRecord(e0, 0));
+    const int gb = grid_for(n, 256);
+    tfi::dev::k1_init<<<gb, 256>>>(n, parent, qpar, D0, hop0, anc);
+    for (int k = 0; k < K; ++k) {
+        tfi::dev::k1_jump<<<gb, 256>>>(n, anc + int64_t(k) * n, D0, hop0, anc + int64_t(k + 1) * n, D1, hop1);
+        std::swap(D0, D1);
+        std::swap(hop0, hop1);
+    }
+    tfi::dev::k1_records<<<grid_for(R, 256), 256>>>(R, rv, ra, rp, D0, hop0, anc, n, K, p->dev_rec_r, p->dev_rec_x);
+    TFI_CUDA(cudaGetLastError());
+    TFI_CUDA(cudaEventRecord(e1, 0));
+    TFI_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    p->device_keys_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return TFI_OK;
+}
+
 tfi_status upload_plan(tfi_plan_t p) {
     tfi::HostPlan &hp = p->hp;
     TFI_CUDA(cudaGetDevice(&p->device));
@@ -346,6 +420,7 @@ tfi_status upload_plan(tfi_plan_t p) {
     if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->kbuf), K * dm * sizeof(float))) return rc;
     if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->vbuf), K * dm * sizeof(float))) return rc;
     if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->lbuf), size_t(hp.n) * dm * sizeof(float))) return rc;
+    if (tfi_status rc = run_device_keys(p)) return rc;
     for (cudaStream_t &st : p->aux) TFI_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     for (cudaEvent_t *e : {&p->ev_fork, &p->ev_leaf, &p->ev_bucket, &p->ev_dir})
         TFI_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
@@ -614,6 +689,7 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info) {
     info->ftab_len = hp.ftab_len;
     info->device_bytes = plan->dev_bytes;
     info->plan_seconds = hp.plan_seconds;
+    info->device_keys_ms = plan->device_keys_ms;
     return TFI_OK;
 }
 
@@ -706,6 +782,22 @@ tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t 
                 v.insert(v.end(), row, row + 3);
             }
             break;
+        case TFI_EXPORT_DEVICE_KEYS: {
+            if (!plan->on_device) return fail(TFI_ERR_NO_DEVICE, "plan was built host-only");
+            const size_t R = hp.recs.size();
+            std::vector<int32_t> r(R), x(R);
+            if (R) {
+                TFI_CUDA(cudaMemcpy(r.data(), plan->dev_rec_r, R * 4, cudaMemcpyDeviceToHost));
+                TFI_CUDA(cudaMemcpy(x.data(), plan->dev_rec_x, R * 4, cudaMemcpyDeviceToHost));
+            }
+            for (size_t c = 0; c < hp.calls.size(); ++c) {
+                for (int64_t i = hp.calls[c].rec_begin; i < hp.calls[c].rec_end; ++i) {
+                    const int64_t row[4] = {int64_t(c), hp.recs[size_t(i)].v, r[size_t(i)], x[size_t(i)]};
+                    v.insert(v.end(), row, row + 4);
+                }
+            }
+            break;
+        }
         default:
             return fail(TFI_ERR_ARG, "unknown export");
     }

@@ -184,3 +184,24 @@ def test_stage_profile_and_model():
     assert prof["gather"][1] == 1 and prof["gather"][0] > 0
     model = p.stage_model(16)
     assert model["bucket"][0] > 0 and model["leaf"][1] > 0
+
+
+@pytest.mark.parametrize("make,delta,policy", [
+    (lambda: W.configs.sweep("rrt", n=1 << 16, d=1)["tree"], 1 / 64, "adaptive"),
+    (lambda: W.configs.sweep("binary", n=1 << 15, d=1)["tree"], 1 / 64, "adaptive"),
+    (lambda: W.configs.sweep("caterpillar", n=1 << 13, d=1)["tree"], 1 / 64, "centroid"),
+    (lambda: W.configs.rrt_n2000()["tree"], 1.0, "diameter"),
+    (lambda: W.spider(8, 300), 1.0, "adaptive"),
+    (lambda: W.path(5000), 1.0, "diameter"),
+    (lambda: W.configs.uneven_batch(count=30, lo=4, hi=2000)["tree"], 1.0, "adaptive"),
+])
+def test_device_keys_bit_exact(make, delta, policy):
+    # (a2) depths and backbone coordinates computed on the device equal the planner's
+    t = make()
+    p = tfi.Plan.from_spec(t, delta, W.KernelSpec.exp(0.1), policy=policy, leaf_max=16, max_channels=1)
+    host = p.export("records")
+    dev = p.export("device_keys")
+    assert dev.shape[0] == host.shape[0]
+    assert np.array_equal(dev[:, :2], host[:, :2])
+    assert np.array_equal(dev[:, 2:4], host[:, 2:4])
+    assert p.info()["device_keys_ms"] > 0
