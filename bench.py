@@ -203,6 +203,44 @@ def run_reference(a):
 
 
 # ---------------------------------------------------------------------------
+# dense tensor-core baseline at N = 2^16 (same tree recipe)
+# ---------------------------------------------------------------------------
+def dense_baseline(a, n=1 << 16, reps=5):
+    import torch
+
+    import paper_2609_34025_b300 as tfi
+    import workloads as W
+
+    cfg = W.configs.sweep(shape=a.shape, n=n, d=a.d, kernel=a.kernel)
+    plan = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=a.policy, leaf_max=a.leaf_max,
+                              max_channels=a.d)
+    x = torch.from_numpy(W.normal_field(n, a.d, seed=123)).cuda()
+    out = torch.empty_like(x)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, k):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(k):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / k
+
+    stad_ms = timed(lambda: plan.apply(x, out), 20)
+    dense_ms = timed(lambda: plan.dense_apply(x, out), reps)
+    return {"n": n, "d": a.d, "workload": f"sweep_{a.shape}_n{n}_d{a.d}_{a.kernel}", "stad_fwd_ms": stad_ms,
+            "dense_tensor_core_fwd_ms": dense_ms, "speedup": dense_ms / stad_ms,
+            "dense": "tcgen05 kind::f16, BF16 hi/lo split (3 products), FP32 accumulation in TMEM"}
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(a):
@@ -324,6 +362,7 @@ def run_ours(a):
     F_np = F.cpu().numpy().astype(np.float64)
     G_np = G.cpu().numpy().astype(np.float64)
     cpu = cpu_baseline(cfg, F_np, G_np, budget_s=a.cpu_budget) if a.cpu_budget > 0 else None
+    dense = dense_baseline(a) if a.dense else None
     info = plan.info()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -333,7 +372,7 @@ def run_ours(a):
                                    "plan_seconds": round(plan_s, 3), "device_keys_ms": round(info["device_keys_ms"], 3), "plan_calls": info["n_calls"],
                                    "plan_leaves": info["n_leaves"], "plan_levels": info["n_levels"]}),
         "fwd_value": world * n * d / (fwd_ms / 1e3), "fwd_ms": fwd_ms,
-        "roofline": roof, "cpu_baseline": cpu,
+        "roofline": roof, "cpu_baseline": cpu, "dense_baseline": dense,
         "e2e": {"value": world * n * d * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * n * d * 4,
                 "d2h_bytes_per_step": 2 * n * d * 4},
         "gpu_launches": int(round(sum(launches.values()) * 2 * a.steps)),
@@ -358,6 +397,7 @@ def main():
     ap.add_argument("--policy", default="adaptive")
     ap.add_argument("--leaf-max", dest="leaf_max", type=int, default=512)
     ap.add_argument("--cpu-budget", dest="cpu_budget", type=float, default=15.0)
+    ap.add_argument("--no-dense", dest="dense", action="store_false", help="skip the dense tensor-core baseline")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3

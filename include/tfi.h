@@ -121,6 +121,18 @@ tfi_status tfi_apply(tfi_plan_t plan, const void *F, void *out, int32_t d, int32
 tfi_status tfi_apply_backward(tfi_plan_t plan, const void *grad_out, void *grad_F, int32_t d, int32_t dtype,
                               tfi_stream_t stream);
 
+/* The same out = K F evaluated densely on the tensor cores: per tree of the
+ * forest, out[i] = sum_j f(dhat(i, j)) F[j] with the f(D) tile generated in
+ * shared memory (root distances + a range minimum over the tree's preorder)
+ * and multiplied by tcgen05.mma (BF16 operands split into hi + lo parts, FP32
+ * accumulation; FP32 fields use three products). Cost O(sum over trees of
+ * n_T^2 d): the dense evaluation the paper compares against (runtime
+ * protocol of the attention appendix), and a fast path for small trees with
+ * many channels. The first call builds the per-tree preorder and sparse table
+ * on the device (allocates). Synchronises `stream` before returning; a
+ * tensor-core completion wait that gives up returns TFI_ERR_TIMEOUT. */
+tfi_status tfi_dense_apply(tfi_plan_t plan, const void *F, void *out, int32_t d, int32_t dtype, tfi_stream_t stream);
+
 /* As tfi_apply, with F and out in HOST memory (pinned memory gives
  * asynchronous copies). Copies F in, applies, copies out, and synchronises the
  * stream before returning. Uses plan-owned device staging buffers. */

@@ -59,7 +59,7 @@ class _Info(ctypes.Structure):
 
 EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_host", "tfi_destroy",
                     "tfi_plan_get_info", "tfi_plan_export", "tfi_profile_enable", "tfi_profile_read",
-                    "tfi_stage_model", "tfi_apply_static", "tfi_last_error")
+                    "tfi_stage_model", "tfi_apply_static", "tfi_dense_apply", "tfi_last_error")
 STAGES = ("leaf", "bucket", "fft", "direct", "gather")
 
 _lib = None
@@ -78,6 +78,7 @@ def lib():
         L.tfi_apply.argtypes = [vp, vp, vp, i32, i32, vp]
         L.tfi_apply_backward.argtypes = [vp, vp, vp, i32, i32, vp]
         L.tfi_apply_host.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.tfi_dense_apply.argtypes = [vp, vp, vp, i32, i32, vp]
         L.tfi_destroy.argtypes = [vp]
         L.tfi_plan_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
         L.tfi_plan_export.argtypes = [vp, i32, vp, i64, ctypes.POINTER(i64)]
@@ -169,6 +170,10 @@ class Plan:
     def apply(self, F, out=None, stream=None):
         """out = K F on the device (stream-ordered)."""
         return self._apply(lib().tfi_apply, F, out, stream)
+
+    def dense_apply(self, F, out=None, stream=None):
+        """out = K F by dense tensor-core evaluation per tree (synchronises)."""
+        return self._apply(lib().tfi_dense_apply, F, out, stream)
 
     def apply_backward(self, grad_out, out=None, stream=None):
         """grad_F = K^T grad_out (= K grad_out: the operator is symmetric)."""

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "dense_tc.cuh"
 #include "kernels.cuh"
 #include "planner.hpp"
 #include "tfi.h"
@@ -63,6 +64,13 @@ struct tfi_plan_s {
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
     void *stage_in = nullptr, *stage_out = nullptr;
     int32_t *dev_rec_r = nullptr, *dev_rec_x = nullptr;  // record keys computed on the device at plan time
+    // dense tensor-core evaluation (built on first use): per-tree preorder, root
+    // distances, sparse table of parent distances, f samples up to the largest diameter
+    bool dense_ready = false;
+    int32_t dense_trees = 0, dense_levels = 0, dense_max_tree = 0;
+    int32_t *dn_tree_ptr = nullptr, *dn_vtx = nullptr, *dn_dist = nullptr, *dn_st = nullptr, *dn_err = nullptr;
+    float *dn_ftab = nullptr;
+    std::vector<int32_t> dn_tree_ptr_h;
     double device_keys_ms = 0.0;
     std::map<int, WorkLists> work;  // per channel count d
     // fork/join inside an apply: leaf terms and direct jobs run on their own
@@ -559,6 +567,150 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
     return TFI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// dense tensor-core evaluation
+// ---------------------------------------------------------------------------
+tfi_status build_dense(tfi_plan_t p) {
+    if (p->dense_ready) return TFI_OK;
+    const tfi::HostPlan &hp = p->hp;
+    const int n = hp.n;
+    std::vector<int32_t> vtx, dist, pdist, tree_ptr(1, 0);
+    vtx.reserve(size_t(n));
+    dist.reserve(size_t(n));
+    pdist.reserve(size_t(n));
+    std::vector<char> seen(size_t(n), 0);
+    std::vector<int64_t> dd(size_t(n), 0);
+    std::vector<int32_t> stack, kids;
+    int64_t max_diam = 0;
+    int32_t max_tree = 1;
+    for (int32_t r = 0; r < n; ++r) {
+        if (seen[size_t(r)]) continue;
+        // preorder from the tree's smallest vertex, children ascending
+        const size_t start = vtx.size();
+        stack.assign(1, r);
+        seen[size_t(r)] = 1;
+        dd[size_t(r)] = 0;
+        std::vector<int64_t> par_d;
+        std::vector<int32_t> order_par;
+        while (!stack.empty()) {
+            const int32_t v = stack.back();
+            stack.pop_back();
+            vtx.push_back(v);
+            dist.push_back(int32_t(std::min<int64_t>(dd[size_t(v)], INT32_MAX)));
+            kids.clear();
+            for (int64_t e = hp.ptr[size_t(v)]; e < hp.ptr[size_t(v) + 1]; ++e) {
+                const int32_t b = hp.adj[size_t(e)];
+                if (seen[size_t(b)]) continue;
+                seen[size_t(b)] = 1;
+                dd[size_t(b)] = dd[size_t(v)] + hp.qlen[size_t(e)];
+                kids.push_back(b);
+            }
+            for (size_t k = kids.size(); k-- > 0;) stack.push_back(kids[k]);
+        }
+        // parent distance of every preorder entry = root distance of its parent
+        // (recovered as the smallest root distance among ancestors: the parent of
+        // entry w is the last earlier entry with a smaller distance on its root path)
+        const size_t end = vtx.size();
+        std::vector<int32_t> anc;
+        for (size_t i = start; i < end; ++i) {
+            // ancestors of vtx[i] on the preorder stack: pop entries that are not ancestors
+            const int32_t v = vtx[i];
+            while (!anc.empty()) {
+                const int32_t a = anc.back();
+                bool is_parent = false;
+                for (int64_t e = hp.ptr[size_t(v)]; e < hp.ptr[size_t(v) + 1]; ++e)
+                    if (hp.adj[size_t(e)] == a && dd[size_t(a)] < dd[size_t(v)]) is_parent = true;
+                if (is_parent) break;
+                anc.pop_back();
+            }
+            pdist.push_back(anc.empty() ? 0 : int32_t(dd[size_t(anc.back())]));
+            anc.push_back(v);
+        }
+        // exact diameter: farthest from the root, then farthest from that vertex
+        int32_t far = vtx[start];
+        for (size_t i = start; i < end; ++i)
+            if (dd[size_t(vtx[i])] > dd[size_t(far)]) far = vtx[i];
+        {
+            std::vector<int64_t> d2;
+            std::vector<int32_t> q(1, far);
+            std::vector<char> s2;
+            std::map<int32_t, int64_t> dmap;
+            dmap[far] = 0;
+            for (size_t h = 0; h < q.size(); ++h) {
+                const int32_t a = q[h];
+                for (int64_t e = hp.ptr[size_t(a)]; e < hp.ptr[size_t(a) + 1]; ++e) {
+                    const int32_t b = hp.adj[size_t(e)];
+                    if (dmap.count(b)) continue;
+                    dmap[b] = dmap[a] + hp.qlen[size_t(e)];
+                    max_diam = std::max(max_diam, dmap[b]);
+                    q.push_back(b);
+                }
+            }
+        }
+        tree_ptr.push_back(int32_t(end));
+        max_tree = std::max<int32_t>(max_tree, int32_t(end - start));
+    }
+    if (max_diam >= tfi::kGridMax) return fail(TFI_ERR_GRID_OVERFLOW, "tree diameter beyond 2^30 grid units");
+    if (hp.f.kind == TFI_F_TABLE && max_diam >= int64_t(hp.f.table.size()))
+        return fail(TFI_ERR_GRID_OVERFLOW, "sampled kernel table shorter than the largest tree diameter");
+    std::vector<float> ftab(size_t(max_diam + 1));
+    for (int64_t k = 0; k <= max_diam; ++k) ftab[size_t(k)] = float(hp.f.grid(k, hp.delta));
+    int levels = 1;
+    while ((2 << (levels - 1)) <= max_tree) ++levels;
+    if (tfi_status rc = p->upload(&p->dn_tree_ptr, tree_ptr)) return rc;
+    if (tfi_status rc = p->upload(&p->dn_vtx, vtx)) return rc;
+    if (tfi_status rc = p->upload(&p->dn_dist, dist)) return rc;
+    if (tfi_status rc = p->upload(&p->dn_ftab, ftab)) return rc;
+    void *st = nullptr, *errp = nullptr;
+    if (tfi_status rc = p->alloc(&st, size_t(levels) * size_t(n) * 4)) return rc;
+    if (tfi_status rc = p->alloc(&errp, 16)) return rc;
+    p->dn_st = static_cast<int32_t *>(st);
+    p->dn_err = static_cast<int32_t *>(errp);
+    TFI_CUDA(cudaMemset(p->dn_err, 0, 16));
+    TFI_CUDA(cudaMemcpy(p->dn_st, pdist.data(), size_t(n) * 4, cudaMemcpyHostToDevice));
+    for (int l = 1; l < levels; ++l)
+        tfi::tc::sparse_level<<<grid_for(n, 256), 256>>>(p->dn_st + int64_t(l - 1) * n, p->dn_st + int64_t(l) * n, n,
+                                                         1 << (l - 1));
+    TFI_CUDA(cudaGetLastError());
+    TFI_CUDA(cudaDeviceSynchronize());
+    p->dense_trees = int32_t(tree_ptr.size()) - 1;
+    p->dense_levels = levels;
+    p->dense_max_tree = max_tree;
+    p->dn_tree_ptr_h = tree_ptr;
+    p->dense_ready = true;
+    return TFI_OK;
+}
+
+template <typename T, int NC>
+tfi_status dense_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
+    if (tfi_status rc = build_dense(p)) return rc;
+    constexpr size_t smem = tfi::tc::dense_smem_bytes<T, NC>();
+    TFI_CUDA(cudaFuncSetAttribute(tfi::tc::dense_tc_kernel<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(smem)));
+    std::vector<tfi::tc::DenseItem> items;
+    for (int t = 0; t < p->dense_trees; ++t)
+        for (int32_t t0 = p->dn_tree_ptr_h[size_t(t)]; t0 < p->dn_tree_ptr_h[size_t(t) + 1]; t0 += tfi::tc::kTileM)
+            for (int c0 = 0; c0 < d; c0 += NC) items.push_back(tfi::tc::DenseItem{t0, t, c0, 0});
+    tfi::tc::DenseItem *d_items = nullptr;
+    TFI_CUDA(cudaMalloc(&d_items, items.size() * sizeof(items[0])));
+    TFI_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(items[0]), cudaMemcpyHostToDevice, s));
+    tfi::tc::dense_tc_kernel<T, NC><<<unsigned(items.size()), 128, smem, s>>>(
+        d_items, p->dn_tree_ptr, p->dn_vtx, p->dn_dist, p->dn_st, int64_t(p->hp.n), p->dense_levels, p->dn_ftab, F, d,
+        out, p->dn_err);
+    const cudaError_t le = cudaGetLastError();
+    const cudaError_t se = cudaStreamSynchronize(s);
+    cudaFree(d_items);
+    if (le != cudaSuccess) return fail(TFI_ERR_CUDA, std::string("dense_tc_kernel launch: ") + cudaGetErrorString(le));
+    if (se != cudaSuccess) return fail(TFI_ERR_CUDA, std::string("dense_tc_kernel: ") + cudaGetErrorString(se));
+    int32_t err = 0;
+    TFI_CUDA(cudaMemcpy(&err, p->dn_err, 4, cudaMemcpyDeviceToHost));
+    if (err) {
+        cudaMemset(p->dn_err, 0, 4);
+        return fail(TFI_ERR_TIMEOUT, "a tensor-core completion wait gave up");
+    }
+    return TFI_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -626,6 +778,16 @@ tfi_status tfi_apply_backward(tfi_plan_t plan, const void *grad_out, void *grad_
                               tfi_stream_t stream) {
     // K is symmetric: the adjoint is the same integrator applied to grad_out
     return tfi_apply(plan, grad_out, grad_F, d, dtype, stream);
+}
+
+tfi_status tfi_dense_apply(tfi_plan_t plan, const void *F, void *out, int32_t d, int32_t dtype,
+                           tfi_stream_t stream) {
+    if (tfi_status rc = check_apply_args(plan, F, out, d, dtype)) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dtype == TFI_DTYPE_F32)
+        return dense_impl<float, 16>(plan, static_cast<const float *>(F), static_cast<float *>(out), d, s);
+    return dense_impl<__nv_bfloat16, 64>(plan, static_cast<const __nv_bfloat16 *>(F),
+                                         static_cast<__nv_bfloat16 *>(out), d, s);
 }
 
 tfi_status tfi_apply_static(tfi_plan_t plan, const void *F, void *out, int32_t d, int32_t dtype,
