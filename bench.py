@@ -362,7 +362,7 @@ def run_ours(a):
     F_np = F.cpu().numpy().astype(np.float64)
     G_np = G.cpu().numpy().astype(np.float64)
     cpu = cpu_baseline(cfg, F_np, G_np, budget_s=a.cpu_budget) if a.cpu_budget > 0 else None
-    dense = dense_baseline(a) if a.dense else None
+    dense = dense_baseline(a, n=a.dense_n) if a.dense else None
     info = plan.info()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -398,6 +398,7 @@ def main():
     ap.add_argument("--leaf-max", dest="leaf_max", type=int, default=512)
     ap.add_argument("--cpu-budget", dest="cpu_budget", type=float, default=15.0)
     ap.add_argument("--no-dense", dest="dense", action="store_false", help="skip the dense tensor-core baseline")
+    ap.add_argument("--dense-n", dest="dense_n", type=int, default=1 << 16, help="tree size of the dense baseline")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
