@@ -78,10 +78,25 @@ __global__ void bucket_kernel(int64_t n_keys, const int32_t *__restrict__ key_pt
 #pragma unroll
         for (int i = 0; i < V; ++i) acc[i] = 0.f;
         const int e1 = key_ptr[k + 1];
-        for (int e = key_ptr[k]; e < e1; ++e) {
-            const T *row = F + int64_t(key_vtx[e]) * d + c;
+        // up to four members at a time: all their index and row loads are in flight
+        // together; the sum still runs in member order
+        for (int e = key_ptr[k]; e < e1; e += 4) {
+            int v[4];
 #pragma unroll
-            for (int i = 0; i < V; ++i) acc[i] += to_f<T>(row[i]);
+            for (int q = 0; q < 4; ++q) v[q] = e + q < e1 ? __ldg(key_vtx + e + q) : -1;
+            float x[4][V];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const T *row = F + int64_t(v[q] < 0 ? v[0] : v[q]) * d + c;
+#pragma unroll
+                for (int i = 0; i < V; ++i) x[q][i] = to_f<T>(row[i]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (v[q] < 0) break;
+#pragma unroll
+                for (int i = 0; i < V; ++i) acc[i] += x[q][i];
+            }
         }
         float *dst = kbuf + k * d + c;
 #pragma unroll
@@ -504,64 +519,74 @@ __global__ void gather_kernel(int n, const int32_t *__restrict__ vrec_ptr, const
 }
 
 // ---------------------------------------------------------------------------
-// dense leaves: one CTA per leaf group, CH channels per pass
-// dhat(i, j) = D(i) + D(j) - 2 min_{w in (i, j]} D(parent(w)) in preorder
+// dense leaves: one CTA per leaf group, CH channels per pass.
+// In a leaf's preorder, dhat(i, j) = D(i) + D(j) - 2 min_{w in (min(i,j), max(i,j)]}
+// D(parent(w)). Each target i walks all sources of its leaf in one order with a
+// running minimum: first j = i+1 .. hi-1 (min over (i, j] grows by one entry),
+// then j = hi-2-k downwards over j < i (min over (j, i]). In the first phase
+// neighbouring threads read neighbouring rows; in the second every thread of a
+// leaf reads the same row. Field rows use a padded stride, and the f samples are
+// staged in shared memory when they fit.
 // ---------------------------------------------------------------------------
-// Shared-memory layout of leaf_kernel, in 4-byte words: distances, sparse
-// table (levels x max_gs), then the field rows at a 16-byte aligned offset.
-__host__ __device__ inline int leaf_sx_offset(int max_gs, int levels) { return ((max_gs * (1 + levels)) + 3) & ~3; }
-__host__ __device__ inline size_t leaf_smem_bytes(int max_gs, int levels, int ch) {
-    return size_t(leaf_sx_offset(max_gs, levels)) * 4 + size_t(max_gs) * ch * 4;
+template <int CH>
+struct LeafStride {
+    static constexpr int v = CH >= 8 ? CH + 4 : CH;
+};
+
+__host__ __device__ inline size_t leaf_smem_bytes(int max_gs, int ch, int ftab_smem) {
+    const int sv = ch >= 8 ? ch + 4 : ch;
+    return size_t(2 * max_gs + 4) * 4 + size_t(max_gs) * sv * 4 + size_t(ftab_smem) * 4;
 }
 
 template <typename T, int CH>
 __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__restrict__ leaf_vtx,
                             const int32_t *__restrict__ leaf_dist, const int32_t *__restrict__ leaf_pdist,
                             const int32_t *__restrict__ leaf_lo, const int32_t *__restrict__ leaf_hi,
-                            const T *__restrict__ F, int d, const float *__restrict__ ftab, float *__restrict__ leaf_out,
-                            int max_gs) {
-    extern __shared__ int smem_i[];
+                            const T *__restrict__ F, int d, const float *__restrict__ ftab, int ftab_smem,
+                            float *__restrict__ leaf_out, int max_gs) {
+    constexpr int SV = LeafStride<CH>::v;
+    extern __shared__ __align__(16) int smem_i[];
     const int gb = gptr[blockIdx.x], ge = gptr[blockIdx.x + 1], gs = ge - gb;
     const int c0 = blockIdx.y * CH;
-    int levels = 1;
-    while ((2 << (levels - 1)) <= max_gs) ++levels;
     int *sdist = smem_i;
-    int *st = sdist + max_gs;                                   // levels x max_gs
-    // max_gs x CH field rows, 16-byte aligned for vector loads
-    float *sx = reinterpret_cast<float *>(smem_i + leaf_sx_offset(max_gs, levels));
+    int *spd = sdist + max_gs;
+    float *sx = reinterpret_cast<float *>(smem_i + ((2 * max_gs + 3) & ~3));   // 16-byte aligned rows
+    float *sf = sx + max_gs * SV;
     for (int i = threadIdx.x; i < gs; i += blockDim.x) {
         sdist[i] = leaf_dist[gb + i];
-        st[i] = leaf_pdist[gb + i];
+        spd[i] = leaf_pdist[gb + i];
         const int64_t v = leaf_vtx[gb + i];
 #pragma unroll
-        for (int c = 0; c < CH; ++c) sx[i * CH + c] = (c0 + c < d) ? to_f<T>(F[v * d + c0 + c]) : 0.f;
+        for (int c = 0; c < CH; ++c) sx[i * SV + c] = (c0 + c < d) ? to_f<T>(F[v * d + c0 + c]) : 0.f;
     }
+    for (int i = threadIdx.x; i < ftab_smem; i += blockDim.x) sf[i] = ftab[i];
     __syncthreads();
-    for (int l = 1; (1 << l) <= gs; ++l) {
-        const int h = 1 << (l - 1);
-        for (int i = threadIdx.x; i + (1 << l) <= gs; i += blockDim.x)
-            st[l * max_gs + i] = min(st[(l - 1) * max_gs + i], st[(l - 1) * max_gs + i + h]);
-        __syncthreads();
-    }
+    const float *fsrc = ftab_smem > 0 ? sf : ftab;
     for (int i = threadIdx.x; i < gs; i += blockDim.x) {
         const int lo = leaf_lo[gb + i] - gb, hi = leaf_hi[gb + i] - gb;
         const int di = sdist[i];
         float acc[CH];
+        const float f0 = fsrc[0];
 #pragma unroll
-        for (int c = 0; c < CH; ++c) acc[c] = 0.f;
-        for (int j = lo; j < hi; ++j) {
-            int dist = 0;
-            if (j != i) {
-                const int a = min(i, j) + 1, b = max(i, j);
-                const int l = 31 - __clz(b - a + 1);
-                const int m = min(st[l * max_gs + a], st[l * max_gs + b - (1 << l) + 1]);
-                dist = di + sdist[j] - 2 * m;
+        for (int c = 0; c < CH; ++c) acc[c] = f0 * sx[i * SV + c];
+        const int nf = hi - 1 - i;              // sources after i
+        const int steps = hi - lo - 1;          // all sources but i
+        int m = 0x7fffffff;
+        for (int k = 0; k < steps; ++k) {
+            int j;
+            if (k < nf) {
+                j = i + 1 + k;
+                m = min(m, spd[j]);
+            } else {
+                if (k == nf) m = 0x7fffffff;
+                j = hi - 2 - k;
+                m = min(m, spd[j + 1]);
             }
-            const float f = __ldg(ftab + dist);
+            const float f = fsrc[di + sdist[j] - 2 * m];
             if (CH % 4 == 0) {
 #pragma unroll
                 for (int c = 0; c < CH; c += 4) {
-                    const float4 q = *reinterpret_cast<const float4 *>(sx + j * CH + c);
+                    const float4 q = *reinterpret_cast<const float4 *>(sx + j * SV + c);
                     acc[c] = fmaf(f, q.x, acc[c]);
                     acc[c + 1] = fmaf(f, q.y, acc[c + 1]);
                     acc[c + 2] = fmaf(f, q.z, acc[c + 2]);
@@ -569,7 +594,7 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
                 }
             } else {
 #pragma unroll
-                for (int c = 0; c < CH; ++c) acc[c] = fmaf(f, sx[j * CH + c], acc[c]);
+                for (int c = 0; c < CH; ++c) acc[c] = fmaf(f, sx[j * SV + c], acc[c]);
             }
         }
         const int64_t v = leaf_vtx[gb + i];

@@ -192,15 +192,16 @@ int grid_for(int64_t work, int threads) {
     return int(std::max<int64_t>(1, std::min<int64_t>(b, 148 * 32)));
 }
 
+constexpr int kLeafFtabSmemMax = 12288;  // f samples staged in shared memory up to this many
+
 template <int CH, typename T>
-void launch_leaf(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
+void launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s) {
     if (p->n_groups == 0) return;
-    int levels = 1;
-    while ((2 << (levels - 1)) <= p->max_gs) ++levels;
-    const size_t smem = tfi::dev::leaf_smem_bytes(p->max_gs, levels, CH);
+    const int fts = p->hp.ftab_len <= kLeafFtabSmemMax ? int(p->hp.ftab_len) : 0;
+    const size_t smem = tfi::dev::leaf_smem_bytes(p->max_gs, CH, fts);
     dim3 grid(p->n_groups, (d + CH - 1) / CH);
     tfi::dev::leaf_kernel<T, CH><<<grid, 256, smem, s>>>(p->lgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist,
-                                                         p->leaf_lo, p->leaf_hi, F, d, p->ftab, p->lbuf, p->max_gs);
+                                                         p->leaf_lo, p->leaf_hi, F, d, p->ftab, fts, lbuf, p->max_gs);
 }
 
 template <int CH>
@@ -261,11 +262,11 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     TFI_CUDA(cudaStreamWaitEvent(s_leaf, p->ev_fork, 0));
     // (a7) dense leaves -> lbuf, on the leaf stream
     StageMark m_leaf(p, s_leaf, TFI_STAGE_LEAF);
-    if (d >= 16) launch_leaf<16>(p, F, d, s_leaf);
-    else if (d > 4) launch_leaf<8>(p, F, d, s_leaf);
-    else if (d > 2) launch_leaf<4>(p, F, d, s_leaf);
-    else if (d == 2) launch_leaf<2>(p, F, d, s_leaf);
-    else launch_leaf<1>(p, F, d, s_leaf);
+    if (d >= 16) launch_leaf<16>(p, F, p->lbuf, d, s_leaf);
+    else if (d > 4) launch_leaf<8>(p, F, p->lbuf, d, s_leaf);
+    else if (d > 2) launch_leaf<4>(p, F, p->lbuf, d, s_leaf);
+    else if (d == 2) launch_leaf<2>(p, F, p->lbuf, d, s_leaf);
+    else launch_leaf<1>(p, F, p->lbuf, d, s_leaf);
     m_leaf.done(p->n_groups > 0 ? 1 : 0);
     TFI_CUDA(cudaEventRecord(p->ev_leaf, s_leaf));
     // (a3) bin sums
@@ -534,15 +535,7 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
         TFI_CUDA(cudaMemcpyAsync(d_dir, dir.data(), dir.size() * sizeof(dir[0]), cudaMemcpyHostToDevice, s));
     // every workspace value an apply reads is written earlier in the same apply,
     // so nothing needs clearing between calls
-    if (p->n_groups > 0) {
-        int levels = 1;
-        while ((2 << (levels - 1)) <= p->max_gs) ++levels;
-        const int CH = 16;
-        const size_t smem = tfi::dev::leaf_smem_bytes(p->max_gs, levels, CH);
-        dim3 grid(p->n_groups, (d + CH - 1) / CH);
-        tfi::dev::leaf_kernel<T, 16><<<grid, 256, smem, s>>>(p->lgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist,
-                                                             p->leaf_lo, p->leaf_hi, F, d, p->ftab, lbuf, p->max_gs);
-    }
+    if (p->n_groups > 0) launch_leaf<16>(p, F, lbuf, d, s);
     if (K > 0) {
         tfi::dev::bucket_kernel<T, 1><<<grid_for(int64_t(K) * d, 256), 256, 0, s>>>(int64_t(K), p->key_ptr, p->key_vtx,
                                                                                    F, d, kbuf);
