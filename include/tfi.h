@@ -164,6 +164,20 @@ tfi_status tfi_apply_host(tfi_plan_t plan, const void *F_host, void *out_host, i
 #define TFI_STATIC_SCRATCH_BYTES (32u << 20)
 tfi_status tfi_apply_static(tfi_plan_t plan, const void *F, void *out, int32_t d, int32_t dtype, tfi_stream_t stream);
 
+/* CUDA-graph replay of a whole step. tfi_graph_create captures, on `stream`,
+ * one apply out = K F and, when grad_out and grad_F are both non-NULL, the
+ * adjoint grad_F = K grad_out, with these fixed device buffers, into one
+ * instantiated CUDA graph (all calls of every tree of the forest, leaf,
+ * bin-sum, table and gather launches with their stream fork / join).
+ * tfi_graph_launch replays it on `stream`; refill the input buffers in place
+ * between launches. The plan must outlive the graph, and its workspace is
+ * shared with other applies of the same plan (one stream at a time). */
+typedef struct tfi_graph_s *tfi_graph_t;
+tfi_status tfi_graph_create(tfi_plan_t plan, const void *F, void *out, const void *grad_out, void *grad_F, int32_t d,
+                            int32_t dtype, tfi_stream_t stream, tfi_graph_t *graph);
+tfi_status tfi_graph_launch(tfi_graph_t graph, tfi_stream_t stream);
+tfi_status tfi_graph_destroy(tfi_graph_t graph);
+
 /* Release everything the plan owns. NULL is accepted and ignored. */
 tfi_status tfi_destroy(tfi_plan_t plan);
 

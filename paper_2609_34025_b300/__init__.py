@@ -59,7 +59,8 @@ class _Info(ctypes.Structure):
 
 EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_host", "tfi_destroy",
                     "tfi_plan_get_info", "tfi_plan_export", "tfi_profile_enable", "tfi_profile_read",
-                    "tfi_stage_model", "tfi_apply_static", "tfi_dense_apply", "tfi_last_error")
+                    "tfi_stage_model", "tfi_apply_static", "tfi_dense_apply", "tfi_graph_create", "tfi_graph_launch",
+                    "tfi_graph_destroy", "tfi_last_error")
 STAGES = ("leaf", "bucket", "fft", "direct", "gather")
 
 _lib = None
@@ -79,6 +80,9 @@ def lib():
         L.tfi_apply_backward.argtypes = [vp, vp, vp, i32, i32, vp]
         L.tfi_apply_host.argtypes = [vp, vp, vp, i32, i32, vp]
         L.tfi_dense_apply.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.tfi_graph_create.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, ctypes.POINTER(vp)]
+        L.tfi_graph_launch.argtypes = [vp, vp]
+        L.tfi_graph_destroy.argtypes = [vp]
         L.tfi_destroy.argtypes = [vp]
         L.tfi_plan_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
         L.tfi_plan_export.argtypes = [vp, i32, vp, i64, ctypes.POINTER(i64)]
@@ -226,6 +230,33 @@ class Plan:
         _check(lib().tfi_plan_export(self._h, code, buf.ctypes.data if ln.value else None, ln.value,
                                      ctypes.byref(ln)))
         return buf.reshape(-1, width) if width > 1 else buf
+
+
+class Graph:
+    """A captured forward (+ optional backward) step on fixed buffers, replayed by one graph launch."""
+
+    def __init__(self, plan: Plan, F, out, grad_out=None, grad_F=None, stream=None):
+        self.plan = plan
+        self.bufs = (F, out, grad_out, grad_F)  # keep the buffers alive
+        h = ctypes.c_void_p()
+        ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        _check(lib().tfi_graph_create(plan._h, ptr(F), ptr(out), ptr(grad_out), ptr(grad_F), int(F.shape[1]),
+                                      _dtype_code(F), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().tfi_graph_launch(self._h, _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tfi_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _autograd_fn():

@@ -2,11 +2,13 @@
 #include "planner.hpp"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
 #include <deque>
 #include <numeric>
+#include <thread>
 
 #include "tfi.h"
 
@@ -375,83 +377,149 @@ private:
 constexpr double kFftCostPerPointLog = 3.0;
 constexpr double kFftCostPerKey = 4.0;
 
+// Run fn(i) for i in [0, n) on all hardware threads (dynamic scheduling).
+template <typename Fn>
+void parallel_for(size_t n, Fn fn) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nth = std::min<size_t>(n, hw);
+    std::atomic<size_t> next(0);
+    auto worker = [&]() {
+        for (;;) {
+            const size_t i = next.fetch_add(1);
+            if (i >= n) break;
+            fn(i);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < nth; ++t) pool.emplace_back(worker);
+    if (n) worker();
+    for (std::thread &th : pool) th.join();
+}
+
+// Bins of one call: its A-bins (distinct (depth, coordinate)) and each
+// component's b-bins (distinct depth), members ascending by vertex id.
+struct CallBins {
+    std::vector<int32_t> kr, kx, ksize, kvtx;   // bins in order; member lists concatenated
+    std::vector<int32_t> rec_akey, rec_bkey;    // per record of the call (local bin index, -1 none)
+    std::vector<std::pair<int32_t, int32_t>> jobs;  // local bin ranges: call table first, then components
+};
+
+void build_call_bins(const HostPlan &hp, const Call &call, CallBins &cb) {
+    const int64_t nrec = call.rec_end - call.rec_begin;
+    cb.rec_akey.assign(size_t(nrec), -1);
+    cb.rec_bkey.assign(size_t(nrec), -1);
+    struct Item {
+        uint64_t key;
+        int32_t v;
+        int32_t pos;
+        bool operator<(const Item &o) const { return key != o.key ? key < o.key : v < o.v; }
+    };
+    std::vector<Item> items(static_cast<size_t>(nrec));
+    for (int64_t i = 0; i < nrec; ++i) {
+        const Rec &rc = hp.recs[size_t(call.rec_begin + i)];
+        items[size_t(i)] = Item{(uint64_t(uint32_t(rc.r)) << 32) | uint32_t(rc.x), rc.v, int32_t(i)};
+    }
+    std::sort(items.begin(), items.end());
+    int32_t kb = 0;
+    for (size_t i = 0; i < items.size(); ++i) {
+        if (i == 0 || items[i].key != items[i - 1].key) {
+            cb.kr.push_back(int32_t(items[i].key >> 32));
+            cb.kx.push_back(int32_t(items[i].key & 0xffffffffu));
+            cb.ksize.push_back(0);
+        }
+        cb.ksize.back()++;
+        cb.kvtx.push_back(items[i].v);
+        cb.rec_akey[size_t(items[i].pos)] = int32_t(cb.kr.size() - 1);
+    }
+    cb.jobs.push_back({kb, int32_t(cb.kr.size())});
+    int64_t pos = call.bb_end - call.bb_begin;
+    for (int32_t a = call.comp_begin; a < call.comp_end; ++a) {
+        const int64_t cbeg = pos, cend = pos + hp.comps[size_t(a)].size;
+        pos = cend;
+        items.resize(size_t(cend - cbeg));
+        for (int64_t i = cbeg; i < cend; ++i) {
+            const Rec &rc = hp.recs[size_t(call.rec_begin + i)];
+            items[size_t(i - cbeg)] = Item{uint64_t(uint32_t(rc.r)), rc.v, int32_t(i)};
+        }
+        std::sort(items.begin(), items.end());
+        kb = int32_t(cb.kr.size());
+        for (size_t i = 0; i < items.size(); ++i) {
+            if (i == 0 || items[i].key != items[i - 1].key) {
+                cb.kr.push_back(int32_t(items[i].key));
+                cb.kx.push_back(0);
+                cb.ksize.push_back(0);
+            }
+            cb.ksize.back()++;
+            cb.kvtx.push_back(items[i].v);
+            cb.rec_bkey[size_t(items[i].pos)] = int32_t(cb.kr.size() - 1);
+        }
+        cb.jobs.push_back({kb, int32_t(cb.kr.size())});
+    }
+}
+
 int flatten(HostPlan &hp, std::string &err) {
     const int64_t R = int64_t(hp.recs.size());
     std::vector<int32_t> rec_akey(size_t(R), -1), rec_bkey(size_t(R), -1);
-    hp.key_ptr.assign(1, 0);
-    std::vector<int64_t> idx;
-    auto add_job = [&](int64_t kb, int64_t ke, int is_comp) {
-        Job j{};
-        j.kb = kb;
-        j.ke = ke;
-        j.is_comp = is_comp;
-        int32_t maxr = 0, maxx = 0;
-        for (int64_t k = kb; k < ke; ++k) {
-            maxr = std::max(maxr, hp.key_r[size_t(k)]);
-            maxx = std::max(maxx, hp.key_x[size_t(k)]);
-        }
-        j.maxr = maxr;
-        j.maxx = maxx;
-        j.lp1 = ceil_log2(2 * int64_t(maxr) + 1);
-        j.lp2 = maxx > 0 ? ceil_log2(2 * int64_t(maxx)) : 0;
-        const double nk = double(ke - kb);
-        const int lg = j.lp1 + j.lp2;
-        const double np = std::ldexp(1.0, lg);
-        const double cost_fft = kFftCostPerPointLog * np * std::max(1, lg) + kFftCostPerKey * nk;
-        j.mode = (lg <= kFftMaxLog && cost_fft < nk * nk) ? 0 : 1;
-        hp.jobs.push_back(j);
-    };
-    for (size_t c = 0; c < hp.calls.size(); ++c) {
-        const Call &call = hp.calls[c];
-        // A-bins: distinct (depth, coordinate) of the call (Eq. "sumofFFTterms" aggregates A_r[t])
-        idx.resize(size_t(call.rec_end - call.rec_begin));
-        std::iota(idx.begin(), idx.end(), call.rec_begin);
-        std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
-            const Rec &x = hp.recs[size_t(a)], &y = hp.recs[size_t(b)];
-            if (x.r != y.r) return x.r < y.r;
-            if (x.x != y.x) return x.x < y.x;
-            return x.v < y.v;
-        });
-        const int64_t kb = int64_t(hp.key_r.size());
-        for (size_t i = 0; i < idx.size(); ++i) {
-            const Rec &rc = hp.recs[size_t(idx[i])];
-            if (i == 0 || rc.r != hp.recs[size_t(idx[i - 1])].r || rc.x != hp.recs[size_t(idx[i - 1])].x) {
-                if (i) hp.key_ptr.push_back(int32_t(hp.key_vtx.size()));
-                hp.key_r.push_back(rc.r);
-                hp.key_x.push_back(rc.x);
-            }
-            hp.key_vtx.push_back(rc.v);
-            rec_akey[size_t(idx[i])] = int32_t(hp.key_r.size() - 1);
-        }
-        hp.key_ptr.push_back(int32_t(hp.key_vtx.size()));
-        add_job(kb, int64_t(hp.key_r.size()), 0);
-        // b-bins of each component: distinct depths (Eq. "stad-E" profile b_alpha)
-        int64_t pos = call.rec_begin + (call.bb_end - call.bb_begin);
-        for (int32_t a = call.comp_begin; a < call.comp_end; ++a) {
-            const int64_t cb = pos, ce = pos + hp.comps[size_t(a)].size;
-            pos = ce;
-            idx.resize(size_t(ce - cb));
-            std::iota(idx.begin(), idx.end(), cb);
-            std::sort(idx.begin(), idx.end(), [&](int64_t p, int64_t q) {
-                const Rec &x = hp.recs[size_t(p)], &y = hp.recs[size_t(q)];
-                if (x.r != y.r) return x.r < y.r;
-                return x.v < y.v;
-            });
-            const int64_t bk = int64_t(hp.key_r.size());
-            for (size_t i = 0; i < idx.size(); ++i) {
-                const Rec &rc = hp.recs[size_t(idx[i])];
-                if (i == 0 || rc.r != hp.recs[size_t(idx[i - 1])].r) {
-                    if (i) hp.key_ptr.push_back(int32_t(hp.key_vtx.size()));
-                    hp.key_r.push_back(rc.r);
-                    hp.key_x.push_back(0);
-                }
-                hp.key_vtx.push_back(rc.v);
-                rec_bkey[size_t(idx[i])] = int32_t(hp.key_r.size() - 1);
-            }
-            hp.key_ptr.push_back(int32_t(hp.key_vtx.size()));
-            add_job(bk, int64_t(hp.key_r.size()), 1);
-        }
+    const size_t C = hp.calls.size();
+    // bins per call, in parallel; then global offsets in call order
+    std::vector<CallBins> bins(C);
+    parallel_for(C, [&](size_t c) { build_call_bins(hp, hp.calls[c], bins[c]); });
+    std::vector<int64_t> koff(C + 1, 0), voff(C + 1, 0), joff(C + 1, 0);
+    for (size_t c = 0; c < C; ++c) {
+        koff[c + 1] = koff[c] + int64_t(bins[c].kr.size());
+        voff[c + 1] = voff[c] + int64_t(bins[c].kvtx.size());
+        joff[c + 1] = joff[c] + int64_t(bins[c].jobs.size());
     }
+    if (voff[C] >= int64_t(INT32_MAX)) {
+        err = "plan too large for 32-bit bin indices";
+        return TFI_ERR_UNSUPPORTED;
+    }
+    hp.key_r.resize(size_t(koff[C]));
+    hp.key_x.resize(size_t(koff[C]));
+    hp.key_ptr.resize(size_t(koff[C]) + 1);
+    hp.key_vtx.resize(size_t(voff[C]));
+    hp.jobs.resize(size_t(joff[C]));
+    hp.key_ptr[size_t(koff[C])] = int32_t(voff[C]);
+    parallel_for(C, [&](size_t c) {
+        CallBins &cb = bins[c];
+        const Call &call = hp.calls[c];
+        int64_t vo = voff[c];
+        for (size_t k = 0; k < cb.kr.size(); ++k) {
+            hp.key_r[size_t(koff[c]) + k] = cb.kr[k];
+            hp.key_x[size_t(koff[c]) + k] = cb.kx[k];
+            hp.key_ptr[size_t(koff[c]) + k] = int32_t(vo);
+            vo += cb.ksize[k];
+        }
+        std::copy(cb.kvtx.begin(), cb.kvtx.end(), hp.key_vtx.begin() + voff[c]);
+        for (int64_t i = 0; i < call.rec_end - call.rec_begin; ++i) {
+            rec_akey[size_t(call.rec_begin + i)] = int32_t(koff[c]) + cb.rec_akey[size_t(i)];
+            if (cb.rec_bkey[size_t(i)] >= 0)
+                rec_bkey[size_t(call.rec_begin + i)] = int32_t(koff[c]) + cb.rec_bkey[size_t(i)];
+        }
+        for (size_t j = 0; j < cb.jobs.size(); ++j) {
+            Job jb{};
+            jb.kb = koff[c] + cb.jobs[j].first;
+            jb.ke = koff[c] + cb.jobs[j].second;
+            jb.is_comp = j > 0 ? 1 : 0;
+            int32_t maxr = 0, maxx = 0;
+            for (int64_t k = jb.kb; k < jb.ke; ++k) {
+                maxr = std::max(maxr, hp.key_r[size_t(k)]);
+                maxx = std::max(maxx, hp.key_x[size_t(k)]);
+            }
+            jb.maxr = maxr;
+            jb.maxx = maxx;
+            jb.lp1 = ceil_log2(2 * int64_t(maxr) + 1);
+            jb.lp2 = maxx > 0 ? ceil_log2(2 * int64_t(maxx)) : 0;
+            const double nk = double(jb.ke - jb.kb);
+            const int lg = jb.lp1 + jb.lp2;
+            const double np = std::ldexp(1.0, lg);
+            const double cost_fft = kFftCostPerPointLog * np * std::max(1, lg) + kFftCostPerKey * nk;
+            jb.mode = (lg <= kFftMaxLog && cost_fft < nk * nk) ? 0 : 1;
+            hp.jobs[size_t(joff[c]) + j] = jb;
+        }
+        CallBins().kr.swap(cb.kr);
+        cb = CallBins();
+    });
     if (hp.key_vtx.size() >= size_t(INT32_MAX)) {
         err = "plan too large for 32-bit bin indices";
         return TFI_ERR_UNSUPPORTED;
@@ -591,6 +659,110 @@ int flatten(HostPlan &hp, std::string &err) {
     return TFI_OK;
 }
 
+// Plan every tree of a forest on its own, in parallel, with an order-preserving
+// local relabelling (local id = rank of the vertex id within its tree, so every
+// smallest-id tie-break is unchanged), then merge the per-tree plans in tree
+// order. Each vertex belongs to one tree, so per-vertex call order (level order)
+// and every bin's member order are the same as planning the forest as a whole.
+int plan_forest(HostPlan &hp, const std::vector<std::vector<int32_t>> &trees, std::string &err) {
+    const size_t T = trees.size();
+    std::vector<HostPlan> local(T);
+    std::vector<std::string> errs(T);
+    std::vector<int> rcs(T, 0);
+    std::vector<size_t> order(T);
+    std::iota(order.begin(), order.end(), size_t(0));
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return trees[a].size() > trees[b].size(); });
+    std::atomic<size_t> next(0);
+    auto worker = [&]() {
+        std::vector<int32_t> loc_of;  // global -> local, filled per tree
+        for (;;) {
+            const size_t qi = next.fetch_add(1);
+            if (qi >= T) break;
+            const size_t t = order[qi];
+            const std::vector<int32_t> &vs = trees[t];
+            HostPlan &lp = local[t];
+            lp.n = int32_t(vs.size());
+            lp.delta = hp.delta;
+            lp.f = hp.f;
+            lp.policy = hp.policy;
+            lp.leaf_max = hp.leaf_max;
+            lp.ptr.assign(vs.size() + 1, 0);
+            for (size_t i = 0; i < vs.size(); ++i) lp.ptr[i + 1] = lp.ptr[i] + (hp.ptr[size_t(vs[i]) + 1] - hp.ptr[size_t(vs[i])]);
+            lp.adj.resize(size_t(lp.ptr.back()));
+            lp.qlen.resize(size_t(lp.ptr.back()));
+            for (size_t i = 0; i < vs.size(); ++i) {
+                int64_t o = lp.ptr[i];
+                for (int64_t e = hp.ptr[size_t(vs[i])]; e < hp.ptr[size_t(vs[i]) + 1]; ++e, ++o) {
+                    const int32_t g = hp.adj[size_t(e)];
+                    lp.adj[size_t(o)] = int32_t(std::lower_bound(vs.begin(), vs.end(), g) - vs.begin());
+                    lp.qlen[size_t(o)] = hp.qlen[size_t(e)];
+                }
+            }
+            Builder b(lp);
+            rcs[t] = b.run(errs[t]);
+            lp.ptr.clear();
+            lp.ptr.shrink_to_fit();
+            lp.adj.clear();
+            lp.adj.shrink_to_fit();
+            lp.qlen.clear();
+            lp.qlen.shrink_to_fit();
+        }
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nth = std::min<size_t>(T, hw);
+    std::vector<std::thread> pool;
+    for (size_t i = 1; i < nth; ++i) pool.emplace_back(worker);
+    worker();
+    for (std::thread &th : pool) th.join();
+    for (size_t t = 0; t < T; ++t) {
+        if (rcs[t]) {
+            err = errs[t];
+            return rcs[t];
+        }
+    }
+    // merge in tree order, mapping local ids back to global ones
+    for (size_t t = 0; t < T; ++t) {
+        const std::vector<int32_t> &vs = trees[t];
+        HostPlan &lp = local[t];
+        const int64_t bb0 = int64_t(hp.bb.size()), rec0 = int64_t(hp.recs.size()), lv0 = int64_t(hp.leaf_vtx.size());
+        const int32_t comp0 = int32_t(hp.comps.size()), call0 = int32_t(hp.calls.size());
+        for (Call c : lp.calls) {
+            c.minv = vs[size_t(c.minv)];
+            c.bb_begin += bb0;
+            c.bb_end += bb0;
+            c.rec_begin += rec0;
+            c.rec_end += rec0;
+            c.comp_begin += comp0;
+            c.comp_end += comp0;
+            hp.calls.push_back(c);
+        }
+        for (int32_t v : lp.bb) hp.bb.push_back(vs[size_t(v)]);
+        for (Rec r : lp.recs) {
+            r.v = vs[size_t(r.v)];
+            if (r.comp >= 0) r.comp += comp0;
+            hp.recs.push_back(r);
+        }
+        for (Comp cp : lp.comps) {
+            cp.call += call0;
+            cp.minv = vs[size_t(cp.minv)];
+            hp.comps.push_back(cp);
+        }
+        for (Leaf lf : lp.leaves) {
+            lf.minv = vs[size_t(lf.minv)];
+            lf.begin += lv0;
+            lf.end += lv0;
+            hp.leaves.push_back(lf);
+        }
+        for (int32_t v : lp.leaf_vtx) hp.leaf_vtx.push_back(vs[size_t(v)]);
+        hp.leaf_dist.insert(hp.leaf_dist.end(), lp.leaf_dist.begin(), lp.leaf_dist.end());
+        hp.leaf_pdist.insert(hp.leaf_pdist.end(), lp.leaf_pdist.begin(), lp.leaf_pdist.end());
+        hp.n_levels = std::max(hp.n_levels, lp.n_levels);
+        HostPlan().calls.swap(lp.calls);
+        lp = HostPlan();
+    }
+    return TFI_OK;
+}
+
 }  // namespace
 
 int build_plan(HostPlan &hp, int32_t n, int32_t m, const int32_t *u, const int32_t *v, const double *w,
@@ -659,8 +831,30 @@ int build_plan(HostPlan &hp, int32_t n, int32_t m, const int32_t *u, const int32
             }
         }
     }
-    Builder b(hp);
-    if (int rc = b.run(err)) return rc;
+    // trees of the forest, each as an ascending vertex list (tree order = smallest vertex)
+    std::vector<int32_t> tree_of(size_t(n), -1);
+    std::vector<std::vector<int32_t>> trees;
+    for (int32_t s0 = 0; s0 < n; ++s0) {
+        if (tree_of[size_t(s0)] >= 0) continue;
+        const int32_t id = int32_t(trees.size());
+        trees.emplace_back();
+        std::vector<int32_t> &vs = trees.back();
+        vs.push_back(s0);
+        tree_of[size_t(s0)] = id;
+        for (size_t h = 0; h < vs.size(); ++h)
+            for (int64_t e = hp.ptr[size_t(vs[h])]; e < hp.ptr[size_t(vs[h]) + 1]; ++e)
+                if (tree_of[size_t(hp.adj[size_t(e)])] < 0) {
+                    tree_of[size_t(hp.adj[size_t(e)])] = id;
+                    vs.push_back(hp.adj[size_t(e)]);
+                }
+        std::sort(vs.begin(), vs.end());
+    }
+    if (trees.size() <= 1) {
+        Builder b(hp);
+        if (int rc = b.run(err)) return rc;
+    } else if (int rc = plan_forest(hp, trees, err)) {
+        return rc;
+    }
     if (int rc = flatten(hp, err)) return rc;
     hp.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return TFI_OK;

@@ -239,7 +239,9 @@ struct StageMark {
     int stage;
     cudaEvent_t a = nullptr;
     StageMark(tfi_plan_t p_, cudaStream_t s_, int st) : p(p_), s(s_), stage(st) {
-        if (p->profiling && (a = p->next_event())) cudaEventRecord(a, s);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s, &cs);
+        if (p->profiling && cs == cudaStreamCaptureStatusNone && (a = p->next_event())) cudaEventRecord(a, s);
     }
     void done(int launches) {
         if (!a) return;
@@ -810,6 +812,62 @@ tfi_status tfi_apply_host(tfi_plan_t plan, const void *F_host, void *out_host, i
     if (tfi_status rc = tfi_apply(plan, plan->stage_in, plan->stage_out, d, dtype, stream)) return rc;
     TFI_CUDA(cudaMemcpyAsync(out_host, plan->stage_out, bytes, cudaMemcpyDeviceToHost, s));
     TFI_CUDA(cudaStreamSynchronize(s));
+    return TFI_OK;
+}
+
+}  // extern "C"
+
+struct tfi_graph_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~tfi_graph_s() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+extern "C" {
+
+tfi_status tfi_graph_create(tfi_plan_t plan, const void *F, void *out, const void *grad_out, void *grad_F, int32_t d,
+                            int32_t dtype, tfi_stream_t stream, tfi_graph_t *graph) {
+    if (!graph) return fail(TFI_ERR_ARG, "null graph handle");
+    *graph = nullptr;
+    if (tfi_status rc = check_apply_args(plan, F, out, d, dtype)) return rc;
+    const bool bwd = grad_out && grad_F;
+    if (bwd) {
+        if (tfi_status rc = check_apply_args(plan, grad_out, grad_F, d, dtype)) return rc;
+    }
+    // everything that allocates or sets attributes happens before capture
+    WorkLists *wl = nullptr;
+    if (tfi_status rc = build_work(plan, d, &wl)) return rc;
+    if (tfi_status rc = set_attributes()) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::unique_ptr<tfi_graph_s> g(new (std::nothrow) tfi_graph_s());
+    if (!g) return fail(TFI_ERR_OOM, "host allocation failed");
+    TFI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    tfi_status rc = tfi_apply(plan, F, out, d, dtype, stream);
+    if (rc == TFI_OK && bwd) rc = tfi_apply_backward(plan, grad_out, grad_F, d, dtype, stream);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &gr);
+    if (rc != TFI_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(TFI_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+    g->graph = gr;
+    TFI_CUDA(cudaGraphInstantiate(&g->exec, gr, 0));
+    *graph = g.release();
+    return TFI_OK;
+}
+
+tfi_status tfi_graph_launch(tfi_graph_t graph, tfi_stream_t stream) {
+    if (!graph || !graph->exec) return fail(TFI_ERR_ARG, "null graph");
+    TFI_CUDA(cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
+    return TFI_OK;
+}
+
+tfi_status tfi_graph_destroy(tfi_graph_t graph) {
+    delete graph;
     return TFI_OK;
 }
 

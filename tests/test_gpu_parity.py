@@ -205,3 +205,20 @@ def test_device_keys_bit_exact(make, delta, policy):
     assert np.array_equal(dev[:, :2], host[:, :2])
     assert np.array_equal(dev[:, 2:4], host[:, 2:4])
     assert p.info()["device_keys_ms"] > 0
+
+
+def test_graph_replay_matches_apply():
+    cfg = W.configs.uneven_batch(count=25, lo=8, hi=3000, d=16)
+    t = cfg["tree"]
+    p = tfi.Plan.from_spec(t, cfg["delta"], cfg["kernel"], leaf_max=64, max_channels=16)
+    F = torch.from_numpy(W.normal_field(t.n, 16, seed=1)).cuda()
+    G = torch.from_numpy(W.normal_field(t.n, 16, seed=2)).cuda()
+    out, gF = torch.empty_like(F), torch.empty_like(F)
+    g = tfi.Graph(p, F, out, G, gF)
+    for seed in (3, 4):
+        F.copy_(torch.from_numpy(W.normal_field(t.n, 16, seed=seed)).cuda())
+        g.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(out, p.apply(F)) and torch.equal(gF, p.apply(G))
+    ref = brute.integrate(t, cfg["delta"], cfg["kernel"], F.cpu().numpy().astype(np.float64))
+    assert _err(out.cpu().numpy(), ref) <= TOL["f32"]
