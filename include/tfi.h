@@ -169,8 +169,9 @@ tfi_status tfi_apply_static(tfi_plan_t plan, const void *F, void *out, int32_t d
  * adjoint grad_F = K grad_out, with these fixed device buffers, into one
  * instantiated CUDA graph (all calls of every tree of the forest, leaf,
  * bin-sum, table and gather launches with their stream fork / join).
- * tfi_graph_launch replays it on `stream`; refill the input buffers in place
- * between launches. The plan must outlive the graph, and its workspace is
+ * Capture runs on a private stream after a device synchronisation, so
+ * `stream` of tfi_graph_create is not used. tfi_graph_launch replays the graph
+ * on `stream`; refill the input buffers in place between launches. The plan must outlive the graph, and its workspace is
  * shared with other applies of the same plan (one stream at a time). */
 typedef struct tfi_graph_s *tfi_graph_t;
 tfi_status tfi_graph_create(tfi_plan_t plan, const void *F, void *out, const void *grad_out, void *grad_F, int32_t d,

@@ -841,12 +841,21 @@ tfi_status tfi_graph_create(tfi_plan_t plan, const void *F, void *out, const voi
     WorkLists *wl = nullptr;
     if (tfi_status rc = build_work(plan, d, &wl)) return rc;
     if (tfi_status rc = set_attributes()) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // capture on a private stream (the legacy default stream cannot be captured);
+    // the instantiated graph may then be launched on any stream
+    (void)stream;
     std::unique_ptr<tfi_graph_s> g(new (std::nothrow) tfi_graph_s());
     if (!g) return fail(TFI_ERR_OOM, "host allocation failed");
+    cudaStream_t s = nullptr;
+    TFI_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } guard{s};
+    TFI_CUDA(cudaDeviceSynchronize());
     TFI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    tfi_status rc = tfi_apply(plan, F, out, d, dtype, stream);
-    if (rc == TFI_OK && bwd) rc = tfi_apply_backward(plan, grad_out, grad_F, d, dtype, stream);
+    tfi_status rc = tfi_apply(plan, F, out, d, dtype, s);
+    if (rc == TFI_OK && bwd) rc = tfi_apply_backward(plan, grad_out, grad_F, d, dtype, s);
     cudaGraph_t gr = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(s, &gr);
     if (rc != TFI_OK) {
