@@ -69,12 +69,14 @@ typedef struct {
  *   TFI_F_EXPSUM   f(x) = sum_k a_k exp(-b_k x)   params = [a_1, b_1, a_2, b_2, ...]
  *   TFI_F_GAUSS    f(x) = a exp(-c x^2)           params = [a, c]
  *   TFI_F_RATIONAL f(x) = a / (1 + c x^e)^p       params = [a, c, e, p]
+ *   TFI_F_POWEXP   f(x) = a x^p exp(-b x)          params = [a, p, b]
  *   TFI_F_TABLE    f(k delta) = table[k] for k < table_len; a plan that needs a
  *                  longer table fails with TFI_ERR_GRID_OVERFLOW. */
 #define TFI_F_TABLE    0
 #define TFI_F_EXPSUM   1
 #define TFI_F_GAUSS    2
 #define TFI_F_RATIONAL 3
+#define TFI_F_POWEXP   4
 typedef struct {
     int32_t kind;
     int32_t n_params;
@@ -178,6 +180,18 @@ tfi_status tfi_graph_create(tfi_plan_t plan, const void *F, void *out, const voi
                             int32_t dtype, tfi_stream_t stream, tfi_graph_t *graph);
 tfi_status tfi_graph_launch(tfi_graph_t graph, tfi_stream_t stream);
 tfi_status tfi_graph_destroy(tfi_graph_t graph);
+
+/* Entropic optimal transport on the tree metric (Appendix "Sinkhorn
+ * Implementation Details", Eq. "app-sinkhorn-updates"): starting from
+ * u = v = 1, repeat `iters` times
+ *     u = a / (K v + delta_reg),   v = b / (K^T u + delta_reg)
+ * with K this plan's operator (symmetric, so K^T = K). a, b, u, v: device,
+ * n x d FP32, one marginal pair per channel; u, v are overwritten with the
+ * scalings (the plan is diag(u) K diag(v) per channel). One iteration is
+ * captured once as a CUDA graph and replayed; the call synchronises `stream`.
+ * The first call allocates an n x max_channels buffer for K x. */
+tfi_status tfi_sinkhorn(tfi_plan_t plan, const float *a, const float *b, float *u, float *v, int32_t d, int32_t iters,
+                        double delta_reg, tfi_stream_t stream);
 
 /* Release everything the plan owns. NULL is accepted and ignored. */
 tfi_status tfi_destroy(tfi_plan_t plan);

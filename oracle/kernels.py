@@ -24,6 +24,9 @@ def f_of_x(spec, x: np.ndarray) -> np.ndarray:
     if spec.kind == "rational":
         a, c, e, pw = p
         return a / np.power(1.0 + c * np.power(x, e), pw)
+    if spec.kind == "powexp":
+        a, pw, b = p
+        return a * np.power(x, pw) * np.exp(-b * x)
     raise ValueError(spec.kind)
 
 

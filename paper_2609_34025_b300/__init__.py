@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libtfi.so")
 TFI_OK = 0
 _STATUS = {0: "OK", 1: "ARG", 2: "NOT_TREE", 3: "WEIGHT", 4: "GRID_OVERFLOW", 5: "OOM", 6: "CUDA", 7: "TIMEOUT",
            8: "UNSUPPORTED", 9: "NO_DEVICE"}
-KERNEL_KINDS = {"table": 0, "expsum": 1, "gauss": 2, "rational": 3}
+KERNEL_KINDS = {"table": 0, "expsum": 1, "gauss": 2, "rational": 3, "powexp": 4}
 POLICIES = {"adaptive": 0, "diameter": 1, "centroid": 2}
 DTYPE_F32, DTYPE_BF16 = 0, 1
 EXPORTS = {"calls": (0, 7), "backbone": (1, 1), "records": (2, 5), "leaves": (3, 3), "device_keys": (4, 4)}
@@ -60,7 +60,7 @@ class _Info(ctypes.Structure):
 EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_host", "tfi_destroy",
                     "tfi_plan_get_info", "tfi_plan_export", "tfi_profile_enable", "tfi_profile_read",
                     "tfi_stage_model", "tfi_apply_static", "tfi_dense_apply", "tfi_graph_create", "tfi_graph_launch",
-                    "tfi_graph_destroy", "tfi_last_error")
+                    "tfi_graph_destroy", "tfi_sinkhorn", "tfi_last_error")
 STAGES = ("leaf", "bucket", "fft", "direct", "gather")
 
 _lib = None
@@ -83,6 +83,7 @@ def lib():
         L.tfi_graph_create.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, ctypes.POINTER(vp)]
         L.tfi_graph_launch.argtypes = [vp, vp]
         L.tfi_graph_destroy.argtypes = [vp]
+        L.tfi_sinkhorn.argtypes = [vp, vp, vp, vp, vp, i32, i32, ctypes.c_double, vp]
         L.tfi_destroy.argtypes = [vp]
         L.tfi_plan_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
         L.tfi_plan_export.argtypes = [vp, i32, vp, i64, ctypes.POINTER(i64)]
@@ -178,6 +179,19 @@ class Plan:
     def dense_apply(self, F, out=None, stream=None):
         """out = K F by dense tensor-core evaluation per tree (synchronises)."""
         return self._apply(lib().tfi_dense_apply, F, out, stream)
+
+    def sinkhorn(self, a, b, iters=200, delta_reg=1e-30, stream=None):
+        """Sinkhorn scalings (u, v) for marginal pairs a, b (CUDA float32, n x d)."""
+        import torch
+
+        for t in (a, b):
+            if not t.is_cuda or t.dtype != torch.float32 or t.shape[0] != self.n or not t.is_contiguous():
+                raise ValueError("marginals must be contiguous CUDA float32 tensors of shape (n, d)")
+        u, v = torch.empty_like(a), torch.empty_like(a)
+        _check(lib().tfi_sinkhorn(self._h, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                  ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()), int(a.shape[1]),
+                                  int(iters), float(delta_reg), _stream_handle(stream)))
+        return u, v
 
     def apply_backward(self, grad_out, out=None, stream=None):
         """grad_F = K^T grad_out (= K grad_out: the operator is symmetric)."""

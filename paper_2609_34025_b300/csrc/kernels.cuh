@@ -605,6 +605,20 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
 }
 
 // ---------------------------------------------------------------------------
+// Sinkhorn scaling update (Eq. "app-sinkhorn-updates"): out = marg / (Kx + delta)
+// ---------------------------------------------------------------------------
+__global__ void sinkhorn_scale(int64_t n, const float *__restrict__ marg, const float *__restrict__ Kx, float delta,
+                               float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = marg[i] / (Kx[i] + delta);
+}
+
+__global__ void fill_value(int64_t n, float v, float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = v;
+}
+
+// ---------------------------------------------------------------------------
 // (a2) distances and bin keys on the device, at plan time.
 // Root grid distances D and hop depths by pointer doubling over the rooted
 // parent array (a prefix sum along every root path: D_{k+1}[v] = D_k[v] +

@@ -28,6 +28,8 @@ double KernelFn::grid(int64_t k, double delta) const {
             return params[0] * std::exp(-params[1] * x * x);
         case TFI_F_RATIONAL:
             return params[0] / std::pow(1.0 + params[1] * std::pow(x, params[2]), params[3]);
+        case TFI_F_POWEXP:
+            return params[0] * std::pow(x, params[1]) * std::exp(-params[2] * x);
     }
     return NAN;
 }

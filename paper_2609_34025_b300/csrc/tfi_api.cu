@@ -62,6 +62,7 @@ struct tfi_plan_s {
     float *ftab = nullptr;
     float2 *spectra = nullptr, *twiddle = nullptr;
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
+    float *sk_buf = nullptr;  // Sinkhorn: K x (n x max_channels), allocated on first use
     void *stage_in = nullptr, *stage_out = nullptr;
     int32_t *dev_rec_r = nullptr, *dev_rec_x = nullptr;  // record keys computed on the device at plan time
     // dense tensor-core evaluation (built on first use): per-tree preorder, root
@@ -724,9 +725,9 @@ tfi_status tfi_plan(const tfi_tree *tree, const tfi_kernel *kernel, const tfi_op
     if (opt->leaf_max < 1 || opt->leaf_max > tfi::kLeafMax)
         return fail(TFI_ERR_ARG, "leaf_max must be in [1, " + std::to_string(tfi::kLeafMax) + "]");
     if (opt->max_channels < 1) return fail(TFI_ERR_ARG, "max_channels must be >= 1");
-    if (kernel->kind < 0 || kernel->kind > 3) return fail(TFI_ERR_ARG, "unknown kernel kind");
+    if (kernel->kind < 0 || kernel->kind > 4) return fail(TFI_ERR_ARG, "unknown kernel kind");
     if (kernel->n_params < 0 || (kernel->n_params > 0 && !kernel->params)) return fail(TFI_ERR_ARG, "bad kernel params");
-    const int need[4] = {0, 2, 2, 4};
+    const int need[5] = {0, 2, 2, 4, 3};
     if (kernel->kind == TFI_F_EXPSUM ? (kernel->n_params < 2 || kernel->n_params % 2)
                                      : kernel->n_params != need[kernel->kind])
         return fail(TFI_ERR_ARG, "wrong number of kernel parameters");
@@ -866,6 +867,54 @@ tfi_status tfi_graph_create(tfi_plan_t plan, const void *F, void *out, const voi
     g->graph = gr;
     TFI_CUDA(cudaGraphInstantiate(&g->exec, gr, 0));
     *graph = g.release();
+    return TFI_OK;
+}
+
+tfi_status tfi_sinkhorn(tfi_plan_t plan, const float *a, const float *b, float *u, float *v, int32_t d, int32_t iters,
+                        double delta_reg, tfi_stream_t stream) {
+    if (!plan || !a || !b || !u || !v) return fail(TFI_ERR_ARG, "null argument");
+    if (iters < 0 || !(delta_reg >= 0.0)) return fail(TFI_ERR_ARG, "need iters >= 0 and delta_reg >= 0");
+    if (tfi_status rc = check_apply_args(plan, u, v, d, TFI_DTYPE_F32)) return rc;
+    const int64_t nd = int64_t(plan->hp.n) * d;
+    if (!plan->sk_buf) {
+        void *q = nullptr;
+        if (tfi_status rc = plan->alloc(&q, size_t(plan->hp.n) * size_t(plan->hp.max_channels) * 4)) return rc;
+        plan->sk_buf = static_cast<float *>(q);
+    }
+    WorkLists *wl = nullptr;
+    if (tfi_status rc = build_work(plan, d, &wl)) return rc;
+    if (tfi_status rc = set_attributes()) return rc;
+    cudaStream_t us = static_cast<cudaStream_t>(stream);
+    // u0 = v0 = 1
+    tfi::dev::fill_value<<<grid_for(nd, 256), 256, 0, us>>>(nd, 1.f, u);
+    tfi::dev::fill_value<<<grid_for(nd, 256), 256, 0, us>>>(nd, 1.f, v);
+    TFI_CUDA(cudaGetLastError());
+    if (iters == 0) return TFI_OK;
+    // one iteration (two applies, two scalings) captured once, replayed `iters` times
+    cudaStream_t s = nullptr;
+    TFI_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct Guard {
+        cudaStream_t s;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t e = nullptr;
+        ~Guard() {
+            if (e) cudaGraphExecDestroy(e);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(s);
+        }
+    } gd{s};
+    TFI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const float dl = float(delta_reg);
+    tfi_status rc = tfi_apply(plan, v, plan->sk_buf, d, TFI_DTYPE_F32, s);
+    if (rc == TFI_OK) tfi::dev::sinkhorn_scale<<<grid_for(nd, 256), 256, 0, s>>>(nd, a, plan->sk_buf, dl, u);
+    if (rc == TFI_OK) rc = tfi_apply(plan, u, plan->sk_buf, d, TFI_DTYPE_F32, s);
+    if (rc == TFI_OK) tfi::dev::sinkhorn_scale<<<grid_for(nd, 256), 256, 0, s>>>(nd, b, plan->sk_buf, dl, v);
+    const cudaError_t ce = cudaStreamEndCapture(s, &gd.g);
+    if (rc != TFI_OK) return rc;
+    if (ce != cudaSuccess) return fail(TFI_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+    TFI_CUDA(cudaGraphInstantiate(&gd.e, gd.g, 0));
+    for (int32_t it = 0; it < iters; ++it) TFI_CUDA(cudaGraphLaunch(gd.e, us));
+    TFI_CUDA(cudaStreamSynchronize(us));
     return TFI_OK;
 }
 

@@ -277,3 +277,23 @@ def test_figure1_projection_and_depth():
     assert dec["pi"][13] == gd["u_pi_backbone_index"] and dec["d"][13] == gd["u_depth"]
     anchors = [c["anchor"] for c in dec["comps"]]
     assert anchors.count(gd["shared_anchor_backbone_index"]) == 2 and len(anchors) == 4
+
+
+def test_sinkhorn_oracle_marginals_and_cost_identity():
+    # after the v update, v * (K^T u) = b exactly; at convergence u * (K v) ~ a (Eq. app-sinkhorn-updates);
+    # sum_ij u_i K_ij D_ij v_j computed from the matrices equals the f2 = x exp(-x/eps) form
+    from oracle import sinkhorn as S
+    rng = np.random.default_rng(21)
+    t = W.random_recursive(120, rng).with_weights(rng.uniform(0.05, 0.3, size=119))
+    eps, delta = 0.5, 1.0 / 64
+    K = S.dense_matrix(t, delta, W.KernelSpec.exp(1.0 / eps))
+    a, b = W.dirichlet_pairs(t.n, 3, seed=4)
+    a, b = a.astype(np.float64), b.astype(np.float64)
+    u, v = S.sinkhorn(K, a, b, 500)
+    np.testing.assert_allclose(v * (K.T @ u), b, rtol=1e-12)
+    np.testing.assert_allclose(u * (K @ v), a, rtol=1e-6)
+    adj = brute.Adjacency(t, delta)
+    D = delta * adj.dist_rows(np.arange(t.n))
+    K2 = S.dense_matrix(t, delta, W.KernelSpec.powexp(1.0 / eps))
+    direct = np.einsum("ic,ij,ij,jc->c", u, K, D, v)
+    np.testing.assert_allclose(S.transport_cost(K2, u, v), direct, rtol=1e-12)
