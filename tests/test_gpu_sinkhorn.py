@@ -1,6 +1,13 @@
 """Sinkhorn on the tree metric (Eq. app-sinkhorn-updates): the device driver
 (FP32, graph-replayed iterations) against the FP64 dense oracle, on the
-torus-MST workload recipe at a size the dense oracle handles."""
+torus-MST workload recipe at a size the dense oracle handles.
+
+Two regimes. At eps = 2 the FP64 iteration has converged after 200 steps
+(marginal residual ~1e-9), so the transport costs must agree. At eps = 0.5 it
+is still moving after 200 steps, where FP32 and FP64 trajectories may part, so
+the update rule is checked on a short trajectory instead. (FP32 represents
+exp(-x/eps) only for x < 87 eps; this tree's diameter is about 22, so the
+benchmark's eps = 0.05 truncates the FP32 kernel by construction.)"""
 import numpy as np
 import pytest
 
@@ -13,21 +20,33 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_sinkhorn_torus_mst_matches_fp64_oracle():
+def _setup(eps):
     cfg = W.configs.torus_sinkhorn(n=3000, pairs=8)
-    t, delta, eps = cfg["tree"], cfg["delta"], 0.05
+    t, delta = cfg["tree"], cfg["delta"]
+    spec = W.KernelSpec.exp(1.0 / eps)
     a, b = W.dirichlet_pairs(t.n, 8, seed=1)
-    plan = tfi.Plan.from_spec(t, delta, cfg["kernel"], leaf_max=256, max_channels=8)
+    plan = tfi.Plan.from_spec(t, delta, spec, leaf_max=256, max_channels=8)
+    return t, delta, spec, a, b, plan
+
+
+def test_sinkhorn_converged_transport_cost_matches_fp64():
+    eps = 2.0
+    t, delta, spec, a, b, plan = _setup(eps)
     u, v = plan.sinkhorn(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), iters=200)
-    K = S.dense_matrix(t, delta, cfg["kernel"])
+    K = S.dense_matrix(t, delta, spec)
     uo, vo = S.sinkhorn(K, a.astype(np.float64), b.astype(np.float64), 200)
-    # transport cost of diag(u) K diag(v): GPU applies K2 = x exp(-x/eps) with its own plan
     plan2 = tfi.Plan.from_spec(t, delta, W.KernelSpec.powexp(1.0 / eps), leaf_max=256, max_channels=8)
-    k2v = plan2.apply(v).double().cpu().numpy()
-    cost_gpu = np.einsum("ic,ic->c", u.double().cpu().numpy(), k2v)
-    K2 = S.dense_matrix(t, delta, W.KernelSpec.powexp(1.0 / eps))
-    cost_ref = S.transport_cost(K2, uo, vo)
+    cost_gpu = np.einsum("ic,ic->c", u.double().cpu().numpy(), plan2.apply(v).double().cpu().numpy())
+    cost_ref = S.transport_cost(S.dense_matrix(t, delta, W.KernelSpec.powexp(1.0 / eps)), uo, vo)
     assert np.all(np.abs(cost_gpu - cost_ref) <= 1e-3 * np.abs(cost_ref))
-    # the marginal constraint after the v update holds for the device scalings too
     ku = plan.apply(u).double().cpu().numpy()
     assert np.abs(v.double().cpu().numpy() * ku - b).max() <= 1e-4 * np.abs(b).max()
+
+
+def test_sinkhorn_update_rule_short_trajectory():
+    t, delta, spec, a, b, plan = _setup(0.5)
+    u, v = plan.sinkhorn(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), iters=10)
+    uo, vo = S.sinkhorn(S.dense_matrix(t, delta, spec), a.astype(np.float64), b.astype(np.float64), 10)
+    for got, ref in ((u, uo), (v, vo)):
+        g = got.double().cpu().numpy()
+        assert (np.abs(g - ref).max(0) / np.abs(ref).max(0)).max() <= 1e-3
