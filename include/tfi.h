@@ -94,6 +94,10 @@ typedef struct {
 #define TFI_POLICY_CENTROID 2
 
 #define TFI_PLAN_HOST_ONLY  1   /* build the decomposition on the host only (no GPU use) */
+#define TFI_PLAN_SWEEP      2   /* exponential-sum kernels only: evaluate every call's cross table
+                                   and corrections by the two backbone sweeps of Algorithm 7
+                                   ("CrossSubRoutineExp"): G_q[s] = lambda^q G_0[s],
+                                   E_alpha[q] = lambda^q E_alpha[0], O(J |V(S)|) per call */
 
 typedef struct {
     double delta;           /* grid step > 0 */
@@ -214,6 +218,7 @@ typedef struct {
     int64_t device_bytes;   /* device memory owned by the plan (without per-d work lists) */
     double plan_seconds;    /* host wall time of tfi_plan */
     double device_keys_ms;  /* device time of the plan-time distance / bin-key pass (0 host-only) */
+    int64_t n_jobs_sweep;   /* tables evaluated by exponential sweeps (TFI_PLAN_SWEEP) */
 } tfi_plan_info;
 tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
 
@@ -244,13 +249,16 @@ tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t 
  *   BUCKET  segmented bin sums of field rows (A_r[t] and b_alpha[r])
  *   FFT     cross tables / corrections by shared-memory FFT correlation
  *   DIRECT  cross tables / corrections by direct summation over occupied bins
- *   GATHER  per-vertex sum over calls of G - E, plus the leaf term, one write per row */
+ *   GATHER  per-vertex sum over calls of G - E, plus the leaf term, one write per row
+ *   SWEEP   per call, G_0 by forward and backward backbone sweeps and E_alpha[0] per
+ *           component, for each exponential term (TFI_PLAN_SWEEP plans) */
 #define TFI_STAGE_LEAF   0
 #define TFI_STAGE_BUCKET 1
 #define TFI_STAGE_FFT    2
 #define TFI_STAGE_DIRECT 3
 #define TFI_STAGE_GATHER 4
-#define TFI_N_STAGES     5
+#define TFI_STAGE_SWEEP  5   /* exponential-sum sweeps (TFI_PLAN_SWEEP plans) */
+#define TFI_N_STAGES     6
 
 /* Per-stage timing with CUDA events recorded on the apply's stream. enable != 0
  * starts recording (and clears previous totals); 0 stops. Adds two event

@@ -54,14 +54,14 @@ class _Info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "n", "n_calls", "n_leaves", "n_levels", "n_records", "n_keys", "n_jobs_fft", "n_jobs_direct",
         "n_centroid", "sum_table", "sum_fft_points", "sum_leaf_pairs", "ftab_len", "device_bytes")] + [
-        ("plan_seconds", ctypes.c_double), ("device_keys_ms", ctypes.c_double)]
+        ("plan_seconds", ctypes.c_double), ("device_keys_ms", ctypes.c_double), ("n_jobs_sweep", ctypes.c_int64)]
 
 
 EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_host", "tfi_destroy",
                     "tfi_plan_get_info", "tfi_plan_export", "tfi_profile_enable", "tfi_profile_read",
                     "tfi_stage_model", "tfi_apply_static", "tfi_dense_apply", "tfi_graph_create", "tfi_graph_launch",
                     "tfi_graph_destroy", "tfi_sinkhorn", "tfi_last_error")
-STAGES = ("leaf", "bucket", "fft", "direct", "gather")
+STAGES = ("leaf", "bucket", "fft", "direct", "gather", "sweep")
 
 _lib = None
 
@@ -124,7 +124,7 @@ class Plan:
     """A planned tree (or forest): the decomposition, f samples and spectra on the device."""
 
     def __init__(self, n, u, v, w, delta=1.0, kernel=("expsum", [1.0, 1.0]), table=None, policy="adaptive",
-                 leaf_max=64, max_channels=16, host_only=False):
+                 leaf_max=64, max_channels=16, host_only=False, sweep=False):
         u = np.ascontiguousarray(u, dtype=np.int32)
         v = np.ascontiguousarray(v, dtype=np.int32)
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -134,7 +134,8 @@ class Plan:
         tree = _Tree(int(n), int(u.shape[0]), u.ctypes.data, v.ctypes.data, w.ctypes.data)
         ker = _Kernel(KERNEL_KINDS[kind], int(params.shape[0]), params.ctypes.data if params.size else None,
                       0 if tab is None else int(tab.shape[0]), None if tab is None else tab.ctypes.data)
-        opt = _Options(float(delta), POLICIES[policy], int(leaf_max), int(max_channels), 1 if host_only else 0)
+        opt = _Options(float(delta), POLICIES[policy], int(leaf_max), int(max_channels),
+                       (1 if host_only else 0) | (2 if sweep else 0))
         h = ctypes.c_void_p()
         _check(lib().tfi_plan(ctypes.byref(tree), ctypes.byref(ker), ctypes.byref(opt), ctypes.byref(h)))
         self._h = h

@@ -605,6 +605,91 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
 }
 
 // ---------------------------------------------------------------------------
+// Exponential-sum sweeps (Algorithm 7, "CrossSubRoutineExp") for kernels
+// f(k delta) = sum_l c_l exp(-beta_l k), beta_l = b_l delta per grid unit.
+// For one term, G_q[s] = lambda^q G_0[s] and E_alpha[q] = lambda^q E_alpha[0]
+// (Eq. "stad-specialized-factorization"), so every bin value the gather reads
+// is c lambda^r times G_0 at its backbone vertex (A-bins) or E_alpha[0] (b-bins).
+// G_0[t] = sum_s lambda^{|X_t - X_s|} a_s with a_s = sum over the vertices
+// projecting to p_s of lambda^{d(v)} x_v, computed as a forward partial sum
+// Fw[t] = a_t + lambda^{X_t - X_{t-1}} Fw[t-1], a backward one Bw likewise, and
+// G_0 = Fw + Bw - a (the paper's backward update (1 - lambda^2) G + lambda G
+// rewritten as two positive recurrences; the same value in exact arithmetic).
+// ---------------------------------------------------------------------------
+struct SweepJobDev {
+    int32_t sb, se, rb, m, cjb, cje;
+};
+
+template <int WARPS>
+__global__ void sweep_g_kernel(const SweepJobDev *__restrict__ jobs, int n_jobs, const int32_t *__restrict__ key_r,
+                               const int32_t *__restrict__ key_x, const int32_t *__restrict__ sw_keys,
+                               const int32_t *__restrict__ sw_run, int d, const float *__restrict__ kbuf,
+                               float *__restrict__ vbuf, float *__restrict__ scratch, const float *__restrict__ beta,
+                               const float *__restrict__ coef, int J) {
+    const int w = blockIdx.x * WARPS + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (w >= n_jobs) return;
+    const SweepJobDev jb = jobs[w];
+    for (int c = lane; c < d; c += 32) {
+        for (int l = 0; l < J; ++l) {
+            const float b = beta[l], cl = coef[l];
+            float fw = 0.f;
+            int prev_x = 0;
+            for (int t = 0; t < jb.m; ++t) {
+                const int e0 = sw_run[jb.rb + t], e1 = sw_run[jb.rb + t + 1];
+                const int x = key_x[sw_keys[e0]];
+                float a = 0.f;
+                for (int e = e0; e < e1; ++e) {
+                    const int k = sw_keys[e];
+                    a += expf(-b * float(key_r[k])) * kbuf[int64_t(k) * d + c];
+                }
+                fw = t == 0 ? a : a + expf(-b * float(x - prev_x)) * fw;
+                scratch[(int64_t(jb.rb + t) * 2) * d + c] = fw;
+                scratch[(int64_t(jb.rb + t) * 2 + 1) * d + c] = a;
+                prev_x = x;
+            }
+            float bw = 0.f;
+            int next_x = 0;
+            for (int t = jb.m - 1; t >= 0; --t) {
+                const int e0 = sw_run[jb.rb + t], e1 = sw_run[jb.rb + t + 1];
+                const int x = key_x[sw_keys[e0]];
+                const float a = scratch[(int64_t(jb.rb + t) * 2 + 1) * d + c];
+                bw = t == jb.m - 1 ? a : a + expf(-b * float(next_x - x)) * bw;
+                const float g0 = scratch[(int64_t(jb.rb + t) * 2) * d + c] + bw - a;
+                for (int e = e0; e < e1; ++e) {
+                    const int k = sw_keys[e];
+                    const float v = cl * expf(-b * float(key_r[k])) * g0;
+                    float *dst = vbuf + int64_t(k) * d + c;
+                    *dst = l == 0 ? v : *dst + v;
+                }
+                next_x = x;
+            }
+        }
+    }
+}
+
+template <int WARPS>
+__global__ void sweep_e_kernel(const int32_t *__restrict__ ejobs, int n_jobs, const JobDev *__restrict__ jobs,
+                               const int32_t *__restrict__ key_r, int d, const float *__restrict__ kbuf,
+                               float *__restrict__ vbuf, const float *__restrict__ beta,
+                               const float *__restrict__ coef, int J) {
+    const int w = blockIdx.x * WARPS + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (w >= n_jobs) return;
+    const JobDev jb = jobs[ejobs[w]];
+    for (int c = lane; c < d; c += 32) {
+        for (int l = 0; l < J; ++l) {
+            const float b = beta[l], cl = coef[l];
+            float e0v = 0.f;   // E_alpha[0] = sum_r lambda^r b_alpha[r]
+            for (int k = jb.kb; k < jb.ke; ++k) e0v += expf(-b * float(key_r[k])) * kbuf[int64_t(k) * d + c];
+            for (int k = jb.kb; k < jb.ke; ++k) {
+                const float v = cl * expf(-b * float(key_r[k])) * e0v;
+                float *dst = vbuf + int64_t(k) * d + c;
+                *dst = l == 0 ? v : *dst + v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Sinkhorn scaling update (Eq. "app-sinkhorn-updates"): out = marg / (Kx + delta)
 // ---------------------------------------------------------------------------
 __global__ void sinkhorn_scale(int64_t n, const float *__restrict__ marg, const float *__restrict__ Kx, float delta,

@@ -522,6 +522,37 @@ int flatten(HostPlan &hp, std::string &err) {
         CallBins().kr.swap(cb.kr);
         cb = CallBins();
     });
+    if (hp.flags & TFI_PLAN_SWEEP) {
+        // Algorithm 7: every table of a call is produced by its sweep job
+        for (Job &j : hp.jobs) j.mode = 2;
+        for (size_t c = 0; c < C; ++c) {
+            const Job &g = hp.jobs[size_t(joff[c])];
+            SweepJob sj{};
+            sj.sb = int32_t(hp.sw_keys.size());
+            std::vector<int32_t> ks(size_t(g.ke - g.kb));
+            std::iota(ks.begin(), ks.end(), int32_t(g.kb));
+            std::stable_sort(ks.begin(), ks.end(), [&](int32_t a, int32_t b) {
+                return hp.key_x[size_t(a)] != hp.key_x[size_t(b)] ? hp.key_x[size_t(a)] < hp.key_x[size_t(b)]
+                                                                  : hp.key_r[size_t(a)] < hp.key_r[size_t(b)];
+            });
+            sj.rb = int32_t(hp.sw_run.size());
+            for (size_t i = 0; i < ks.size(); ++i) {
+                if (i == 0 || hp.key_x[size_t(ks[i])] != hp.key_x[size_t(ks[i - 1])])
+                    hp.sw_run.push_back(int32_t(hp.sw_keys.size()));
+                hp.sw_keys.push_back(ks[i]);
+            }
+            sj.se = int32_t(hp.sw_keys.size());
+            sj.m = int32_t(hp.sw_run.size()) - sj.rb;
+            hp.sw_run.push_back(sj.se);  // closing boundary of the last run
+            sj.cjb = int32_t(joff[c] + 1);
+            sj.cje = int32_t(joff[c + 1]);
+            hp.sweeps.push_back(sj);
+        }
+        for (size_t i = 0; i + 1 < hp.f.params.size(); i += 2) {
+            hp.sw_coef.push_back(float(hp.f.params[i]));
+            hp.sw_beta.push_back(float(hp.f.params[i + 1] * hp.delta));
+        }
+    }
     if (hp.key_vtx.size() >= size_t(INT32_MAX)) {
         err = "plan too large for 32-bit bin indices";
         return TFI_ERR_UNSUPPORTED;

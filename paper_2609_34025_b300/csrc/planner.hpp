@@ -58,13 +58,22 @@ struct Job {
     int64_t kb, ke;       // key range
     int32_t maxr, maxx;   // largest depth / coordinate among the keys
     int32_t lp1, lp2;     // log2 FFT sizes (depth, backbone)
-    int32_t mode;         // 0 = FFT, 1 = direct
+    int32_t mode;         // 0 = FFT, 1 = direct, 2 = exponential sweep (inside the call's sweep job)
     int32_t is_comp;      // 1 for a correction job
+};
+
+// Algorithm 7 job: one call. Its A-bins in sw_keys[sb, se) are grouped into m
+// runs (one per backbone vertex, ascending coordinate; within a run ascending
+// depth) with boundaries sw_run[rb .. rb+m]; its components' b-bins are the
+// jobs [cjb, cje).
+struct SweepJob {
+    int32_t sb, se, rb, m, cjb, cje;
 };
 
 struct HostPlan {
     // input
     int32_t n = 0;
+    int32_t flags = 0;
     double delta = 1.0;
     KernelFn f;
     int32_t policy = 0, leaf_max = 1, max_channels = 1;
@@ -91,6 +100,10 @@ struct HostPlan {
     std::vector<int32_t> k1_parent, k1_qpar;               // parent (self at a root) and edge length to it
     int32_t k1_maxhop = 0;                                 // largest hop depth below a root
     std::vector<int32_t> rec_anchor, rec_p1;               // per record: pi(v) and the call's p_1
+    // exponential-sum sweeps (TFI_PLAN_SWEEP)
+    std::vector<int32_t> sw_keys, sw_run;
+    std::vector<SweepJob> sweeps;
+    std::vector<float> sw_beta, sw_coef;                   // per term: decay per grid unit, coefficient
     int64_t ftab_len = 0;
     std::vector<float> ftab;
     // FFT spectra per (lp1, lp2) class, bit-reversed order, scaled by 1/(P1 P2), interleaved re/im

@@ -63,6 +63,11 @@ struct tfi_plan_s {
     float2 *spectra = nullptr, *twiddle = nullptr;
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
     float *sk_buf = nullptr;  // Sinkhorn: K x (n x max_channels), allocated on first use
+    // exponential sweeps
+    tfi::dev::SweepJobDev *sw_jobs = nullptr;
+    int32_t *sw_keys = nullptr, *sw_run = nullptr, *sw_ejobs = nullptr;
+    float *sw_beta = nullptr, *sw_coef = nullptr, *sw_scratch = nullptr;
+    int32_t n_sweeps = 0, n_sw_ejobs = 0, sw_terms = 0;
     void *stage_in = nullptr, *stage_out = nullptr;
     int32_t *dev_rec_r = nullptr, *dev_rec_x = nullptr;  // record keys computed on the device at plan time
     // dense tensor-core evaluation (built on first use): per-tree preorder, root
@@ -156,7 +161,7 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
     const auto &jobs = p->hp.jobs;
     for (size_t j = 0; j < jobs.size(); ++j) {
         const tfi::Job &jb = jobs[j];
-        if (jb.ke == jb.kb) continue;
+        if (jb.ke == jb.kb || jb.mode == 2) continue;
         if (jb.mode == 0) {
             const int lnp = jb.lp1 + jb.lp2;
             const int np = fft_pairs_per_cta(lnp, pairs);
@@ -294,6 +299,18 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
         else launch_direct<1>(p, *wl, d, s_dir);
         m_dir.done(wl->n_dir > 0 ? 1 : 0);
         TFI_CUDA(cudaEventRecord(p->ev_dir, s_dir));
+        if (p->n_sweeps > 0) {
+            StageMark m_sw(p, s, TFI_STAGE_SWEEP);
+            constexpr int WARPS = 4;
+            tfi::dev::sweep_g_kernel<WARPS><<<(p->n_sweeps + WARPS - 1) / WARPS, 32 * WARPS, 0, s>>>(
+                p->sw_jobs, p->n_sweeps, p->key_r, p->key_x, p->sw_keys, p->sw_run, d, p->kbuf, p->vbuf,
+                p->sw_scratch, p->sw_beta, p->sw_coef, p->sw_terms);
+            if (p->n_sw_ejobs > 0)
+                tfi::dev::sweep_e_kernel<WARPS><<<(p->n_sw_ejobs + WARPS - 1) / WARPS, 32 * WARPS, 0, s>>>(
+                    p->sw_ejobs, p->n_sw_ejobs, p->jobs, p->key_r, d, p->kbuf, p->vbuf, p->sw_beta, p->sw_coef,
+                    p->sw_terms);
+            m_sw.done(p->n_sw_ejobs > 0 ? 2 : 1);
+        }
         StageMark m_fft(p, s, TFI_STAGE_FFT);
         for (size_t c = 0; c < wl->fft_lnp.size(); ++c) {
             const size_t smem = size_t(wl->fft_npair[c]) * size_t(tfi::dev::padded_size(1 << wl->fft_lnp[c])) *
@@ -423,6 +440,28 @@ tfi_status upload_plan(tfi_plan_t p) {
     for (int g = 0; g < p->n_groups; ++g)
         p->max_gs = std::max(p->max_gs, hp.lgrp_ptr[size_t(g) + 1] - hp.lgrp_ptr[size_t(g)]);
     if (tfi_status rc = p->upload(&p->ftab, hp.ftab)) return rc;
+    if (!hp.sweeps.empty()) {
+        std::vector<tfi::dev::SweepJobDev> sj(hp.sweeps.size());
+        for (size_t i = 0; i < sj.size(); ++i) {
+            const tfi::SweepJob &q = hp.sweeps[i];
+            sj[i] = tfi::dev::SweepJobDev{q.sb, q.se, q.rb, q.m, q.cjb, q.cje};
+        }
+        std::vector<int32_t> ej;
+        for (size_t j = 0; j < hp.jobs.size(); ++j)
+            if (hp.jobs[j].is_comp && hp.jobs[j].ke > hp.jobs[j].kb) ej.push_back(int32_t(j));
+        if (tfi_status rc = p->upload(&p->sw_jobs, sj)) return rc;
+        if (tfi_status rc = p->upload(&p->sw_keys, hp.sw_keys)) return rc;
+        if (tfi_status rc = p->upload(&p->sw_run, hp.sw_run)) return rc;
+        if (tfi_status rc = p->upload(&p->sw_ejobs, ej)) return rc;
+        if (tfi_status rc = p->upload(&p->sw_beta, hp.sw_beta)) return rc;
+        if (tfi_status rc = p->upload(&p->sw_coef, hp.sw_coef)) return rc;
+        void *q = nullptr;
+        if (tfi_status rc = p->alloc(&q, hp.sw_run.size() * 2 * size_t(hp.max_channels) * 4)) return rc;
+        p->sw_scratch = static_cast<float *>(q);
+        p->n_sweeps = int32_t(sj.size());
+        p->n_sw_ejobs = int32_t(ej.size());
+        p->sw_terms = int32_t(hp.sw_beta.size());
+    }
     std::vector<float2> spec(hp.spectra.size() / 2), tw(hp.twiddle.size() / 2);
     std::memcpy(spec.data(), hp.spectra.data(), hp.spectra.size() * sizeof(float));
     std::memcpy(tw.data(), hp.twiddle.data(), hp.twiddle.size() * sizeof(float));
@@ -485,6 +524,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 template <typename T>
 tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
+    if (p->n_sweeps > 0) return fail(TFI_ERR_UNSUPPORTED, "tfi_apply_static does not run exponential-sweep plans");
     if (tfi_status rc = set_attributes()) return rc;
     // work lists for d, built on the host (same grouping as the plan-owned path)
     const int pairs = (d + 1) / 2;
@@ -492,7 +532,7 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
     std::vector<tfi::dev::DirItem> dir;
     for (size_t j = 0; j < p->hp.jobs.size(); ++j) {
         const tfi::Job &jb = p->hp.jobs[j];
-        if (jb.ke == jb.kb) continue;
+        if (jb.ke == jb.kb || jb.mode == 2) continue;
         if (jb.mode == 0) {
             const int lnp = jb.lp1 + jb.lp2;
             const int np = fft_pairs_per_cta(lnp, pairs);
@@ -740,6 +780,9 @@ tfi_status tfi_plan(const tfi_tree *tree, const tfi_kernel *kernel, const tfi_op
     hp.policy = opt->policy;
     hp.leaf_max = opt->leaf_max;
     hp.max_channels = opt->max_channels;
+    hp.flags = opt->flags;
+    if ((opt->flags & TFI_PLAN_SWEEP) && kernel->kind != TFI_F_EXPSUM)
+        return fail(TFI_ERR_ARG, "TFI_PLAN_SWEEP needs an exponential-sum kernel (TFI_F_EXPSUM)");
     hp.f.kind = kernel->kind;
     hp.f.params.assign(kernel->params, kernel->params + kernel->n_params);
     if (kernel->kind == TFI_F_TABLE) hp.f.table.assign(kernel->table, kernel->table + kernel->table_len);
@@ -948,8 +991,10 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info) {
         if (j.mode == 0) {
             info->n_jobs_fft++;
             info->sum_fft_points += int64_t(1) << (j.lp1 + j.lp2);
-        } else {
+        } else if (j.mode == 1) {
             info->n_jobs_direct++;
+        } else {
+            info->n_jobs_sweep++;
         }
     }
     for (const tfi::Call &c : hp.calls) {
@@ -1009,6 +1054,10 @@ tfi_status tfi_stage_model(tfi_plan_t plan, int32_t d, int32_t dtype, double *by
             kf += nk;
             // two complex transforms and one complex product per channel pair
             flops[TFI_STAGE_FFT] += std::ceil(D / 2) * (2 * 5 * np * lg + 6 * np);
+        } else if (j.mode == 2) {
+            // per term: lambda^r weighting in and out, two recurrences per backbone vertex
+            bytes[TFI_STAGE_SWEEP] += nk * (2 * D * 4 + 8);
+            flops[TFI_STAGE_SWEEP] += double(hp.sw_beta.size()) * nk * D * 6;
         } else {
             kd += nk;
             flops[TFI_STAGE_DIRECT] += 2.0 * nk * nk * D;

@@ -1,0 +1,62 @@
+"""Exponential-sum sweeps (Algorithm 7) as the table evaluator (TFI_PLAN_SWEEP),
+through the C ABI, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import brute
+
+from ._lib import tfi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _err(y, ref):
+    y = np.asarray(y, dtype=np.float64).reshape(ref.shape[0], -1)
+    return float((np.abs(y - ref).max(0) / np.maximum(np.abs(ref).max(0), 1e-300)).max())
+
+
+def _check(t, delta, spec, d, policy="adaptive", leaf_max=64, tol=1e-4, targets=None):
+    p = tfi.Plan.from_spec(t, delta, spec, policy=policy, leaf_max=leaf_max, max_channels=d, sweep=True)
+    info = p.info()
+    assert info["n_jobs_fft"] == 0 and info["n_jobs_direct"] == 0 and info["n_jobs_sweep"] >= info["n_calls"]
+    F = W.normal_field(t.n, d, seed=17)
+    y = p.apply(torch.from_numpy(F).cuda()).cpu().numpy()
+    ref = brute.integrate(t, delta, spec, F.astype(np.float64), targets=targets)
+    if targets is not None:
+        y = y[targets]
+    assert _err(y, ref) <= tol
+    return p
+
+
+@pytest.mark.parametrize("policy", ["adaptive", "diameter", "centroid"])
+@pytest.mark.parametrize("leaf_max", [1, 64])
+def test_sweep_rrt_n2000(policy, leaf_max):
+    cfg = W.configs.rrt_n2000()
+    _check(cfg["tree"], cfg["delta"], cfg["kernel"], 16, policy=policy, leaf_max=leaf_max)
+
+
+def test_sweep_grid_weights_and_long_path():
+    cfg = W.configs.sweep(shape="caterpillar", n=4096, d=4, kernel="exp")
+    _check(cfg["tree"], cfg["delta"], cfg["kernel"], 4)
+    path = W.path(5000).with_weights(np.random.default_rng(1).integers(1, 9, 4999) / 8.0)
+    _check(path, 1 / 8, W.KernelSpec.exp(0.3), 3, policy="diameter", leaf_max=1)
+
+
+def test_sweep_expsum_attention_trees():
+    cfg = W.configs.attention(heads=2)
+    for h in cfg["heads"]:
+        _check(h["tree"], 1.0, h["kernel"], 64, leaf_max=16)
+
+
+def test_sweep_full_size_sampled():
+    cfg = W.configs.sweep(shape="rrt", n=1 << 20, d=16, kernel="exp")
+    tgt = np.sort(np.random.default_rng(2).choice(cfg["tree"].n, 32, replace=False)).astype(np.int32)
+    _check(cfg["tree"], cfg["delta"], cfg["kernel"], 16, leaf_max=512, targets=tgt)
+
+
+def test_sweep_requires_expsum():
+    t = W.path(10)
+    with pytest.raises(tfi.TfiError):
+        tfi.Plan.from_spec(t, 1.0, W.KernelSpec.gauss(0.1), sweep=True)
