@@ -241,6 +241,38 @@ def dense_baseline(a, n=1 << 16, reps=5):
 
 
 # ---------------------------------------------------------------------------
+# the same exponential workload with Algorithm 7 sweeps as the table evaluator
+# ---------------------------------------------------------------------------
+def sweep_evaluator(a, cfg, F, G, steps=10):
+    import torch
+
+    import paper_2609_34025_b300 as tfi
+
+    n, d = F.shape
+    plan = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=a.policy, leaf_max=a.leaf_max,
+                              max_channels=d, sweep=True)
+    out, gF = torch.empty_like(F), torch.empty_like(F)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        plan.apply(F, out)
+        plan.apply_backward(G, gF)
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.apply(F, out)
+        plan.apply_backward(G, gF)
+        e1.record()
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / steps
+    return {"value": n * d / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "evaluator": "Algorithm 7 exponential sweeps (TFI_PLAN_SWEEP), same tree, field and kernel"}
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(a):
@@ -363,6 +395,7 @@ def run_ours(a):
     G_np = G.cpu().numpy().astype(np.float64)
     cpu = cpu_baseline(cfg, F_np, G_np, budget_s=a.cpu_budget) if a.cpu_budget > 0 else None
     dense = dense_baseline(a, n=a.dense_n) if a.dense else None
+    sweep = sweep_evaluator(a, cfg, F, G) if a.kernel == "exp" else None
     info = plan.info()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -372,7 +405,7 @@ def run_ours(a):
                                    "plan_seconds": round(plan_s, 3), "device_keys_ms": round(info["device_keys_ms"], 3), "plan_calls": info["n_calls"],
                                    "plan_leaves": info["n_leaves"], "plan_levels": info["n_levels"]}),
         "fwd_value": world * n * d / (fwd_ms / 1e3), "fwd_ms": fwd_ms,
-        "roofline": roof, "cpu_baseline": cpu, "dense_baseline": dense,
+        "roofline": roof, "cpu_baseline": cpu, "dense_baseline": dense, "sweep_evaluator": sweep,
         "e2e": {"value": world * n * d * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * n * d * 4,
                 "d2h_bytes_per_step": 2 * n * d * 4},
         "gpu_launches": int(round(sum(launches.values()) * 2 * a.steps)),
