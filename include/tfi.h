@@ -197,6 +197,31 @@ tfi_status tfi_graph_destroy(tfi_graph_t graph);
 tfi_status tfi_sinkhorn(tfi_plan_t plan, const float *a, const float *b, float *u, float *v, int32_t d, int32_t iters,
                         double delta_reg, tfi_stream_t stream);
 
+/* Gradient with respect to the kernel f (learnable kernels). out = K F is
+ * linear in the grid samples f_k = f(k delta), so for a loss L with
+ * grad_out = dL/dout:
+ *     C[k] = dL/df_k = sum over ordered pairs (u, v) with dhat(u, v) = k of <grad_out[u], F[v]>
+ * and, for the analytic kinds, dL/dtheta = sum_k (d f(k delta) / d theta) C[k]
+ * (theta in the order of tfi_kernel.params). C is computed with the plan's own
+ * decomposition: per table job a 2D FFT correlation of the bin sums of
+ * grad_out and F (channels summed in the frequency domain), per leaf its pair
+ * histogram; every sum runs in a fixed order (deterministic).
+ *   grad_out, F: device, n x d, dtype. C: device FP64 array of C_len >=
+ *   tfi_plan_info.hist_len entries, or NULL. dtheta: host FP64 array of
+ *   n_params entries, or NULL (a TFI_F_TABLE kernel has no parameters); when
+ *   given, the call synchronises `stream`. The first call allocates the
+ *   gradient workspace. Needs every table of the plan to fit one shared-memory
+ *   transform (P1 P2 <= 2^13), else TFI_ERR_UNSUPPORTED. */
+tfi_status tfi_kernel_grad(tfi_plan_t plan, const void *grad_out, const void *F, int32_t d, int32_t dtype, double *C,
+                           int64_t C_len, double *dtheta, tfi_stream_t stream);
+
+/* Replace the plan's kernel f without replanning (e.g. a training step on
+ * learnable parameters): same kind and number of parameters (or, for
+ * TFI_F_TABLE, a table at least as long as the plan needs). Recomputes the
+ * FP32 samples and the FP64 spectra on the host and copies them into the
+ * plan's device buffers (synchronous; no allocation). */
+tfi_status tfi_set_kernel(tfi_plan_t plan, const tfi_kernel *kernel);
+
 /* Release everything the plan owns. NULL is accepted and ignored. */
 tfi_status tfi_destroy(tfi_plan_t plan);
 
@@ -219,6 +244,7 @@ typedef struct {
     double plan_seconds;    /* host wall time of tfi_plan */
     double device_keys_ms;  /* device time of the plan-time distance / bin-key pass (0 host-only) */
     int64_t n_jobs_sweep;   /* tables evaluated by exponential sweeps (TFI_PLAN_SWEEP) */
+    int64_t hist_len;       /* length of the kernel-gradient histogram (1 + largest pair distance in a call) */
 } tfi_plan_info;
 tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
 

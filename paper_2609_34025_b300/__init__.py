@@ -54,13 +54,14 @@ class _Info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "n", "n_calls", "n_leaves", "n_levels", "n_records", "n_keys", "n_jobs_fft", "n_jobs_direct",
         "n_centroid", "sum_table", "sum_fft_points", "sum_leaf_pairs", "ftab_len", "device_bytes")] + [
-        ("plan_seconds", ctypes.c_double), ("device_keys_ms", ctypes.c_double), ("n_jobs_sweep", ctypes.c_int64)]
+        ("plan_seconds", ctypes.c_double), ("device_keys_ms", ctypes.c_double), ("n_jobs_sweep", ctypes.c_int64),
+        ("hist_len", ctypes.c_int64)]
 
 
 EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_host", "tfi_destroy",
                     "tfi_plan_get_info", "tfi_plan_export", "tfi_profile_enable", "tfi_profile_read",
                     "tfi_stage_model", "tfi_apply_static", "tfi_dense_apply", "tfi_graph_create", "tfi_graph_launch",
-                    "tfi_graph_destroy", "tfi_sinkhorn", "tfi_last_error")
+                    "tfi_graph_destroy", "tfi_sinkhorn", "tfi_kernel_grad", "tfi_set_kernel", "tfi_last_error")
 STAGES = ("leaf", "bucket", "fft", "direct", "gather", "sweep")
 
 _lib = None
@@ -84,6 +85,8 @@ def lib():
         L.tfi_graph_launch.argtypes = [vp, vp]
         L.tfi_graph_destroy.argtypes = [vp]
         L.tfi_sinkhorn.argtypes = [vp, vp, vp, vp, vp, i32, i32, ctypes.c_double, vp]
+        L.tfi_kernel_grad.argtypes = [vp, vp, vp, i32, i32, vp, i64, vp, vp]
+        L.tfi_set_kernel.argtypes = [vp, ctypes.POINTER(_Kernel)]
         L.tfi_destroy.argtypes = [vp]
         L.tfi_plan_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
         L.tfi_plan_export.argtypes = [vp, i32, vp, i64, ctypes.POINTER(i64)]
@@ -142,6 +145,8 @@ class Plan:
         self.n = int(n)
         self.max_channels = int(max_channels)
         self.host_only = host_only
+        self.kernel_kind = KERNEL_KINDS[kind]
+        self.n_params = 0 if kind == "table" else int(params.shape[0])
 
     @classmethod
     def from_spec(cls, tree, delta, spec, **kw):
@@ -193,6 +198,30 @@ class Plan:
                                   ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()), int(a.shape[1]),
                                   int(iters), float(delta_reg), _stream_handle(stream)))
         return u, v
+
+    def kernel_grad(self, grad_out, F, stream=None):
+        """(C, dtheta): C[k] = dL/df(k delta) (CUDA float64) and dL/dtheta (numpy) for grad_out = dL/dout."""
+        import torch
+
+        for t in (grad_out, F):
+            if not t.is_cuda or t.dim() != 2 or t.shape[0] != self.n or not t.is_contiguous():
+                raise ValueError("grad_out and F must be contiguous CUDA tensors of shape (n, d)")
+        L = self.info()["hist_len"]
+        C = torch.empty(L, dtype=torch.float64, device=grad_out.device)
+        th = np.zeros(max(1, self.n_params), dtype=np.float64)
+        _check(lib().tfi_kernel_grad(self._h, ctypes.c_void_p(grad_out.data_ptr()), ctypes.c_void_p(F.data_ptr()),
+                                     int(F.shape[1]), _dtype_code(F), ctypes.c_void_p(C.data_ptr()), L,
+                                     th.ctypes.data if self.n_params else None, _stream_handle(stream)))
+        return C, th[: self.n_params]
+
+    def set_kernel(self, params=None, table=None):
+        """Replace f's parameters (same kind and count) or its sampled table, without replanning."""
+        params = np.ascontiguousarray(params if params is not None else [], dtype=np.float64)
+        tab = None if table is None else np.ascontiguousarray(table, dtype=np.float64)
+        ker = _Kernel(self.kernel_kind, int(params.shape[0]), params.ctypes.data if params.size else None,
+                      0 if tab is None else int(tab.shape[0]), None if tab is None else tab.ctypes.data)
+        _check(lib().tfi_set_kernel(self._h, ctypes.byref(ker)))
+        self.n_params = int(params.shape[0]) if tab is None else 0
 
     def apply_backward(self, grad_out, out=None, stream=None):
         """grad_F = K^T grad_out (= K grad_out: the operator is symmetric)."""
@@ -292,7 +321,43 @@ def _autograd_fn():
     return TreeFieldIntegral
 
 
+def _learnable_fn():
+    import torch
+
+    class LearnableKernelIntegral(torch.autograd.Function):
+        """y = K_theta F with dL/dF = K_theta dL/dy and dL/dtheta = sum_k df(k delta)/dtheta C[k]."""
+
+        @staticmethod
+        def forward(ctx, F, theta, plan):
+            plan.set_kernel(params=theta.detach().double().cpu().numpy())
+            ctx.plan = plan
+            ctx.save_for_backward(F)
+            ctx.theta_dtype = theta.dtype
+            return plan.apply(F.contiguous())
+
+        @staticmethod
+        def backward(ctx, g):
+            (F,) = ctx.saved_tensors
+            g = g.contiguous()
+            dF = ctx.plan.apply_backward(g)
+            _, dth = ctx.plan.kernel_grad(g, F.contiguous())
+            return dF, torch.from_numpy(dth).to(dtype=ctx.theta_dtype), None
+
+    return LearnableKernelIntegral
+
+
 _TFI = None
+_LTFI = None
+
+
+def integrate_learnable(F, theta, plan: Plan):
+    """Differentiable in F and in the kernel parameters theta (1-D tensor in the
+    order of the plan's kernel params): sets the plan's kernel to theta, applies,
+    and back-propagates through the hand-written adjoint and kernel gradient."""
+    global _LTFI
+    if _LTFI is None:
+        _LTFI = _learnable_fn()
+    return _LTFI.apply(F, theta, plan)
 
 
 def integrate(F, plan: Plan):

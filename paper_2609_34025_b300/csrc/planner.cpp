@@ -459,6 +459,58 @@ void build_call_bins(const HostPlan &hp, const Call &call, CallBins &cb) {
     }
 }
 
+}  // namespace
+
+// Everything in a plan that depends on the values of f: FP32 grid samples, the
+// FP64-computed spectra of kappa[j][b] = f(j + min(b, P2 - b)) per FFT size
+// class (scaled by 1/(P1 P2), bit-reversed along both axes), and the terms of
+// an exponential sum for the sweeps.
+int sample_kernel(HostPlan &hp, std::string &err) {
+    if (hp.f.kind == TFI_F_TABLE && hp.hist_len > int64_t(hp.f.table.size())) {
+        err = "sampled kernel table shorter than the largest grid distance the plan needs";
+        return TFI_ERR_GRID_OVERFLOW;
+    }
+    hp.ftab.resize(size_t(hp.ftab_len));
+    for (int64_t k = 0; k < hp.ftab_len; ++k) hp.ftab[size_t(k)] = float(hp.f.grid(k, hp.delta));
+    std::vector<std::complex<double>> buf;
+    for (int cls = 0; cls < 16 * 16; ++cls) {
+        const int32_t off = hp.spec_class_off[size_t(cls)];
+        if (off < 0) continue;
+        const int lp1 = cls / 16, lp2 = cls % 16;
+        const int64_t P1 = int64_t(1) << lp1, P2 = int64_t(1) << lp2, NP = P1 * P2;
+        buf.assign(size_t(NP), 0.0);
+        for (int64_t a = 0; a < P1; ++a) {
+            for (int64_t b = 0; b < P2; ++b) {
+                double fv = hp.f.grid(a + std::min(b, P2 - b), hp.delta);
+                if (!std::isfinite(fv)) fv = 0.0;  // beyond a sampled table: never read for occupied bins
+                buf[size_t(a * P2 + b)] = fv;
+            }
+        }
+        for (int64_t a = 0; a < P1; ++a) fft64(buf.data() + a * P2, lp2, 1);
+        for (int64_t b = 0; b < P2; ++b) fft64(buf.data() + b, lp1, P2);
+        const double scale = 1.0 / double(NP);
+        for (int64_t a = 0; a < P1; ++a) {
+            for (int64_t b = 0; b < P2; ++b) {
+                const std::complex<double> sv =
+                    buf[size_t(int64_t(bitrev(uint32_t(a), lp1)) * P2 + int64_t(bitrev(uint32_t(b), lp2)))] * scale;
+                hp.spectra[size_t(off) + size_t(2 * (a * P2 + b))] = float(sv.real());
+                hp.spectra[size_t(off) + size_t(2 * (a * P2 + b) + 1)] = float(sv.imag());
+            }
+        }
+    }
+    hp.sw_coef.clear();
+    hp.sw_beta.clear();
+    if (hp.flags & TFI_PLAN_SWEEP) {
+        for (size_t i = 0; i + 1 < hp.f.params.size(); i += 2) {
+            hp.sw_coef.push_back(float(hp.f.params[i]));
+            hp.sw_beta.push_back(float(hp.f.params[i + 1] * hp.delta));
+        }
+    }
+    return TFI_OK;
+}
+
+namespace {
+
 int flatten(HostPlan &hp, std::string &err) {
     const int64_t R = int64_t(hp.recs.size());
     std::vector<int32_t> rec_akey(size_t(R), -1), rec_bkey(size_t(R), -1);
@@ -548,10 +600,6 @@ int flatten(HostPlan &hp, std::string &err) {
             sj.cje = int32_t(joff[c + 1]);
             hp.sweeps.push_back(sj);
         }
-        for (size_t i = 0; i + 1 < hp.f.params.size(); i += 2) {
-            hp.sw_coef.push_back(float(hp.f.params[i]));
-            hp.sw_beta.push_back(float(hp.f.params[i + 1] * hp.delta));
-        }
     }
     if (hp.key_vtx.size() >= size_t(INT32_MAX)) {
         err = "plan too large for 32-bit bin indices";
@@ -639,46 +687,20 @@ int flatten(HostPlan &hp, std::string &err) {
         need_any = std::max(need_any, top);
         if (j.mode == 1) need = std::max(need, top);
     }
-    if (hp.f.kind == TFI_F_TABLE && need_any >= int64_t(hp.f.table.size())) {
-        err = "sampled kernel table shorter than the largest grid distance the plan needs";
-        return TFI_ERR_GRID_OVERFLOW;
-    }
     hp.ftab_len = need + 1;
-    hp.ftab.resize(size_t(hp.ftab_len));
-    for (int64_t k = 0; k < hp.ftab_len; ++k) hp.ftab[size_t(k)] = float(hp.f.grid(k, hp.delta));
-    // kernel spectra per FFT class: kappa[j][b] = f(j + min(b, P2 - b)); 2D DFT in FP64,
-    // scaled by 1/(P1 P2), stored in bit-reversed order along both axes
+    hp.hist_len = std::max(need_any, need_leaf) + 1;
+    // FFT size classes in first-use order; their spectra depend on f
     hp.spec_class_off.assign(16 * 16, -1);
-    std::vector<std::complex<double>> buf;
+    int32_t off = 0;
     for (const Job &j : hp.jobs) {
         if (j.mode != 0) continue;
         const int cls = j.lp1 * 16 + j.lp2;
         if (hp.spec_class_off[size_t(cls)] >= 0) continue;
-        const int64_t P1 = int64_t(1) << j.lp1, P2 = int64_t(1) << j.lp2, NP = P1 * P2;
-        buf.assign(size_t(NP), 0.0);
-        for (int64_t a = 0; a < P1; ++a) {
-            for (int64_t b = 0; b < P2; ++b) {
-                const int64_t k = a + std::min(b, P2 - b);
-                double fv = hp.f.grid(k, hp.delta);
-                if (!std::isfinite(fv)) fv = 0.0;  // beyond a sampled table: never read for occupied bins
-                buf[size_t(a * P2 + b)] = fv;
-            }
-        }
-        for (int64_t a = 0; a < P1; ++a) fft64(buf.data() + a * P2, j.lp2, 1);
-        for (int64_t b = 0; b < P2; ++b) fft64(buf.data() + b, j.lp1, P2);
-        hp.spec_class_off[size_t(cls)] = int32_t(hp.spectra.size());
-        const size_t off = hp.spectra.size();
-        hp.spectra.resize(off + size_t(2 * NP));
-        const double scale = 1.0 / double(NP);
-        for (int64_t a = 0; a < P1; ++a) {
-            for (int64_t b = 0; b < P2; ++b) {
-                const std::complex<double> s =
-                    buf[size_t(int64_t(bitrev(uint32_t(a), j.lp1)) * P2 + int64_t(bitrev(uint32_t(b), j.lp2)))] * scale;
-                hp.spectra[off + size_t(2 * (a * P2 + b))] = float(s.real());
-                hp.spectra[off + size_t(2 * (a * P2 + b) + 1)] = float(s.imag());
-            }
-        }
+        hp.spec_class_off[size_t(cls)] = off;
+        off += int32_t(2) << (j.lp1 + j.lp2);
     }
+    hp.spectra.assign(size_t(off), 0.f);
+    if (int rc = sample_kernel(hp, err)) return rc;
     // compact per-level twiddles: twiddle[h + o] = exp(-2 pi i o / (8 h)) for h = 2^L, o < h
     const int64_t tw = int64_t(1) << kTwLog;
     hp.twiddle.assign(size_t(2 * tw), 0.f);

@@ -105,6 +105,7 @@ struct HostPlan {
     std::vector<SweepJob> sweeps;
     std::vector<float> sw_beta, sw_coef;                   // per term: decay per grid unit, coefficient
     int64_t ftab_len = 0;
+    int64_t hist_len = 0;                                  // 1 + largest grid distance any pair of a call can have
     std::vector<float> ftab;
     // FFT spectra per (lp1, lp2) class, bit-reversed order, scaled by 1/(P1 P2), interleaved re/im
     std::vector<int32_t> spec_class_off;                   // [lp1 * 16 + lp2] -> offset in floats (complex = 2)
@@ -118,6 +119,10 @@ constexpr int kFftMaxLog = 14;
 constexpr int kLeafMax = 1024;        // largest dense leaf (shared-memory sparse table)
 constexpr int kLeafGroup = 256;       // small leaves are packed into groups of <= this many vertices
 constexpr int64_t kGridMax = int64_t(1) << 30;
+
+// Recompute the f-dependent parts of a built plan (samples, spectra, sweep
+// terms) from hp.f. Returns 0 or a TFI_ERR_* code with a message.
+int sample_kernel(HostPlan &hp, std::string &err);
 
 // Returns 0 or a TFI_ERR_* code with a message.
 int build_plan(HostPlan &hp, int32_t n, int32_t m, const int32_t *u, const int32_t *v, const double *w,

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "dense_tc.cuh"
+#include "grad.cuh"
 #include "kernels.cuh"
 #include "planner.hpp"
 #include "tfi.h"
@@ -63,6 +64,14 @@ struct tfi_plan_s {
     float2 *spectra = nullptr, *twiddle = nullptr;
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
     float *sk_buf = nullptr;  // Sinkhorn: K x (n x max_channels), allocated on first use
+    // kernel gradient (built on first use)
+    bool grad_ready = false;
+    int32_t n_gjobs = 0, n_gleaves = 0, n_gseg = 0, g_max_lnp = 0;
+    tfi::grad::GradJob *g_jobs = nullptr;
+    int32_t *g_leaf_ptr = nullptr, *g_hist_len = nullptr, *g_seg_len = nullptr, *g_pdst = nullptr;
+    int64_t *g_pair_off = nullptr, *g_hist_off = nullptr, *g_seg_off = nullptr;
+    float *g_seg_sign = nullptr, *g_hist = nullptr, *g_pval = nullptr, *g_gbuf = nullptr;
+    double *g_C = nullptr, *g_params = nullptr, *g_dtheta = nullptr;
     // exponential sweeps
     tfi::dev::SweepJobDev *sw_jobs = nullptr;
     int32_t *sw_keys = nullptr, *sw_run = nullptr, *sw_ejobs = nullptr;
@@ -76,6 +85,7 @@ struct tfi_plan_s {
     int32_t dense_trees = 0, dense_levels = 0, dense_max_tree = 0;
     int32_t *dn_tree_ptr = nullptr, *dn_vtx = nullptr, *dn_dist = nullptr, *dn_st = nullptr, *dn_err = nullptr;
     float *dn_ftab = nullptr;
+    int64_t dense_ftab_len = 0;
     std::vector<int32_t> dn_tree_ptr_h;
     double device_keys_ms = 0.0;
     std::map<int, WorkLists> work;  // per channel count d
@@ -441,6 +451,7 @@ tfi_status upload_plan(tfi_plan_t p) {
         p->max_gs = std::max(p->max_gs, hp.lgrp_ptr[size_t(g) + 1] - hp.lgrp_ptr[size_t(g)]);
     if (tfi_status rc = p->upload(&p->ftab, hp.ftab)) return rc;
     if (!hp.sweeps.empty()) {
+        if (hp.sw_beta.empty()) return fail(TFI_ERR_ARG, "exponential-sweep plan without exponential terms");
         std::vector<tfi::dev::SweepJobDev> sj(hp.sweeps.size());
         for (size_t i = 0; i < sj.size(); ++i) {
             const tfi::SweepJob &q = hp.sweeps[i];
@@ -697,6 +708,7 @@ tfi_status build_dense(tfi_plan_t p) {
     if (tfi_status rc = p->upload(&p->dn_vtx, vtx)) return rc;
     if (tfi_status rc = p->upload(&p->dn_dist, dist)) return rc;
     if (tfi_status rc = p->upload(&p->dn_ftab, ftab)) return rc;
+    p->dense_ftab_len = int64_t(ftab.size());
     void *st = nullptr, *errp = nullptr;
     if (tfi_status rc = p->alloc(&st, size_t(levels) * size_t(n) * 4)) return rc;
     if (tfi_status rc = p->alloc(&errp, 16)) return rc;
@@ -743,6 +755,116 @@ tfi_status dense_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     if (err) {
         cudaMemset(p->dn_err, 0, 4);
         return fail(TFI_ERR_TIMEOUT, "a tensor-core completion wait gave up");
+    }
+    return TFI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel gradient
+// ---------------------------------------------------------------------------
+tfi_status build_grad(tfi_plan_t p) {
+    if (p->grad_ready) return TFI_OK;
+    const tfi::HostPlan &hp = p->hp;
+    std::vector<tfi::grad::GradJob> gj;
+    std::vector<int64_t> seg_off;
+    std::vector<int32_t> seg_len;
+    std::vector<float> seg_sign;
+    int64_t hoff = 0;
+    int max_lnp = 0;
+    for (const tfi::Job &j : hp.jobs) {
+        if (j.ke == j.kb) continue;
+        if (j.lp1 + j.lp2 > 13)
+            return fail(TFI_ERR_UNSUPPORTED, "kernel gradient needs every table to fit one shared-memory transform (P1 P2 <= 2^13)");
+        const int32_t len = 2 * j.maxr + j.maxx + 1;
+        gj.push_back(tfi::grad::GradJob{int32_t(j.kb), int32_t(j.ke), j.lp1, j.lp2, j.maxr, j.maxx, hoff});
+        seg_off.push_back(hoff);
+        seg_len.push_back(len);
+        seg_sign.push_back(j.is_comp ? -1.f : 1.f);
+        hoff += len;
+        max_lnp = std::max(max_lnp, j.lp1 + j.lp2);
+    }
+    std::vector<int32_t> leaf_ptr(1, 0), hist_len;
+    std::vector<int64_t> pair_off, hist_off;
+    int64_t poff = 0;
+    for (const tfi::Leaf &lf : hp.leaves) {
+        const int64_t sz = lf.end - lf.begin;
+        leaf_ptr.push_back(int32_t(lf.end));
+        pair_off.push_back(poff);
+        poff += sz * sz;
+        hist_off.push_back(hoff);
+        hist_len.push_back(int32_t(lf.diam + 1));
+        seg_off.push_back(hoff);
+        seg_len.push_back(int32_t(lf.diam + 1));
+        seg_sign.push_back(1.f);
+        hoff += lf.diam + 1;
+    }
+    if (tfi_status rc = p->upload(&p->g_jobs, gj)) return rc;
+    if (tfi_status rc = p->upload(&p->g_leaf_ptr, leaf_ptr)) return rc;
+    if (tfi_status rc = p->upload(&p->g_pair_off, pair_off)) return rc;
+    if (tfi_status rc = p->upload(&p->g_hist_off, hist_off)) return rc;
+    if (tfi_status rc = p->upload(&p->g_hist_len, hist_len)) return rc;
+    if (tfi_status rc = p->upload(&p->g_seg_off, seg_off)) return rc;
+    if (tfi_status rc = p->upload(&p->g_seg_len, seg_len)) return rc;
+    if (tfi_status rc = p->upload(&p->g_seg_sign, seg_sign)) return rc;
+    void *q = nullptr;
+    if (tfi_status rc = p->alloc(&q, size_t(std::max<int64_t>(hoff, 1)) * 4)) return rc;
+    p->g_hist = static_cast<float *>(q);
+    if (tfi_status rc = p->alloc(&q, size_t(std::max<int64_t>(poff, 1)) * 4)) return rc;
+    p->g_pval = static_cast<float *>(q);
+    if (tfi_status rc = p->alloc(&q, size_t(std::max<int64_t>(poff, 1)) * 4)) return rc;
+    p->g_pdst = static_cast<int32_t *>(q);
+    if (tfi_status rc = p->alloc(&q, std::max<size_t>(1, hp.key_r.size()) * size_t(hp.max_channels) * 4)) return rc;
+    p->g_gbuf = static_cast<float *>(q);
+    if (tfi_status rc = p->alloc(&q, size_t(hp.hist_len) * 8)) return rc;
+    p->g_C = static_cast<double *>(q);
+    if (tfi_status rc = p->alloc(&q, std::max<size_t>(1, hp.f.params.size()) * 8 * 2)) return rc;
+    p->g_params = static_cast<double *>(q);
+    p->g_dtheta = p->g_params + std::max<size_t>(1, hp.f.params.size());
+    p->n_gjobs = int32_t(gj.size());
+    p->n_gleaves = int32_t(hp.leaves.size());
+    p->n_gseg = int32_t(seg_off.size());
+    p->g_max_lnp = max_lnp;
+    p->grad_ready = true;
+    return TFI_OK;
+}
+
+template <typename T>
+tfi_status kernel_grad_impl(tfi_plan_t p, const T *G, const T *F, int d, double *C, double *dtheta, cudaStream_t s) {
+    if (tfi_status rc = build_grad(p)) return rc;
+    const tfi::HostPlan &hp = p->hp;
+    const int64_t n_keys = int64_t(hp.key_r.size());
+    if (n_keys > 0) {
+        tfi::dev::bucket_kernel<T, 1><<<grid_for(n_keys * d, 256), 256, 0, s>>>(n_keys, p->key_ptr, p->key_vtx, G, d,
+                                                                                p->g_gbuf);
+        tfi::dev::bucket_kernel<T, 1><<<grid_for(n_keys * d, 256), 256, 0, s>>>(n_keys, p->key_ptr, p->key_vtx, F, d,
+                                                                                p->kbuf);
+    }
+    if (p->n_gjobs > 0) {
+        const size_t smem = 2 * size_t(tfi::dev::padded_size(1 << p->g_max_lnp)) * sizeof(float2);
+        TFI_CUDA(cudaFuncSetAttribute(tfi::grad::grad_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(std::max<size_t>(smem, 1024))));
+        tfi::grad::grad_fft_kernel<<<p->n_gjobs, 256, smem, s>>>(p->g_jobs, p->key_r, p->key_x, d, p->g_gbuf, p->kbuf,
+                                                                 p->twiddle, p->g_hist);
+    }
+    if (p->n_gleaves > 0) {
+        tfi::grad::grad_leaf_pairs<T><<<p->n_gleaves, 256, 0, s>>>(p->g_leaf_ptr, p->g_pair_off, p->leaf_vtx,
+                                                                    p->leaf_dist, p->leaf_pdist, G, F, d, p->g_pval,
+                                                                    p->g_pdst);
+        tfi::grad::grad_leaf_hist<<<p->n_gleaves, 128, 0, s>>>(p->g_leaf_ptr, p->g_pair_off, p->g_hist_off,
+                                                               p->g_hist_len, p->g_pval, p->g_pdst, p->g_hist);
+    }
+    double *Cd = C ? C : p->g_C;
+    tfi::grad::grad_reduce<<<grid_for(hp.hist_len, 256), 256, 0, s>>>(p->n_gseg, p->g_seg_off, p->g_seg_len,
+                                                                       p->g_seg_sign, p->g_hist, hp.hist_len, Cd);
+    TFI_CUDA(cudaGetLastError());
+    if (dtheta && hp.f.kind != TFI_F_TABLE && !hp.f.params.empty()) {
+        const int np = int(hp.f.params.size());
+        TFI_CUDA(cudaMemcpyAsync(p->g_params, hp.f.params.data(), size_t(np) * 8, cudaMemcpyHostToDevice, s));
+        tfi::grad::grad_params<<<np, 256, 0, s>>>(hp.f.kind, p->g_params, np, hp.delta, Cd, hp.hist_len,
+                                                  p->g_dtheta);
+        TFI_CUDA(cudaGetLastError());
+        TFI_CUDA(cudaMemcpyAsync(dtheta, p->g_dtheta, size_t(np) * 8, cudaMemcpyDeviceToHost, s));
+        TFI_CUDA(cudaStreamSynchronize(s));
     }
     return TFI_OK;
 }
@@ -961,6 +1083,58 @@ tfi_status tfi_sinkhorn(tfi_plan_t plan, const float *a, const float *b, float *
     return TFI_OK;
 }
 
+tfi_status tfi_kernel_grad(tfi_plan_t plan, const void *grad_out, const void *F, int32_t d, int32_t dtype, double *C,
+                           int64_t C_len, double *dtheta, tfi_stream_t stream) {
+    if (!grad_out || !F) return fail(TFI_ERR_ARG, "null field pointer");
+    if (tfi_status rc = check_apply_args(plan, grad_out, F, d, dtype)) return rc;
+    if (C && C_len < plan->hp.hist_len) return fail(TFI_ERR_ARG, "C_len shorter than tfi_plan_info.hist_len");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dtype == TFI_DTYPE_F32)
+        return kernel_grad_impl<float>(plan, static_cast<const float *>(grad_out), static_cast<const float *>(F), d, C,
+                                       dtheta, s);
+    return kernel_grad_impl<__nv_bfloat16>(plan, static_cast<const __nv_bfloat16 *>(grad_out),
+                                           static_cast<const __nv_bfloat16 *>(F), d, C, dtheta, s);
+}
+
+tfi_status tfi_set_kernel(tfi_plan_t plan, const tfi_kernel *kernel) {
+    if (!plan || !kernel) return fail(TFI_ERR_ARG, "null argument");
+    tfi::HostPlan &hp = plan->hp;
+    if (kernel->kind != hp.f.kind) return fail(TFI_ERR_ARG, "kernel kind differs from the plan's");
+    if (kernel->kind == TFI_F_TABLE) {
+        if (!kernel->table || kernel->table_len < hp.hist_len) return fail(TFI_ERR_ARG, "table too short");
+    } else if (kernel->n_params != int32_t(hp.f.params.size()) || !kernel->params) {
+        return fail(TFI_ERR_ARG, "number of kernel parameters differs from the plan's");
+    }
+    tfi::KernelFn old = hp.f;
+    hp.f.params.assign(kernel->params, kernel->params + kernel->n_params);
+    if (kernel->kind == TFI_F_TABLE) hp.f.table.assign(kernel->table, kernel->table + kernel->table_len);
+    std::string err;
+    if (int rc = tfi::sample_kernel(hp, err)) {
+        hp.f = old;
+        std::string e2;
+        tfi::sample_kernel(hp, e2);
+        return fail(rc, err);
+    }
+    if (plan->on_device) {
+        if (!hp.ftab.empty())
+            TFI_CUDA(cudaMemcpy(plan->ftab, hp.ftab.data(), hp.ftab.size() * 4, cudaMemcpyHostToDevice));
+        if (!hp.spectra.empty())
+            TFI_CUDA(cudaMemcpy(plan->spectra, hp.spectra.data(), hp.spectra.size() * 4, cudaMemcpyHostToDevice));
+        if (!hp.sw_beta.empty()) {
+            TFI_CUDA(cudaMemcpy(plan->sw_beta, hp.sw_beta.data(), hp.sw_beta.size() * 4, cudaMemcpyHostToDevice));
+            TFI_CUDA(cudaMemcpy(plan->sw_coef, hp.sw_coef.data(), hp.sw_coef.size() * 4, cudaMemcpyHostToDevice));
+        }
+        if (plan->dense_ready) {
+            // dense f samples cover the largest tree diameter
+            const size_t nd = size_t(plan->dense_ftab_len);
+            std::vector<float> ft(nd);
+            for (size_t k = 0; k < nd; ++k) ft[k] = float(hp.f.grid(int64_t(k), hp.delta));
+            TFI_CUDA(cudaMemcpy(plan->dn_ftab, ft.data(), nd * 4, cudaMemcpyHostToDevice));
+        }
+    }
+    return TFI_OK;
+}
+
 tfi_status tfi_graph_launch(tfi_graph_t graph, tfi_stream_t stream) {
     if (!graph || !graph->exec) return fail(TFI_ERR_ARG, "null graph");
     TFI_CUDA(cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
@@ -1006,6 +1180,7 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info) {
     info->device_bytes = plan->dev_bytes;
     info->plan_seconds = hp.plan_seconds;
     info->device_keys_ms = plan->device_keys_ms;
+    info->hist_len = hp.hist_len;
     return TFI_OK;
 }
 

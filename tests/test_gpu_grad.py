@@ -1,0 +1,87 @@
+"""Gradient with respect to the kernel (learnable f), through the C ABI,
+against the FP64 oracle's distance-binned correlation and its parameter
+gradient (itself pinned by finite differences in the oracle tests)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import brute
+
+from ._lib import tfi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _nerr(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _grad_case(t, delta, spec, d, leaf_max, policy="adaptive", dtype=torch.float32, tol=1e-4):
+    p = tfi.Plan.from_spec(t, delta, spec, policy=policy, leaf_max=leaf_max, max_channels=d)
+    G = torch.from_numpy(W.normal_field(t.n, d, seed=31)).cuda().to(dtype)
+    F = torch.from_numpy(W.normal_field(t.n, d, seed=32)).cuda().to(dtype)
+    C, dth = p.kernel_grad(G, F)
+    Gn, Fn = G.double().cpu().numpy(), F.double().cpu().numpy()
+    ref = brute.corr_hist(t, delta, Gn, Fn)
+    c = C.cpu().numpy()
+    # the plan's histogram may extend past the largest pair distance (those bins hold only round-off)
+    assert len(c) >= len(ref)
+    ref = np.concatenate([ref, np.zeros(len(c) - len(ref))])
+    assert _nerr(c, ref) <= tol
+    if spec.kind == "expsum":
+        assert _nerr(dth, brute.kernel_param_grad(t, delta, spec, Gn, Fn)) <= tol
+    return p
+
+
+@pytest.mark.parametrize("leaf_max", [1, 16, 256])
+@pytest.mark.parametrize("policy", ["adaptive", "centroid"])
+def test_grad_rrt_n2000(leaf_max, policy):
+    cfg = W.configs.rrt_n2000()
+    _grad_case(cfg["tree"], cfg["delta"], W.KernelSpec.expsum([0.5, -0.2], [0.3, 0.05]), 16, leaf_max, policy)
+
+
+def test_grad_attention_heads_fp32_and_bf16():
+    cfg = W.configs.attention(heads=2)
+    for h in cfg["heads"]:
+        _grad_case(h["tree"], 1.0, h["kernel"], 64, 256)
+        _grad_case(h["tree"], 1.0, h["kernel"], 64, 16, dtype=torch.bfloat16, tol=1e-2)
+
+
+def test_grad_weighted_grid_forest():
+    cfg = W.configs.uneven_batch(count=10, lo=20, hi=800, d=8)
+    _grad_case(cfg["tree"], cfg["delta"], W.KernelSpec.rational(0.1, e=1.0, p=2.0), 8, 32)
+
+
+def test_grad_rejects_tables_beyond_one_transform():
+    cfg = W.configs.rrt_n2000()
+    p = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy="diameter", leaf_max=1, max_channels=4)
+    x = torch.zeros(cfg["tree"].n, 4, device="cuda")
+    z = torch.zeros_like(x)
+    with pytest.raises(tfi.TfiError) as e:
+        p.kernel_grad(x, z)
+    assert e.value.name == "UNSUPPORTED"
+
+
+def test_set_kernel_and_learnable_autograd():
+    cfg = W.configs.attention(heads=1)
+    h = cfg["heads"][0]
+    t = h["tree"]
+    p = tfi.Plan.from_spec(t, 1.0, h["kernel"], leaf_max=64, max_channels=32)
+    theta = torch.tensor(h["kernel"].params, dtype=torch.float64, requires_grad=True)
+    F = torch.from_numpy(W.normal_field(t.n, 32, seed=5)).cuda().requires_grad_(True)
+    y = tfi.integrate_learnable(F, theta, p)
+    g = torch.from_numpy(W.normal_field(t.n, 32, seed=6)).cuda()
+    (y * g).sum().backward()
+    spec = W.KernelSpec("expsum", list(h["kernel"].params))
+    Fn, gn = F.detach().double().cpu().numpy(), g.double().cpu().numpy()
+    assert _nerr(theta.grad.numpy(), brute.kernel_param_grad(t, 1.0, spec, gn, Fn)) <= 1e-4
+    assert _nerr(F.grad.cpu().numpy(), brute.integrate(t, 1.0, spec, gn)) <= 1e-4
+    # a new kernel without replanning
+    new = list(h["kernel"].params)
+    new[0] *= -2.0
+    new[3] *= 1.5
+    p.set_kernel(params=new)
+    y2 = p.apply(F.detach()).cpu().numpy()
+    assert _nerr(y2, brute.integrate(t, 1.0, W.KernelSpec("expsum", new), Fn)) <= 1e-4
