@@ -331,9 +331,8 @@ def run_ours(a):
     step_ms = [s.elapsed_time(e) for s, e in ev]
     total_ms = sum(step_ms)
     if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+        from paper_2609_34025_b300.dist import max_over_ranks
+        total_ms = max_over_ranks(total_ms, device="cuda")
         dist.barrier()
     value = world * n * d * a.steps / (total_ms / 1e3)
     # forward only
@@ -358,9 +357,8 @@ def run_ours(a):
         plan.apply_host_ptr(Gh.data_ptr(), Qh.data_ptr(), d)
     e2e_s = time.perf_counter() - e2e_t0
     if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+        from paper_2609_34025_b300.dist import max_over_ranks
+        e2e_s = max_over_ranks(e2e_s, device="cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
