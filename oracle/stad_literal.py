@@ -170,7 +170,8 @@ def choose_backbone(g: Graph, S: set, policy: str = "adaptive"):
 
 
 # ---------------------------------------------------------------------------
-# Eq. "sumofFFTterms" evaluators: direct loop, Algorithm 2, Algorithm 3
+# Eq. "sumofFFTterms" evaluators: direct loop, Algorithm 2, Algorithm 3, and
+# the Hankel-matrix product with antidiagonal prefix sums
 # ---------------------------------------------------------------------------
 
 def compute_g_direct(A: np.ndarray, fv: np.ndarray) -> np.ndarray:
@@ -222,6 +223,47 @@ def compute_g_2dfft(A: np.ndarray, fv: np.ndarray) -> np.ndarray:
     return Y[H: 2 * H + 1, W - 1: 2 * W - 1]           # G_q[s] = Y[q + H, s + W - 1]
 
 
+def _left_offsets(B: np.ndarray, H1: int) -> np.ndarray:
+    """L_q[s] = sum_{t <= s} B[q + s - t, t]: every term lies on the
+    antidiagonal sigma = l + t = q + s, so an inclusive running sum over t
+    along each antidiagonal, read at t = s, gives it."""
+    nl, W = B.shape[:2]
+    out = np.zeros((H1, W) + B.shape[2:])
+    for sigma in range(nl + W - 1):
+        run = np.zeros(B.shape[2:])
+        for t in range(W):
+            l = sigma - t
+            if l < 0:
+                break
+            if l < nl:
+                run = run + B[l, t]
+            q = sigma - t  # reading at s = t
+            if q < H1:
+                out[q, t] = run
+    return out
+
+
+def compute_g_hankel(A: np.ndarray, fv: np.ndarray) -> np.ndarray:
+    """Attention-width evaluation of Eq. "sumofFFTterms" (appendix on the
+    cross term at attention width): with l = q + |s - t| the kernel argument
+    is l + r, so first the depth correlation B[l, t] = sum_r f(l + r) A_r[t]
+    for l = 0 .. H + m - 1 as ONE matrix product with the Hankel matrix
+    F[l, r] = f(l + r) of shape (H + m) x (H + 1) and A reshaped to
+    (H + 1) x (m d); then G_q[s] = sum_t B[q + |s - t|, t] split at t = s into
+    a left part (prefix sums along antidiagonals), a right part (the same on
+    the reversed backbone) and minus B[q, s], counted in both.
+
+    A: (H+1, m, d) aggregates. fv: f at grid distances 0 .. >= 2H + m - 1.
+    """
+    H1, W, d = A.shape
+    nl = H1 - 1 + W
+    Fh = fv[np.arange(nl)[:, None] + np.arange(H1)[None, :]]          # Hankel: depends on l + r only
+    B = (Fh @ A.reshape(H1, W * d)).reshape(nl, W, d)                  # one GEMM for all t and channels
+    left = _left_offsets(B, H1)
+    right = _left_offsets(B[:, ::-1], H1)[:, ::-1]                     # reversed backbone direction
+    return left + right - B[:H1]
+
+
 def compute_e_fft(b: np.ndarray, fv: np.ndarray) -> np.ndarray:
     """E[q] = sum_{r>=1} f(q + r) b[r], q = 0..H_alpha, by a zero-padded 1D FFT
     after reversing the profile (Algorithm 4, correction step). b[0] = 0."""
@@ -252,6 +294,8 @@ def cross_subroutine(dec, x: np.ndarray, fv: np.ndarray, evaluator: str = "fft2d
         G = compute_g_2dfft(A, fv)
     elif evaluator == "fft1d":
         G = compute_g_1d(A, fv)
+    elif evaluator == "hankel":
+        G = compute_g_hankel(A, fv)
     else:
         G = compute_g_direct(A, fv)
     cross = {}

@@ -166,6 +166,37 @@ def test_g_evaluators_agree_with_quadruple_loop():
         Gd = L.compute_g_direct(A, fv)
         np.testing.assert_allclose(L.compute_g_1d(A, fv), Gd, rtol=1e-12, atol=1e-12)
         np.testing.assert_allclose(L.compute_g_2dfft(A, fv), Gd, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(L.compute_g_hankel(A, fv), Gd, rtol=1e-12, atol=1e-12)
+
+
+def test_g_hankel_growing_kernel_and_shapes():
+    # Hankel-matrix evaluation of Eq. sumofFFTterms against the quadruple loop, including a growing
+    # kernel (the appendix reports agreement to ~1e-15 for those too), a path (H = 0, a Toeplitz
+    # product), a single column (m = 1, a Hankel product) and tall / wide tables
+    rng = np.random.default_rng(114)
+    for H1, Wd in [(1, 1), (1, 12), (9, 1), (2, 16), (13, 3), (7, 7)]:
+        A = rng.standard_normal((H1, Wd, 3))
+        for fv in (np.exp(0.3 * np.arange(2 * H1 + Wd + 2)), rng.standard_normal(2 * H1 + Wd + 2)):
+            Gd = L.compute_g_direct(A, fv)
+            Gh = L.compute_g_hankel(A, fv)
+            assert np.abs(Gh - Gd).max() <= 1e-13 * np.abs(Gd).max()
+    # m = 1: G = F A with F[q, r] = f(q + r) exactly (no offsets)
+    A = rng.standard_normal((6, 1, 2))
+    fv = rng.standard_normal(16)
+    Fh = np.array([[fv[q + r] for r in range(6)] for q in range(6)])
+    np.testing.assert_allclose(L.compute_g_hankel(A, fv)[:, 0], Fh @ A[:, 0], rtol=1e-13, atol=1e-13)
+
+
+def test_literal_stad_hankel_equals_brute():
+    rng = np.random.default_rng(115)
+    spec = W.KernelSpec.expsum([0.7, -0.2], [0.3, 0.05])
+    for t in (W.random_recursive(120, rng), W.grid_spanning_tree(8, 8, rng), W.caterpillar_leaves(15)):
+        t = t.with_weights(W.trees.integer_weights(t.m, 1, 3, rng))
+        x = rng.standard_normal((t.n, 2))
+        for policy in ("adaptive", "diameter"):
+            w, _ = L.solve(t, 1.0, spec, x, policy=policy, evaluator="hankel")
+            ref = brute.integrate(t, 1.0, spec, x)
+            assert np.abs(w - ref).max() <= 1e-11 * np.abs(ref).max()
 
 
 def test_caterpillar_closed_form():
