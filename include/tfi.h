@@ -98,6 +98,14 @@ typedef struct {
                                    and corrections by the two backbone sweeps of Algorithm 7
                                    ("CrossSubRoutineExp"): G_q[s] = lambda^q G_0[s],
                                    E_alpha[q] = lambda^q E_alpha[0], O(J |V(S)|) per call */
+#define TFI_PLAN_HANKEL     4   /* also consider the Hankel-matrix evaluator of the cross table
+                                   (attention-width evaluation of Eq. "sumofFFTterms"): B = Fh A
+                                   on tensor cores with Fh[l][r] = f(l + r), then prefix sums
+                                   along antidiagonals. A job qualifies when H + 1 <= 64 and
+                                   H + L + 1 <= 128 (grid units); it is chosen when the
+                                   channel-aware cost model (at max_channels) ranks it below
+                                   direct summation and the FFT */
+#define TFI_PLAN_HANKEL_ALL 8   /* every qualifying job uses the Hankel evaluator */
 
 typedef struct {
     double delta;           /* grid step > 0 */
@@ -245,6 +253,9 @@ typedef struct {
     double device_keys_ms;  /* device time of the plan-time distance / bin-key pass (0 host-only) */
     int64_t n_jobs_sweep;   /* tables evaluated by exponential sweeps (TFI_PLAN_SWEEP) */
     int64_t hist_len;       /* length of the kernel-gradient histogram (1 + largest pair distance in a call) */
+    int64_t n_jobs_hankel;  /* tables evaluated by the Hankel-matrix product (TFI_PLAN_HANKEL) */
+    int64_t device_errors;  /* bounded device waits that gave up since the plan was built (0 when healthy;
+                               reading it synchronises the device) */
 } tfi_plan_info;
 tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
 
@@ -277,14 +288,17 @@ tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t 
  *   DIRECT  cross tables / corrections by direct summation over occupied bins
  *   GATHER  per-vertex sum over calls of G - E, plus the leaf term, one write per row
  *   SWEEP   per call, G_0 by forward and backward backbone sweeps and E_alpha[0] per
- *           component, for each exponential term (TFI_PLAN_SWEEP plans) */
+ *           component, for each exponential term (TFI_PLAN_SWEEP plans)
+ *   HANKEL  cross tables / corrections by the Hankel-matrix product and antidiagonal
+ *           prefix sums (TFI_PLAN_HANKEL plans) */
 #define TFI_STAGE_LEAF   0
 #define TFI_STAGE_BUCKET 1
 #define TFI_STAGE_FFT    2
 #define TFI_STAGE_DIRECT 3
 #define TFI_STAGE_GATHER 4
 #define TFI_STAGE_SWEEP  5   /* exponential-sum sweeps (TFI_PLAN_SWEEP plans) */
-#define TFI_N_STAGES     6
+#define TFI_STAGE_HANKEL 6   /* Hankel-matrix products on tensor cores (TFI_PLAN_HANKEL plans) */
+#define TFI_N_STAGES     7
 
 /* Per-stage timing with CUDA events recorded on the apply's stream. enable != 0
  * starts recording (and clears previous totals); 0 stops. Adds two event

@@ -55,14 +55,15 @@ class _Info(ctypes.Structure):
         "n", "n_calls", "n_leaves", "n_levels", "n_records", "n_keys", "n_jobs_fft", "n_jobs_direct",
         "n_centroid", "sum_table", "sum_fft_points", "sum_leaf_pairs", "ftab_len", "device_bytes")] + [
         ("plan_seconds", ctypes.c_double), ("device_keys_ms", ctypes.c_double), ("n_jobs_sweep", ctypes.c_int64),
-        ("hist_len", ctypes.c_int64)]
+        ("hist_len", ctypes.c_int64), ("n_jobs_hankel", ctypes.c_int64), ("device_errors", ctypes.c_int64)]
 
 
 EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_host", "tfi_destroy",
                     "tfi_plan_get_info", "tfi_plan_export", "tfi_profile_enable", "tfi_profile_read",
                     "tfi_stage_model", "tfi_apply_static", "tfi_dense_apply", "tfi_graph_create", "tfi_graph_launch",
                     "tfi_graph_destroy", "tfi_sinkhorn", "tfi_kernel_grad", "tfi_set_kernel", "tfi_last_error")
-STAGES = ("leaf", "bucket", "fft", "direct", "gather", "sweep")
+STAGES = ("leaf", "bucket", "fft", "direct", "gather", "sweep", "hankel")
+HANKEL_MODES = {None: 0, False: 0, "auto": 4, "all": 8}
 
 _lib = None
 
@@ -127,7 +128,7 @@ class Plan:
     """A planned tree (or forest): the decomposition, f samples and spectra on the device."""
 
     def __init__(self, n, u, v, w, delta=1.0, kernel=("expsum", [1.0, 1.0]), table=None, policy="adaptive",
-                 leaf_max=64, max_channels=16, host_only=False, sweep=False):
+                 leaf_max=64, max_channels=16, host_only=False, sweep=False, hankel=None):
         u = np.ascontiguousarray(u, dtype=np.int32)
         v = np.ascontiguousarray(v, dtype=np.int32)
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -138,7 +139,7 @@ class Plan:
         ker = _Kernel(KERNEL_KINDS[kind], int(params.shape[0]), params.ctypes.data if params.size else None,
                       0 if tab is None else int(tab.shape[0]), None if tab is None else tab.ctypes.data)
         opt = _Options(float(delta), POLICIES[policy], int(leaf_max), int(max_channels),
-                       (1 if host_only else 0) | (2 if sweep else 0))
+                       (1 if host_only else 0) | (2 if sweep else 0) | HANKEL_MODES[hankel])
         h = ctypes.c_void_p()
         _check(lib().tfi_plan(ctypes.byref(tree), ctypes.byref(ker), ctypes.byref(opt), ctypes.byref(h)))
         self._h = h

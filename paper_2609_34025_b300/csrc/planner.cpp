@@ -1,6 +1,8 @@
 // Host-side decomposition planner (see planner.hpp).
 #include "planner.hpp"
 
+#include "hankel_layout.hpp"
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -378,6 +380,19 @@ private:
 // two channels per complex transform) plus the key scatter and read-back.
 constexpr double kFftCostPerPointLog = 3.0;
 constexpr double kFftCostPerKey = 4.0;
+// Hankel evaluator, per occupied backbone column and channel: the split-TF32
+// product (3 x 2 NP KT flops at ~1/12 the cost of an FP32 FMA on the tensor
+// cores), the operand staging (KT loads) and two prefix-sum updates per row; a
+// CTA always covers 128 channels, so fewer channels pay for 128.
+constexpr double kHankelMmaCost = 6.0 / 12.0;
+constexpr double kHankelStageCost = 1.0;
+constexpr double kHankelScanCost = 4.0;
+
+double hankel_cost(int32_t H, int32_t L, double ncols, double nk, int d) {
+    const HankelLayout lay = hankel_layout(H, L);
+    const double per_col = kHankelMmaCost * lay.NP * lay.KT + kHankelStageCost * lay.KT + kHankelScanCost * lay.S;
+    return ncols * per_col * 128.0 / double(std::min(d, 128)) + 2 * nk;
+}
 
 // Run fn(i) for i in [0, n) on all hardware threads (dynamic scheduling).
 template <typename Fn>
@@ -568,7 +583,18 @@ int flatten(HostPlan &hp, std::string &err) {
             const int lg = jb.lp1 + jb.lp2;
             const double np = std::ldexp(1.0, lg);
             const double cost_fft = kFftCostPerPointLog * np * std::max(1, lg) + kFftCostPerKey * nk;
-            jb.mode = (lg <= kFftMaxLog && cost_fft < nk * nk) ? 0 : 1;
+            const bool fft_ok = lg <= kFftMaxLog;
+            jb.mode = (fft_ok && cost_fft < nk * nk) ? 0 : 1;
+            const bool hk_ok = (hp.flags & (TFI_PLAN_HANKEL | TFI_PLAN_HANKEL_ALL)) && hankel_fits(maxr, maxx);
+            if (hk_ok) {
+                int64_t ncols = 0;  // occupied backbone columns
+                std::vector<uint8_t> seen(size_t(maxx) + 1, 0);
+                for (int64_t k = jb.kb; k < jb.ke; ++k) seen[size_t(hp.key_x[size_t(k)])] = 1;
+                for (uint8_t b : seen) ncols += b;
+                const double best = std::min(nk * nk, fft_ok ? cost_fft : nk * nk);
+                if ((hp.flags & TFI_PLAN_HANKEL_ALL) || hankel_cost(maxr, maxx, double(ncols), nk, hp.max_channels) < best)
+                    jb.mode = 3;
+            }
             hp.jobs[size_t(joff[c]) + j] = jb;
         }
         CallBins().kr.swap(cb.kr);
@@ -685,7 +711,7 @@ int flatten(HostPlan &hp, std::string &err) {
     for (const Job &j : hp.jobs) {
         const int64_t top = 2 * int64_t(j.maxr) + j.maxx;
         need_any = std::max(need_any, top);
-        if (j.mode == 1) need = std::max(need, top);
+        if (j.mode == 1 || j.mode == 3) need = std::max(need, top);
     }
     hp.ftab_len = need + 1;
     hp.hist_len = std::max(need_any, need_leaf) + 1;

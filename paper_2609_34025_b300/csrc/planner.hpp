@@ -58,7 +58,8 @@ struct Job {
     int64_t kb, ke;       // key range
     int32_t maxr, maxx;   // largest depth / coordinate among the keys
     int32_t lp1, lp2;     // log2 FFT sizes (depth, backbone)
-    int32_t mode;         // 0 = FFT, 1 = direct, 2 = exponential sweep (inside the call's sweep job)
+    int32_t mode;         // 0 = FFT, 1 = direct, 2 = exponential sweep (inside the call's sweep job),
+                          // 3 = Hankel-matrix product on tensor cores
     int32_t is_comp;      // 1 for a correction job
 };
 

@@ -13,6 +13,7 @@
 
 #include "dense_tc.cuh"
 #include "grad.cuh"
+#include "hankel_tc.cuh"
 #include "kernels.cuh"
 #include "planner.hpp"
 #include "tfi.h"
@@ -42,6 +43,10 @@ struct WorkLists {
     tfi::dev::FftItem *d_fft = nullptr;
     tfi::dev::DirItem *d_dir = nullptr;
     int n_dir = 0;
+    // Hankel-matrix jobs: one item per (job, 128-channel block), one launch
+    tfi::tc::HankelItem *d_hk = nullptr;
+    int n_hk = 0;
+    size_t hk_smem = 0;
 };
 
 }  // namespace
@@ -88,6 +93,8 @@ struct tfi_plan_s {
     int64_t dense_ftab_len = 0;
     std::vector<int32_t> dn_tree_ptr_h;
     double device_keys_ms = 0.0;
+    int32_t n_hankel = 0;           // jobs evaluated by the Hankel-matrix product
+    int32_t *hk_err = nullptr;      // set by a Hankel CTA whose bounded MMA wait gave up
     std::map<int, WorkLists> work;  // per channel count d
     // fork/join inside an apply: leaf terms and direct jobs run on their own
     // streams, concurrently with the bin sums and FFT jobs
@@ -143,6 +150,7 @@ struct tfi_plan_s {
         for (auto &kv : work) {
             cudaFree(kv.second.d_fft);
             cudaFree(kv.second.d_dir);
+            cudaFree(kv.second.d_hk);
         }
         for (void *p : allocs) cudaFree(p);
     }
@@ -168,11 +176,19 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
     const int pairs = (d + 1) / 2;
     std::map<int, std::vector<tfi::dev::FftItem>> by_class;
     std::vector<tfi::dev::DirItem> dir;
+    std::vector<tfi::tc::HankelItem> hk;
+    uint32_t hk_cols = 32;
     const auto &jobs = p->hp.jobs;
     for (size_t j = 0; j < jobs.size(); ++j) {
         const tfi::Job &jb = jobs[j];
         if (jb.ke == jb.kb || jb.mode == 2) continue;
-        if (jb.mode == 0) {
+        if (jb.mode == 3) {
+            const tfi::HankelLayout lay = tfi::hankel_layout(jb.maxr, jb.maxx);
+            wl.hk_smem = std::max(wl.hk_smem, size_t(lay.bytes));
+            hk_cols = std::max(hk_cols, tfi::hankel_tmem_cols(lay.NP));
+            for (int c0 = 0; c0 < d; c0 += 128)
+                hk.push_back(tfi::tc::HankelItem{int32_t(jb.kb), int32_t(jb.ke), c0, jb.maxr, jb.maxx, {0, 0, 0}});
+        } else if (jb.mode == 0) {
             const int lnp = jb.lp1 + jb.lp2;
             const int np = fft_pairs_per_cta(lnp, pairs);
             for (int p0 = 0; p0 < pairs; p0 += np)
@@ -197,6 +213,15 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
     if (!dir.empty()) {
         TFI_CUDA(cudaMalloc(&wl.d_dir, dir.size() * sizeof(dir[0])));
         TFI_CUDA(cudaMemcpy(wl.d_dir, dir.data(), dir.size() * sizeof(dir[0]), cudaMemcpyHostToDevice));
+    }
+    wl.n_hk = int(hk.size());
+    if (!hk.empty()) {
+        // shared memory also caps co-resident CTAs, and with them the tensor memory
+        // they allocate: at most 512 / hk_cols CTAs may fit on an SM (228 KB each)
+        const size_t max_ctas = 512 / hk_cols;
+        wl.hk_smem = std::max(wl.hk_smem, size_t(228 * 1024) / (max_ctas + 1));
+        TFI_CUDA(cudaMalloc(&wl.d_hk, hk.size() * sizeof(hk[0])));
+        TFI_CUDA(cudaMemcpy(wl.d_hk, hk.data(), hk.size() * sizeof(hk[0]), cudaMemcpyHostToDevice));
     }
     auto res = p->work.emplace(d, wl);
     *out = &res.first->second;
@@ -238,6 +263,7 @@ bool g_attr_done = false;
 tfi_status set_attributes() {
     if (g_attr_done) return TFI_OK;
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    TFI_CUDA(cudaFuncSetAttribute(tfi::tc::hankel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
 #define LEAF_ATTR(T, CH)                                                                                      \
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::leaf_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   200 * 1024));
@@ -320,6 +346,12 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
                     p->sw_ejobs, p->n_sw_ejobs, p->jobs, p->key_r, d, p->kbuf, p->vbuf, p->sw_beta, p->sw_coef,
                     p->sw_terms);
             m_sw.done(p->n_sw_ejobs > 0 ? 2 : 1);
+        }
+        if (wl->n_hk > 0) {
+            StageMark m_hk(p, s, TFI_STAGE_HANKEL);
+            tfi::tc::hankel_kernel<<<wl->n_hk, 128, wl->hk_smem, s>>>(wl->d_hk, p->key_r, p->key_x, d, p->kbuf,
+                                                                      p->vbuf, p->ftab, p->hk_err);
+            m_hk.done(1);
         }
         StageMark m_fft(p, s, TFI_STAGE_FFT);
         for (size_t c = 0; c < wl->fft_lnp.size(); ++c) {
@@ -435,6 +467,14 @@ tfi_status upload_plan(tfi_plan_t p) {
         jd[j].pad = 0;
     }
     if (tfi_status rc = p->upload(&p->jobs, jd)) return rc;
+    p->n_hankel = 0;
+    for (const tfi::Job &jb : hp.jobs) p->n_hankel += jb.mode == 3;
+    {
+        void *q = nullptr;
+        if (tfi_status rc = p->alloc(&q, 16)) return rc;
+        p->hk_err = static_cast<int32_t *>(q);
+        TFI_CUDA(cudaMemset(p->hk_err, 0, 16));
+    }
     if (tfi_status rc = p->upload(&p->vrec_ptr, hp.vrec_ptr)) return rc;
     if (tfi_status rc = p->upload(&p->vrec_akey, hp.vrec_akey)) return rc;
     if (tfi_status rc = p->upload(&p->vrec_bkey, hp.vrec_bkey)) return rc;
@@ -536,6 +576,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 template <typename T>
 tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     if (p->n_sweeps > 0) return fail(TFI_ERR_UNSUPPORTED, "tfi_apply_static does not run exponential-sweep plans");
+    if (p->n_hankel > 0) return fail(TFI_ERR_UNSUPPORTED, "tfi_apply_static does not run Hankel-evaluator plans");
     if (tfi_status rc = set_attributes()) return rc;
     // work lists for d, built on the host (same grouping as the plan-owned path)
     const int pairs = (d + 1) / 2;
@@ -1167,6 +1208,8 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info) {
             info->sum_fft_points += int64_t(1) << (j.lp1 + j.lp2);
         } else if (j.mode == 1) {
             info->n_jobs_direct++;
+        } else if (j.mode == 3) {
+            info->n_jobs_hankel++;
         } else {
             info->n_jobs_sweep++;
         }
@@ -1181,6 +1224,12 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info) {
     info->plan_seconds = hp.plan_seconds;
     info->device_keys_ms = plan->device_keys_ms;
     info->hist_len = hp.hist_len;
+    for (int32_t *e : {plan->hk_err, plan->dn_err}) {
+        if (!e) continue;
+        int32_t v = 0;
+        TFI_CUDA(cudaMemcpy(&v, e, 4, cudaMemcpyDeviceToHost));
+        info->device_errors += v != 0;
+    }
     return TFI_OK;
 }
 
@@ -1223,7 +1272,16 @@ tfi_status tfi_stage_model(tfi_plan_t plan, int32_t d, int32_t dtype, double *by
     double kf = 0, kd = 0;
     for (const tfi::Job &j : hp.jobs) {
         const double nk = double(j.ke - j.kb);
-        if (j.mode == 0) {
+        if (j.mode == 3) {
+            // B = Fh A per occupied column: 2 (H + L + 1)(H + 1) flops per channel (the appendix's
+            // count); each bin is read once and written twice when L > 0 (value, then + suffix)
+            std::vector<uint8_t> seen(size_t(j.maxx) + 1, 0);
+            double ncols = 0;
+            for (int64_t k = j.kb; k < j.ke; ++k) seen[size_t(hp.key_x[size_t(k)])] = 1;
+            for (uint8_t b : seen) ncols += b;
+            flops[TFI_STAGE_HANKEL] += 2.0 * double(j.maxr + j.maxx + 1) * double(j.maxr + 1) * ncols * D;
+            bytes[TFI_STAGE_HANKEL] += nk * ((j.maxx > 0 ? 4 : 2) * D * 4 + 8);
+        } else if (j.mode == 0) {
             const double np = std::ldexp(1.0, j.lp1 + j.lp2);
             const double lg = double(j.lp1 + j.lp2);
             kf += nk;

@@ -106,3 +106,25 @@ def test_info_counts_consistent():
     # every vertex ends on exactly one backbone of a non-leaf call or in exactly one leaf
     assert leaves[:, 2].sum() + calls[:, 4].sum() == t.n and np.all(leaves[:, 2] <= 64)
     assert info["n_jobs_fft"] + info["n_jobs_direct"] >= info["n_calls"]
+
+
+def test_hankel_selection_host_only():
+    # TFI_PLAN_HANKEL_ALL: every job within the limits (H + 1 <= 64, H + L + 1 <= 128 grid units)
+    # uses the Hankel evaluator; TFI_PLAN_HANKEL: the channel-aware cost model picks it more often
+    # with many channels than with one
+    cfg = W.configs.attention(heads=1)
+    h = cfg["heads"][0]
+    mk = lambda **kw: tfi.Plan.from_spec(h["tree"], 1.0, h["kernel"], leaf_max=16, host_only=True, **kw)
+    all_ = mk(max_channels=4096, hankel="all").info()
+    none = mk(max_channels=4096).info()
+    assert all_["n_jobs_hankel"] > 0 and none["n_jobs_hankel"] == 0
+    assert all_["n_jobs_hankel"] + all_["n_jobs_direct"] + all_["n_jobs_fft"] == \
+        none["n_jobs_direct"] + none["n_jobs_fft"]
+    wide = mk(max_channels=4096, hankel="auto").info()["n_jobs_hankel"]
+    narrow = mk(max_channels=1, hankel="auto").info()["n_jobs_hankel"]
+    assert wide >= narrow
+    # grid-unit tables beyond the limits never qualify
+    cfg = W.configs.sweep(shape="rrt", n=1 << 12, d=1, kernel="exp")
+    big = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], leaf_max=1, host_only=True,
+                             hankel="all").info()
+    assert big["n_jobs_fft"] + big["n_jobs_direct"] > 0
