@@ -381,12 +381,14 @@ private:
 constexpr double kFftCostPerPointLog = 3.0;
 constexpr double kFftCostPerKey = 4.0;
 // Hankel evaluator, per occupied backbone column and channel: the split-TF32
-// product (3 x 2 NP KT flops at ~1/12 the cost of an FP32 FMA on the tensor
-// cores), the operand staging (KT loads) and two prefix-sum updates per row; a
-// CTA always covers 128 channels, so fewer channels pay for 128.
-constexpr double kHankelMmaCost = 6.0 / 12.0;
+// product (NP x KT per channel), the operand staging (KT loads) and two
+// prefix-sum updates per row; a CTA always covers 128 channels, so fewer
+// channels pay for 128. The weights are calibrated on the attention-width
+// workload (12 grid spanning trees of 196 vertices, 4096 channels), where the
+// Hankel stage took 0.81x the time of the direct stage over the same tables.
+constexpr double kHankelMmaCost = 0.25;
 constexpr double kHankelStageCost = 1.0;
-constexpr double kHankelScanCost = 4.0;
+constexpr double kHankelScanCost = 3.0;
 
 double hankel_cost(int32_t H, int32_t L, double ncols, double nk, int d) {
     const HankelLayout lay = hankel_layout(H, L);

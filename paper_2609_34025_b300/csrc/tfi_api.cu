@@ -326,7 +326,7 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
         m_bucket.done(1);
         TFI_CUDA(cudaEventRecord(p->ev_bucket, s));
         TFI_CUDA(cudaStreamWaitEvent(s_dir, p->ev_bucket, 0));
-        // (a4, a5) tables: direct jobs on their stream, FFT jobs (one launch per size class) on s
+        // (a4, a5) tables: direct and Hankel jobs on their stream, FFT jobs (one launch per size class) on s
         StageMark m_dir(p, s_dir, TFI_STAGE_DIRECT);
         if (d >= 16) launch_direct<16>(p, *wl, d, s_dir);
         else if (d > 4) launch_direct<8>(p, *wl, d, s_dir);
@@ -334,6 +334,12 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
         else if (d == 2) launch_direct<2>(p, *wl, d, s_dir);
         else launch_direct<1>(p, *wl, d, s_dir);
         m_dir.done(wl->n_dir > 0 ? 1 : 0);
+        if (wl->n_hk > 0) {
+            StageMark m_hk(p, s_dir, TFI_STAGE_HANKEL);
+            tfi::tc::hankel_kernel<<<wl->n_hk, 128, wl->hk_smem, s_dir>>>(wl->d_hk, p->key_r, p->key_x, d, p->kbuf,
+                                                                          p->vbuf, p->ftab, p->hk_err);
+            m_hk.done(1);
+        }
         TFI_CUDA(cudaEventRecord(p->ev_dir, s_dir));
         if (p->n_sweeps > 0) {
             StageMark m_sw(p, s, TFI_STAGE_SWEEP);
@@ -346,12 +352,6 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
                     p->sw_ejobs, p->n_sw_ejobs, p->jobs, p->key_r, d, p->kbuf, p->vbuf, p->sw_beta, p->sw_coef,
                     p->sw_terms);
             m_sw.done(p->n_sw_ejobs > 0 ? 2 : 1);
-        }
-        if (wl->n_hk > 0) {
-            StageMark m_hk(p, s, TFI_STAGE_HANKEL);
-            tfi::tc::hankel_kernel<<<wl->n_hk, 128, wl->hk_smem, s>>>(wl->d_hk, p->key_r, p->key_x, d, p->kbuf,
-                                                                      p->vbuf, p->ftab, p->hk_err);
-            m_hk.done(1);
         }
         StageMark m_fft(p, s, TFI_STAGE_FFT);
         for (size_t c = 0; c < wl->fft_lnp.size(); ++c) {
