@@ -5,8 +5,9 @@ backward (K G) for every head, plus the learnable-f gradient with --grad.
 
 Compares the cross-table evaluators: FFT / direct (default), the Hankel-matrix
 product on tensor cores chosen by the cost model ("auto") or for every
-qualifying table ("all"), and the dense f(D) F path on tensor cores. The leaf
-cutoff s0 is tuned per evaluator. Outputs of head 0 are checked against the
+qualifying table ("all"), dense leaves on the FP32 ALUs instead of the tensor
+cores ("alu_leaf"), and the dense f(D) F path on tensor cores. The leaf cutoff
+s0 is tuned per variant. Outputs of head 0 are checked against the
 FP64 oracle. Prints one JSON line.
 
     python bench_attention.py [--steps 20] [--warmup 3] [--grad]
@@ -63,7 +64,8 @@ def main():
 
     def make(mode, s0):
         return [tfi.Plan.from_spec(h["tree"], 1.0, h["kernel"], leaf_max=s0, max_channels=d,
-                                   hankel=None if mode == "default" else mode) for h in heads]
+                                   hankel=mode if mode in ("auto", "all") else None,
+                                   leaf_alu=mode == "alu_leaf") for h in heads]
 
     def step_fn(plans, graphs):
         def run():
@@ -75,7 +77,7 @@ def main():
         return run
 
     results = {}
-    for mode in ("default", "auto", "all"):
+    for mode in ("default", "auto", "all", "alu_leaf"):
         best = None
         for s0 in (1, 4, 16, 64, 196):
             plans = make(mode, s0)

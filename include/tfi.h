@@ -106,6 +106,10 @@ typedef struct {
                                    channel-aware cost model (at max_channels) ranks it below
                                    direct summation and the FFT */
 #define TFI_PLAN_HANKEL_ALL 8   /* every qualifying job uses the Hankel evaluator */
+#define TFI_PLAN_LEAF_ALU   16  /* dense leaves on the FP32 ALUs for every d (by default BF16 applies
+                                   with d >= 64 sum leaves as f(D) x F products on the tensor cores:
+                                   tcgen05 kind::tf32, f(D) split into hi + lo; FP32 applies always
+                                   use the FP32 ALUs, whose summation holds the 1e-4 bound) */
 
 typedef struct {
     double delta;           /* grid step > 0 */

@@ -128,7 +128,7 @@ class Plan:
     """A planned tree (or forest): the decomposition, f samples and spectra on the device."""
 
     def __init__(self, n, u, v, w, delta=1.0, kernel=("expsum", [1.0, 1.0]), table=None, policy="adaptive",
-                 leaf_max=64, max_channels=16, host_only=False, sweep=False, hankel=None):
+                 leaf_max=64, max_channels=16, host_only=False, sweep=False, hankel=None, leaf_alu=False):
         u = np.ascontiguousarray(u, dtype=np.int32)
         v = np.ascontiguousarray(v, dtype=np.int32)
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -139,7 +139,7 @@ class Plan:
         ker = _Kernel(KERNEL_KINDS[kind], int(params.shape[0]), params.ctypes.data if params.size else None,
                       0 if tab is None else int(tab.shape[0]), None if tab is None else tab.ctypes.data)
         opt = _Options(float(delta), POLICIES[policy], int(leaf_max), int(max_channels),
-                       (1 if host_only else 0) | (2 if sweep else 0) | HANKEL_MODES[hankel])
+                       (1 if host_only else 0) | (2 if sweep else 0) | HANKEL_MODES[hankel] | (16 if leaf_alu else 0))
         h = ctypes.c_void_p()
         _check(lib().tfi_plan(ctypes.byref(tree), ctypes.byref(ker), ctypes.byref(opt), ctypes.byref(h)))
         self._h = h

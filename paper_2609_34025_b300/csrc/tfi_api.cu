@@ -14,6 +14,7 @@
 #include "dense_tc.cuh"
 #include "grad.cuh"
 #include "hankel_tc.cuh"
+#include "leaf_tc.cuh"
 #include "kernels.cuh"
 #include "planner.hpp"
 #include "tfi.h"
@@ -94,7 +95,9 @@ struct tfi_plan_s {
     std::vector<int32_t> dn_tree_ptr_h;
     double device_keys_ms = 0.0;
     int32_t n_hankel = 0;           // jobs evaluated by the Hankel-matrix product
-    int32_t *hk_err = nullptr;      // set by a Hankel CTA whose bounded MMA wait gave up
+    int32_t *hk_err = nullptr;      // [0]: a Hankel CTA, [1]: a tensor-core leaf CTA whose bounded MMA wait gave up
+    tfi::tc::LeafTile *leaf_tiles = nullptr;  // 128-row tiles of the leaf groups (tensor-core leaves)
+    int32_t n_leaf_tiles = 0;
     std::map<int, WorkLists> work;  // per channel count d
     // fork/join inside an apply: leaf terms and direct jobs run on their own
     // streams, concurrently with the bin sums and FFT jobs
@@ -245,6 +248,53 @@ void launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s) {
                                                          p->leaf_lo, p->leaf_hi, F, d, p->ftab, fts, lbuf, p->max_gs);
 }
 
+constexpr int kLeafTcFtabSmem = 4096;  // f samples staged in shared memory by the tensor-core leaf kernel
+constexpr int kLeafTcMinChannels = 64;  // below this the FP32-ALU leaf kernel is used
+
+template <typename T, int NB>
+size_t leaf_tc_smem(int fts) {
+    constexpr uint32_t tcols = NB <= 32 ? 32u : uint32_t(NB);
+    const size_t max_ctas = 512 / tcols;  // tensor memory per SM bounds co-resident CTAs
+    return std::max(size_t(tfi::tc::leaf_tc_layout(NB, sizeof(T) == 4, fts).bytes), size_t(228 * 1024) / (max_ctas + 1));
+}
+
+template <typename T, int NB>
+void launch_leaf_tc_nb(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s) {
+    const int fts = p->hp.ftab_len <= kLeafTcFtabSmem ? int(p->hp.ftab_len) : 0;
+    dim3 grid(unsigned(p->n_leaf_tiles), unsigned((d + NB - 1) / NB));
+    tfi::tc::leaf_tc_kernel<T, NB><<<grid, 256, leaf_tc_smem<T, NB>(fts), s>>>(
+        p->leaf_tiles, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, p->leaf_lo, p->leaf_hi, F, d, p->ftab, fts, lbuf,
+        p->hk_err + 1);
+}
+
+// Tensor-core leaves for BF16 fields: NB = channels per CTA (TMEM columns), the next power of two
+// >= d, from 64 to 256. FP32 fields stay on the FP32-ALU leaf kernel: the tensor cores' FP32
+// accumulation over the ~1000 chained MMAs of a large leaf measured 6.5e-4 normwise on a slowly
+// decaying kernel, beyond the FP32 bound of 1e-4.
+void launch_leaf_tc(tfi_plan_t p, const __nv_bfloat16 *F, float *lbuf, int d, cudaStream_t s) {
+    if (p->n_leaf_tiles == 0) return;
+    using B = __nv_bfloat16;
+    if (d > 128) launch_leaf_tc_nb<B, 256>(p, F, lbuf, d, s);
+    else if (d > 64) launch_leaf_tc_nb<B, 128>(p, F, lbuf, d, s);
+    else launch_leaf_tc_nb<B, 64>(p, F, lbuf, d, s);
+}
+
+// (a7) dense leaves -> lbuf: tensor cores for wide BF16 fields, else the FP32-ALU kernel
+template <typename T>
+void launch_leaves(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
+    if constexpr (sizeof(T) == 2) {
+        if (d >= kLeafTcMinChannels && !(p->hp.flags & TFI_PLAN_LEAF_ALU)) {
+            launch_leaf_tc(p, F, p->lbuf, d, s);
+            return;
+        }
+    }
+    if (d >= 16) launch_leaf<16>(p, F, p->lbuf, d, s);
+    else if (d > 4) launch_leaf<8>(p, F, p->lbuf, d, s);
+    else if (d > 2) launch_leaf<4>(p, F, p->lbuf, d, s);
+    else if (d == 2) launch_leaf<2>(p, F, p->lbuf, d, s);
+    else launch_leaf<1>(p, F, p->lbuf, d, s);
+}
+
 template <int CH>
 void launch_direct(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
     if (wl.n_dir == 0) return;
@@ -264,6 +314,11 @@ tfi_status set_attributes() {
     if (g_attr_done) return TFI_OK;
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
     TFI_CUDA(cudaFuncSetAttribute(tfi::tc::hankel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+#define LEAF_TC_ATTR(T, NB)                                                                                 \
+    TFI_CUDA(cudaFuncSetAttribute(tfi::tc::leaf_tc_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  227 * 1024));
+    LEAF_TC_ATTR(__nv_bfloat16, 64) LEAF_TC_ATTR(__nv_bfloat16, 128) LEAF_TC_ATTR(__nv_bfloat16, 256)
+#undef LEAF_TC_ATTR
 #define LEAF_ATTR(T, CH)                                                                                      \
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::leaf_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   200 * 1024));
@@ -306,11 +361,7 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     TFI_CUDA(cudaStreamWaitEvent(s_leaf, p->ev_fork, 0));
     // (a7) dense leaves -> lbuf, on the leaf stream
     StageMark m_leaf(p, s_leaf, TFI_STAGE_LEAF);
-    if (d >= 16) launch_leaf<16>(p, F, p->lbuf, d, s_leaf);
-    else if (d > 4) launch_leaf<8>(p, F, p->lbuf, d, s_leaf);
-    else if (d > 2) launch_leaf<4>(p, F, p->lbuf, d, s_leaf);
-    else if (d == 2) launch_leaf<2>(p, F, p->lbuf, d, s_leaf);
-    else launch_leaf<1>(p, F, p->lbuf, d, s_leaf);
+    launch_leaves(p, F, d, s_leaf);
     m_leaf.done(p->n_groups > 0 ? 1 : 0);
     TFI_CUDA(cudaEventRecord(p->ev_leaf, s_leaf));
     // (a3) bin sums
@@ -486,6 +537,14 @@ tfi_status upload_plan(tfi_plan_t p) {
     if (tfi_status rc = p->upload(&p->leaf_hi, hp.leaf_hi)) return rc;
     if (tfi_status rc = p->upload(&p->in_leaf, hp.in_leaf)) return rc;
     p->n_groups = int32_t(hp.lgrp_ptr.size()) - 1;
+    {
+        std::vector<tfi::tc::LeafTile> lt;
+        for (int g = 0; g < p->n_groups; ++g)
+            for (int32_t i0 = hp.lgrp_ptr[size_t(g)]; i0 < hp.lgrp_ptr[size_t(g) + 1]; i0 += tfi::tc::kLeafTile)
+                lt.push_back(tfi::tc::LeafTile{hp.lgrp_ptr[size_t(g)], hp.lgrp_ptr[size_t(g) + 1], i0, 0});
+        if (tfi_status rc = p->upload(&p->leaf_tiles, lt)) return rc;
+        p->n_leaf_tiles = int32_t(lt.size());
+    }
     p->max_gs = 1;
     for (int g = 0; g < p->n_groups; ++g)
         p->max_gs = std::max(p->max_gs, hp.lgrp_ptr[size_t(g) + 1] - hp.lgrp_ptr[size_t(g)]);
@@ -1224,10 +1283,14 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info) {
     info->plan_seconds = hp.plan_seconds;
     info->device_keys_ms = plan->device_keys_ms;
     info->hist_len = hp.hist_len;
-    for (int32_t *e : {plan->hk_err, plan->dn_err}) {
-        if (!e) continue;
+    if (plan->hk_err) {
+        int32_t v[2] = {0, 0};
+        TFI_CUDA(cudaMemcpy(v, plan->hk_err, 8, cudaMemcpyDeviceToHost));
+        info->device_errors += (v[0] != 0) + (v[1] != 0);
+    }
+    if (plan->dn_err) {
         int32_t v = 0;
-        TFI_CUDA(cudaMemcpy(&v, e, 4, cudaMemcpyDeviceToHost));
+        TFI_CUDA(cudaMemcpy(&v, plan->dn_err, 4, cudaMemcpyDeviceToHost));
         info->device_errors += v != 0;
     }
     return TFI_OK;

@@ -1,0 +1,102 @@
+"""GPU parity of the tensor-core dense leaves (tcgen05 kind::tf32) against the
+FP64 oracle and against the FP32-ALU leaf kernel.
+
+BF16 applies with d >= 64 sum leaves on the tensor cores (TFI_PLAN_LEAF_ALU
+forces the FP32-ALU kernel); FP32 applies always use the FP32-ALU kernel. With
+a large leaf cutoff s0 most of the operator is dense leaf work: every pair of a
+leaf contributes f(D(i) + D(j) - 2 min parent distance) F[j]. The cases cover
+leaves of up to 1024 vertices (8 row tiles, off-diagonal chunks on both sides),
+groups of packed small leaves, channel blocks of 64..256 with ragged ends, and
+f samples read from global memory (long grid distances).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import brute
+
+from ._lib import tfi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-4, "bf16": 1e-2}
+
+
+def _err(y, ref):
+    y = np.asarray(y, dtype=np.float64).reshape(ref.shape[0], -1)
+    ref = ref.reshape(ref.shape[0], -1)
+    return float((np.abs(y - ref).max(0) / np.maximum(np.abs(ref).max(0), 1e-300)).max())
+
+
+def _rrt(n, seed, lo=1, hi=4):
+    rng = np.random.default_rng(seed)
+    t = W.random_recursive(n, rng)
+    return t.with_weights(W.trees.integer_weights(t.m, lo, hi, rng))
+
+
+def _run(t, delta, spec, d, leaf_max, dtype="bf16", seed=3):
+    """(error of the default path, error of the FP32-ALU leaf path) against the oracle."""
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    F = torch.from_numpy(W.normal_field(t.n, d, seed=seed)).to("cuda", tdt)
+    tc = tfi.Plan.from_spec(t, delta, spec, leaf_max=leaf_max, max_channels=d)
+    alu = tfi.Plan.from_spec(t, delta, spec, leaf_max=leaf_max, max_channels=d, leaf_alu=True)
+    y, y_alu = tc.apply(F), alu.apply(F)
+    torch.cuda.synchronize()
+    assert tc.info()["device_errors"] == 0
+    ref = brute.integrate(t, delta, spec, F.float().cpu().numpy().astype(np.float64))
+    return _err(y.float().cpu().numpy(), ref), _err(y_alu.float().cpu().numpy(), ref), tc.info()
+
+
+@pytest.mark.parametrize("leaf_max", [16, 100, 256, 512, 1024])
+@pytest.mark.parametrize("d", [64, 65, 100, 128])
+def test_leaf_sizes_and_channels(leaf_max, d):
+    t = _rrt(3000, 21)
+    e, e_alu, info = _run(t, 1.0, W.KernelSpec.exp(0.05), d, leaf_max)
+    assert info["sum_leaf_pairs"] > 0
+    assert e <= TOL["bf16"] and e_alu <= TOL["bf16"]
+
+
+@pytest.mark.parametrize("d", [129, 256, 300])
+def test_wide_channel_blocks(d):
+    t = _rrt(1500, 22)
+    e, _, _ = _run(t, 1.0, W.KernelSpec.rational(0.3, e=1.5), d, 400)
+    assert e <= TOL["bf16"]
+
+
+def test_single_leaf_trees_and_packed_groups():
+    # a forest of trees from 1 to 300 vertices, every tree one leaf (s0 = 300): groups pack small leaves
+    cfg = W.configs.uneven_batch(count=60, lo=1, hi=300, d=64)
+    e, e_alu, _ = _run(cfg["tree"], cfg["delta"], cfg["kernel"], 64, 300)
+    assert e <= TOL["bf16"] and e_alu <= TOL["bf16"]
+
+
+def test_long_grid_distances_read_f_from_global_memory():
+    # delta = 1/64 on unit edges: 64 grid units per edge, leaf diameters of ~64,000 samples (> 4096)
+    for t in (W.path(1000), W.spider(4, 200)):
+        e, _, info = _run(t, 1 / 64, W.KernelSpec.exp(0.2), 64, 1024)
+        assert info["ftab_len"] > 4096
+        assert e <= TOL["bf16"]
+
+
+def test_attention_whole_tree_leaf():
+    # s0 = 196: each attention tree is one leaf, the whole operator one f(D) F product per head
+    cfg = W.configs.attention(heads=2)
+    for h in cfg["heads"]:
+        e, _, info = _run(h["tree"], 1.0, h["kernel"], 1024, 196)
+        assert info["n_calls"] == 0
+        assert e <= TOL["bf16"]
+
+
+def test_paths_and_stars():
+    for t in (W.path(1024), W.star(700), W.spider(5, 150), W.caterpillar_leaves(200)):
+        e, _, _ = _run(t, 1.0, W.KernelSpec.exp(0.01), 96, 1024)
+        assert e <= TOL["bf16"]
+
+
+def test_fp32_large_leaves_hold_the_fp32_bound():
+    # FP32 fields sum leaves on the FP32 ALUs in a fixed order: 1024-vertex leaves with a slowly
+    # decaying kernel (heavy cancellation) stay within 1e-4
+    for t in (W.path(1024), W.star(700), _rrt(2000, 23)):
+        e, _, _ = _run(t, 1.0, W.KernelSpec.exp(0.01), 96, 1024, dtype="f32")
+        assert e <= TOL["f32"]
