@@ -1,7 +1,9 @@
 """Attention-width benchmark: one tree per head (12 heads, random spanning trees
 of the 14 x 14 patch grid, unit edges, N = 196), d = 64 images x 64 channels =
 4096 BF16 channels, f = 8-term exponential sum per head. One step = forward and
-backward (K G) for every head, plus the learnable-f gradient with --grad.
+backward (K G) for every head, plus the learnable-f gradient with --grad. The
+heads are independent: each head's step is one CUDA graph replayed on its own
+stream, and the step ends when all streams have joined.
 
 Compares the cross-table evaluators: FFT / direct (default), the Hankel-matrix
 product on tensor cores chosen by the cost model ("auto") or for every
@@ -67,10 +69,19 @@ def main():
                                    hankel=mode if mode in ("auto", "all") else None,
                                    leaf_alu=mode == "alu_leaf") for h in heads]
 
+    # the heads are independent: each replays its graph on its own stream, joined at the end of the step
+    streams = [torch.cuda.Stream() for _ in heads]
+
     def step_fn(plans, graphs):
         def run():
-            for g in graphs:
-                g.launch()
+            cur = torch.cuda.current_stream()
+            start = torch.cuda.Event()
+            start.record(cur)
+            for st, g in zip(streams, graphs):
+                st.wait_event(start)
+                g.launch(stream=st)
+            for st in streams:
+                cur.wait_stream(st)
             if a.grad:
                 for p, g, x in zip(plans, G, X):
                     p.kernel_grad(g, x)

@@ -63,6 +63,24 @@ __device__ __forceinline__ float from_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
+// V consecutive field values of one row as FP32: one 16-byte (FP32) or 8-byte
+// (BF16) load for V = 4; the caller guarantees the alignment.
+template <typename T, int V>
+__device__ __forceinline__ void load_row(const T *__restrict__ row, float *x) {
+    if constexpr (V == 4 && sizeof(T) == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(row));
+        x[0] = q.x, x[1] = q.y, x[2] = q.z, x[3] = q.w;
+    } else if constexpr (V == 4 && sizeof(T) == 2) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row));
+        const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&q.x);
+        const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&q.y);
+        x[0] = __low2float(a), x[1] = __high2float(a), x[2] = __low2float(b), x[3] = __high2float(b);
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) x[i] = to_f<T>(row[i]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // bucket: kbuf[k, c] = sum_{v in bin k} F[v, c]
 // ---------------------------------------------------------------------------
@@ -86,11 +104,7 @@ __global__ void bucket_kernel(int64_t n_keys, const int32_t *__restrict__ key_pt
             for (int q = 0; q < 4; ++q) v[q] = e + q < e1 ? __ldg(key_vtx + e + q) : -1;
             float x[4][V];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const T *row = F + int64_t(v[q] < 0 ? v[0] : v[q]) * d + c;
-#pragma unroll
-                for (int i = 0; i < V; ++i) x[q][i] = to_f<T>(row[i]);
-            }
+            for (int q = 0; q < 4; ++q) load_row<T, V>(F + int64_t(v[q] < 0 ? v[0] : v[q]) * d + c, x[q]);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (v[q] < 0) break;
@@ -101,6 +115,71 @@ __global__ void bucket_kernel(int64_t n_keys, const int32_t *__restrict__ key_pt
         float *dst = kbuf + k * d + c;
 #pragma unroll
         for (int i = 0; i < V; ++i) dst[i] = acc[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// bucket over segments: a bin's members are cut into consecutive segments of
+// at most kBucketSeg members, so that a bin of a thousand vertices is summed
+// by many threads instead of one. A segment that is its bin's only one writes
+// the bin row (dst >= 0); the others write a partial row -1 - dst of sbuf,
+// which bucket_combine adds up in segment order (a fixed order: deterministic).
+// ---------------------------------------------------------------------------
+template <typename T, int V>
+__global__ void bucket_seg_kernel(int64_t n_segs, const int32_t *__restrict__ seg_ptr,
+                                  const int32_t *__restrict__ seg_dst, const int32_t *__restrict__ key_vtx,
+                                  const T *__restrict__ F, int d, float *__restrict__ kbuf, float *__restrict__ sbuf) {
+    const int chunks = d / V;
+    const int64_t total = n_segs * chunks;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t g = t / chunks;
+        const int c = int(t - g * chunks) * V;
+        float acc[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) acc[i] = 0.f;
+        const int e1 = seg_ptr[g + 1];
+        for (int e = seg_ptr[g]; e < e1; e += 4) {
+            int v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = e + q < e1 ? __ldg(key_vtx + e + q) : -1;
+            float x[4][V];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) load_row<T, V>(F + int64_t(v[q] < 0 ? v[0] : v[q]) * d + c, x[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (v[q] < 0) break;
+#pragma unroll
+                for (int i = 0; i < V; ++i) acc[i] += x[q][i];
+            }
+        }
+        const int dst = seg_dst[g];
+        float *out = dst >= 0 ? kbuf + int64_t(dst) * d + c : sbuf + int64_t(-1 - dst) * d + c;
+#pragma unroll
+        for (int i = 0; i < V; ++i) out[i] = acc[i];
+    }
+}
+
+// kbuf[mb_key[m]] = sum of the partial rows mb_ptr[m] .. mb_ptr[m + 1] - 1 of sbuf, in order
+template <int V>
+__global__ void bucket_combine(int64_t n_multi, const int32_t *__restrict__ mb_key, const int32_t *__restrict__ mb_ptr,
+                               int d, const float *__restrict__ sbuf, float *__restrict__ kbuf) {
+    const int chunks = d / V;
+    const int64_t total = n_multi * chunks;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t m = t / chunks;
+        const int c = int(t - m * chunks) * V;
+        float acc[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) acc[i] = 0.f;
+        for (int r = mb_ptr[m]; r < mb_ptr[m + 1]; ++r) {
+            float x[V];
+            load_row<float, V>(sbuf + int64_t(r) * d + c, x);
+#pragma unroll
+            for (int i = 0; i < V; ++i) acc[i] += x[i];
+        }
+        float *out = kbuf + int64_t(mb_key[m]) * d + c;
+#pragma unroll
+        for (int i = 0; i < V; ++i) out[i] = acc[i];
     }
 }
 

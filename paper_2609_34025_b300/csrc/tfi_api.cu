@@ -69,6 +69,10 @@ struct tfi_plan_s {
     float *ftab = nullptr;
     float2 *spectra = nullptr, *twiddle = nullptr;
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
+    // bin sums by segments of at most kBucketSeg members (see bucket_seg_kernel)
+    int32_t *seg_ptr = nullptr, *seg_dst = nullptr, *mb_key = nullptr, *mb_ptr = nullptr;
+    int64_t n_segs = 0, n_multi = 0;
+    float *sbuf = nullptr;
     float *sk_buf = nullptr;  // Sinkhorn: K x (n x max_channels), allocated on first use
     // kernel gradient (built on first use)
     bool grad_ready = false;
@@ -101,7 +105,10 @@ struct tfi_plan_s {
     std::map<int, WorkLists> work;  // per channel count d
     // fork/join inside an apply: leaf terms and direct jobs run on their own
     // streams, concurrently with the bin sums and FFT jobs
-    cudaStream_t aux[2] = {nullptr, nullptr};
+    // aux[0]: leaves (lowest priority), aux[1]: direct / Hankel jobs, aux[2]: the critical path
+    // bin sums -> FFT jobs (both highest priority)
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_crit = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_leaf = nullptr, ev_bucket = nullptr, ev_dir = nullptr;
     // stage profiling (CUDA events on the apply stream)
     bool profiling = false;
@@ -145,7 +152,7 @@ struct tfi_plan_s {
         return TFI_OK;
     }
     ~tfi_plan_s() {
-        for (cudaEvent_t e : {ev_fork, ev_leaf, ev_bucket, ev_dir})
+        for (cudaEvent_t e : {ev_fork, ev_leaf, ev_bucket, ev_dir, ev_crit})
             if (e) cudaEventDestroy(e);
         for (cudaStream_t st : aux)
             if (st) cudaStreamDestroy(st);
@@ -162,10 +169,10 @@ struct tfi_plan_s {
 namespace {
 
 constexpr int kFftThreads = 256;
-constexpr int kFftSmemPairPoints = 1 << 13;  // points x pairs per CTA (64 KB) for classes below 2^14
+constexpr int kFftSmemPairPoints = 1 << 12;  // points x pairs per CTA (32 KB, 4 CTAs per SM) below 2^13
 
 int fft_pairs_per_cta(int lnp, int pairs) {
-    const int cap = lnp >= 13 ? 1 : (kFftSmemPairPoints >> lnp);
+    const int cap = lnp >= 12 ? 1 : (kFftSmemPairPoints >> lnp);
     return std::max(1, std::min(pairs, cap));
 }
 
@@ -231,6 +238,8 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
     return TFI_OK;
 }
 
+constexpr int32_t kBucketSeg = 32;  // members per bin-sum segment
+
 int grid_for(int64_t work, int threads) {
     const int64_t b = (work + threads - 1) / threads;
     return int(std::max<int64_t>(1, std::min<int64_t>(b, 148 * 32)));
@@ -277,6 +286,24 @@ void launch_leaf_tc(tfi_plan_t p, const __nv_bfloat16 *F, float *lbuf, int d, cu
     if (d > 128) launch_leaf_tc_nb<B, 256>(p, F, lbuf, d, s);
     else if (d > 64) launch_leaf_tc_nb<B, 128>(p, F, lbuf, d, s);
     else launch_leaf_tc_nb<B, 64>(p, F, lbuf, d, s);
+}
+
+// (a3) bin sums -> kbuf: segments, then the multi-segment bins' partial rows in order
+template <typename T>
+void launch_bucket(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
+    if (d % 4 == 0 && (reinterpret_cast<uintptr_t>(F) % (4 * sizeof(T))) == 0) {
+        tfi::dev::bucket_seg_kernel<T, 4><<<grid_for(p->n_segs * (d / 4), 256), 256, 0, s>>>(
+            p->n_segs, p->seg_ptr, p->seg_dst, p->key_vtx, F, d, p->kbuf, p->sbuf);
+        if (p->n_multi > 0)
+            tfi::dev::bucket_combine<4><<<grid_for(p->n_multi * (d / 4), 256), 256, 0, s>>>(
+                p->n_multi, p->mb_key, p->mb_ptr, d, p->sbuf, p->kbuf);
+    } else {
+        tfi::dev::bucket_seg_kernel<T, 1><<<grid_for(p->n_segs * d, 256), 256, 0, s>>>(
+            p->n_segs, p->seg_ptr, p->seg_dst, p->key_vtx, F, d, p->kbuf, p->sbuf);
+        if (p->n_multi > 0)
+            tfi::dev::bucket_combine<1><<<grid_for(p->n_multi * d, 256), 256, 0, s>>>(p->n_multi, p->mb_key,
+                                                                                     p->mb_ptr, d, p->sbuf, p->kbuf);
+    }
 }
 
 // (a7) dense leaves -> lbuf: tensor cores for wide BF16 fields, else the FP32-ALU kernel
@@ -355,29 +382,28 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     if (tfi_status rc = build_work(p, d, &wl)) return rc;
     if (tfi_status rc = set_attributes()) return rc;
     const int n = p->hp.n;
-    cudaStream_t s_leaf = p->aux[0], s_dir = p->aux[1];
+    cudaStream_t s_leaf = p->aux[0], s_dir = p->aux[1], s_crit = p->aux[2];
     // fork: everything on the side streams starts after the work already queued on s
     TFI_CUDA(cudaEventRecord(p->ev_fork, s));
+    TFI_CUDA(cudaStreamWaitEvent(s_crit, p->ev_fork, 0));
     TFI_CUDA(cudaStreamWaitEvent(s_leaf, p->ev_fork, 0));
-    // (a7) dense leaves -> lbuf, on the leaf stream
+    const int64_t n_keys = int64_t(p->hp.key_r.size());
+    // (a3) bin sums, first on the high-priority stream
+    if (n_keys > 0) {
+        StageMark m_bucket(p, s_crit, TFI_STAGE_BUCKET);
+        launch_bucket(p, F, d, s_crit);
+        m_bucket.done(p->n_multi > 0 ? 2 : 1);
+        TFI_CUDA(cudaEventRecord(p->ev_bucket, s_crit));
+    }
+    // (a7) dense leaves -> lbuf, on the low-priority leaf stream
     StageMark m_leaf(p, s_leaf, TFI_STAGE_LEAF);
     launch_leaves(p, F, d, s_leaf);
     m_leaf.done(p->n_groups > 0 ? 1 : 0);
     TFI_CUDA(cudaEventRecord(p->ev_leaf, s_leaf));
-    // (a3) bin sums
-    const int64_t n_keys = int64_t(p->hp.key_r.size());
     if (n_keys > 0) {
-        StageMark m_bucket(p, s, TFI_STAGE_BUCKET);
-        if (d % 4 == 0)
-            tfi::dev::bucket_kernel<T, 4><<<grid_for(n_keys * (d / 4), 256), 256, 0, s>>>(n_keys, p->key_ptr,
-                                                                                          p->key_vtx, F, d, p->kbuf);
-        else
-            tfi::dev::bucket_kernel<T, 1><<<grid_for(n_keys * d, 256), 256, 0, s>>>(n_keys, p->key_ptr, p->key_vtx,
-                                                                                    F, d, p->kbuf);
-        m_bucket.done(1);
-        TFI_CUDA(cudaEventRecord(p->ev_bucket, s));
         TFI_CUDA(cudaStreamWaitEvent(s_dir, p->ev_bucket, 0));
-        // (a4, a5) tables: direct and Hankel jobs on their stream, FFT jobs (one launch per size class) on s
+        // (a4, a5) tables: direct and Hankel jobs on their stream, sweeps and FFT jobs (one launch per
+        // size class) after the bin sums on the critical-path stream
         StageMark m_dir(p, s_dir, TFI_STAGE_DIRECT);
         if (d >= 16) launch_direct<16>(p, *wl, d, s_dir);
         else if (d > 4) launch_direct<8>(p, *wl, d, s_dir);
@@ -393,26 +419,32 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
         }
         TFI_CUDA(cudaEventRecord(p->ev_dir, s_dir));
         if (p->n_sweeps > 0) {
-            StageMark m_sw(p, s, TFI_STAGE_SWEEP);
+            StageMark m_sw(p, s_crit, TFI_STAGE_SWEEP);
             constexpr int WARPS = 4;
-            tfi::dev::sweep_g_kernel<WARPS><<<(p->n_sweeps + WARPS - 1) / WARPS, 32 * WARPS, 0, s>>>(
+            tfi::dev::sweep_g_kernel<WARPS><<<(p->n_sweeps + WARPS - 1) / WARPS, 32 * WARPS, 0, s_crit>>>(
                 p->sw_jobs, p->n_sweeps, p->key_r, p->key_x, p->sw_keys, p->sw_run, d, p->kbuf, p->vbuf,
                 p->sw_scratch, p->sw_beta, p->sw_coef, p->sw_terms);
             if (p->n_sw_ejobs > 0)
-                tfi::dev::sweep_e_kernel<WARPS><<<(p->n_sw_ejobs + WARPS - 1) / WARPS, 32 * WARPS, 0, s>>>(
+                tfi::dev::sweep_e_kernel<WARPS><<<(p->n_sw_ejobs + WARPS - 1) / WARPS, 32 * WARPS, 0, s_crit>>>(
                     p->sw_ejobs, p->n_sw_ejobs, p->jobs, p->key_r, d, p->kbuf, p->vbuf, p->sw_beta, p->sw_coef,
                     p->sw_terms);
             m_sw.done(p->n_sw_ejobs > 0 ? 2 : 1);
         }
-        StageMark m_fft(p, s, TFI_STAGE_FFT);
+        StageMark m_fft(p, s_crit, TFI_STAGE_FFT);
         for (size_t c = 0; c < wl->fft_lnp.size(); ++c) {
             const size_t smem = size_t(wl->fft_npair[c]) * size_t(tfi::dev::padded_size(1 << wl->fft_lnp[c])) *
                                 sizeof(float2);
-            tfi::dev::fft_kernel<<<wl->fft_count[c], kFftThreads, smem, s>>>(
+            tfi::dev::fft_kernel<<<wl->fft_count[c], kFftThreads, smem, s_crit>>>(
                 wl->d_fft + wl->fft_off[c], p->jobs, p->key_r, p->key_x, d, p->kbuf, p->vbuf, p->spectra, p->twiddle);
         }
         m_fft.done(int(wl->fft_lnp.size()));
+        TFI_CUDA(cudaEventRecord(p->ev_crit, s_crit));
+        TFI_CUDA(cudaStreamWaitEvent(s, p->ev_crit, 0));
         TFI_CUDA(cudaStreamWaitEvent(s, p->ev_dir, 0));
+    } else {
+        // nothing on the critical-path stream: join it so that it holds no dangling fork
+        TFI_CUDA(cudaEventRecord(p->ev_crit, s_crit));
+        TFI_CUDA(cudaStreamWaitEvent(s, p->ev_crit, 0));
     }
     // join, then (a6) gather
     TFI_CUDA(cudaStreamWaitEvent(s, p->ev_leaf, 0));
@@ -537,6 +569,7 @@ tfi_status upload_plan(tfi_plan_t p) {
     if (tfi_status rc = p->upload(&p->leaf_hi, hp.leaf_hi)) return rc;
     if (tfi_status rc = p->upload(&p->in_leaf, hp.in_leaf)) return rc;
     p->n_groups = int32_t(hp.lgrp_ptr.size()) - 1;
+
     {
         std::vector<tfi::tc::LeafTile> lt;
         for (int g = 0; g < p->n_groups; ++g)
@@ -578,12 +611,50 @@ tfi_status upload_plan(tfi_plan_t p) {
     if (tfi_status rc = p->upload(&p->spectra, spec)) return rc;
     if (tfi_status rc = p->upload(&p->twiddle, tw)) return rc;
     const size_t K = hp.key_r.size(), dm = size_t(hp.max_channels);
+    {
+        // segments of at most kBucketSeg consecutive members per bin
+        std::vector<int32_t> seg_ptr, seg_dst, mb_key, mb_ptr;
+        int32_t slots = 0;
+        for (size_t k = 0; k < K; ++k) {
+            const int32_t b = hp.key_ptr[k], e = hp.key_ptr[k + 1];
+            const int32_t ns = std::max<int32_t>(1, (e - b + kBucketSeg - 1) / kBucketSeg);
+            if (ns == 1) {
+                seg_ptr.push_back(b);
+                seg_dst.push_back(int32_t(k));
+                continue;
+            }
+            mb_key.push_back(int32_t(k));
+            mb_ptr.push_back(slots);
+            for (int32_t q = 0; q < ns; ++q) {
+                seg_ptr.push_back(b + q * kBucketSeg);
+                seg_dst.push_back(-1 - slots++);
+            }
+        }
+        seg_ptr.push_back(hp.key_ptr[K]);
+        mb_ptr.push_back(slots);
+        p->n_segs = int64_t(seg_dst.size());
+        p->n_multi = int64_t(mb_key.size());
+        if (tfi_status rc = p->upload(&p->seg_ptr, seg_ptr)) return rc;
+        if (tfi_status rc = p->upload(&p->seg_dst, seg_dst)) return rc;
+        if (tfi_status rc = p->upload(&p->mb_key, mb_key)) return rc;
+        if (tfi_status rc = p->upload(&p->mb_ptr, mb_ptr)) return rc;
+        if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->sbuf), size_t(slots) * dm * sizeof(float)))
+            return rc;
+    }
     if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->kbuf), K * dm * sizeof(float))) return rc;
     if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->vbuf), K * dm * sizeof(float))) return rc;
     if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->lbuf), size_t(hp.n) * dm * sizeof(float))) return rc;
     if (tfi_status rc = run_device_keys(p)) return rc;
-    for (cudaStream_t &st : p->aux) TFI_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    for (cudaEvent_t *e : {&p->ev_fork, &p->ev_leaf, &p->ev_bucket, &p->ev_dir})
+    {
+        // the leaf terms are needed only by the final gather: their stream yields SMs to the bin
+        // sums and table jobs, whose chain decides when the gather can start
+        int least = 0, greatest = 0;
+        TFI_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        TFI_CUDA(cudaStreamCreateWithPriority(&p->aux[0], cudaStreamNonBlocking, least));
+        TFI_CUDA(cudaStreamCreateWithPriority(&p->aux[1], cudaStreamNonBlocking, greatest));
+        TFI_CUDA(cudaStreamCreateWithPriority(&p->aux[2], cudaStreamNonBlocking, greatest));
+    }
+    for (cudaEvent_t *e : {&p->ev_fork, &p->ev_leaf, &p->ev_bucket, &p->ev_dir, &p->ev_crit})
         TFI_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     p->on_device = true;
     return TFI_OK;
