@@ -598,7 +598,8 @@ __global__ void gather_kernel(int n, const int32_t *__restrict__ vrec_ptr, const
 }
 
 // ---------------------------------------------------------------------------
-// dense leaves: one CTA per leaf group, CH channels per pass.
+// dense leaves of fewer than kLeafWarpMin vertices: one CTA per group of
+// consecutive small leaves, CH channels per pass.
 // In a leaf's preorder, dhat(i, j) = D(i) + D(j) - 2 min_{w in (min(i,j), max(i,j)]}
 // D(parent(w)). Each target i walks all sources of its leaf in one order with a
 // running minimum: first j = i+1 .. hi-1 (min over (i, j] grows by one entry),
@@ -625,7 +626,7 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
                             float *__restrict__ leaf_out, int max_gs) {
     constexpr int SV = LeafStride<CH>::v;
     extern __shared__ __align__(16) int smem_i[];
-    const int gb = gptr[blockIdx.x], ge = gptr[blockIdx.x + 1], gs = ge - gb;
+    const int gb = gptr[2 * blockIdx.x], ge = gptr[2 * blockIdx.x + 1], gs = ge - gb;  // [begin, end) pairs
     const int c0 = blockIdx.y * CH;
     int *sdist = smem_i;
     int *spd = sdist + max_gs;
@@ -680,6 +681,139 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
 #pragma unroll
         for (int c = 0; c < CH; ++c)
             if (c0 + c < d) leaf_out[v * d + c0 + c] = acc[c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// dense leaves of at least kLeafWarpMin vertices: one CTA per big leaf, one
+// warp per tile of 32 consecutive targets. All lanes of a warp visit the same
+// source at the same time, so every field-row and parent-distance load is a
+// shared-memory broadcast serving 32 pairs (the per-target walk above spends one
+// load per pair and is bound by shared-memory bandwidth). With the tile
+// [a, a + 32):
+//   sources after the tile, ascending: m_i = min(m_i, pd[j]) from
+//     m_i = min pd over (i, a + 31] (a warp suffix minimum);
+//   sources before the tile, descending: m_i = min(m_i, pd[j + 1]) from
+//     m_i = min pd over (a, i] (a warp prefix minimum);
+//   sources inside the tile: one ascending sweep for j > i and one descending
+//   sweep for j < i, each starting from an empty minimum.
+// ---------------------------------------------------------------------------
+constexpr int kLeafWarpMin = 64;
+
+__host__ __device__ inline size_t leaf_warp_smem_bytes(int max_leaf, int ch, int ftab_smem) {
+    const int sv = ch >= 8 ? ch + 4 : ch;
+    return size_t(2 * max_leaf + 4) * 4 + size_t(max_leaf) * sv * 4 + size_t(ftab_smem) * 4;
+}
+
+template <typename T, int CH>
+__global__ void __launch_bounds__(256) leaf_warp_kernel(const int32_t *__restrict__ big_lo,
+                                                        const int32_t *__restrict__ big_hi,
+                                                        const int32_t *__restrict__ leaf_vtx,
+                                                        const int32_t *__restrict__ leaf_dist,
+                                                        const int32_t *__restrict__ leaf_pdist, const T *__restrict__ F,
+                                                        int d, const float *__restrict__ ftab, int ftab_smem,
+                                                        float *__restrict__ leaf_out, int max_leaf) {
+    constexpr int SV = LeafStride<CH>::v;
+    constexpr int INF = 0x7fffffff;
+    extern __shared__ __align__(16) int smem_i[];
+    const int lb = big_lo[blockIdx.x], le = big_hi[blockIdx.x], ls = le - lb;
+    const int c0 = blockIdx.y * CH;
+    int *sdist = smem_i;
+    int *spd = sdist + max_leaf;
+    float *sx = reinterpret_cast<float *>(smem_i + ((2 * max_leaf + 3) & ~3));
+    float *sf = sx + max_leaf * SV;
+    for (int i = threadIdx.x; i < ls; i += blockDim.x) {
+        sdist[i] = leaf_dist[lb + i];
+        spd[i] = leaf_pdist[lb + i];
+        const int64_t v = leaf_vtx[lb + i];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) sx[i * SV + c] = (c0 + c < d) ? to_f<T>(F[v * d + c0 + c]) : 0.f;
+    }
+    for (int i = threadIdx.x; i < ftab_smem; i += blockDim.x) sf[i] = ftab[i];
+    __syncthreads();
+    const float *fsrc = ftab_smem > 0 ? sf : ftab;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int a = warp * 32; a < ls; a += nwarps * 32) {
+        const int i = a + lane;
+        const bool act = i < ls;
+        const int tend = min(a + 32, ls);                 // the tile is [a, tend)
+        const int di = act ? sdist[i] : 0;
+        float acc[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) acc[c] = 0.f;
+        auto add = [&](float f, int j) {
+            const float *x = sx + j * SV;
+            if (CH % 4 == 0) {
+#pragma unroll
+                for (int c = 0; c < CH; c += 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(x + c);
+                    acc[c] = fmaf(f, q.x, acc[c]);
+                    acc[c + 1] = fmaf(f, q.y, acc[c + 1]);
+                    acc[c + 2] = fmaf(f, q.z, acc[c + 2]);
+                    acc[c + 3] = fmaf(f, q.w, acc[c + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < CH; ++c) acc[c] = fmaf(f, x[c], acc[c]);
+            }
+        };
+        // inside the tile: j > i ascending, then j < i descending
+        int m = INF;
+        for (int j = a; j < tend; ++j) {
+            if (j > i) m = min(m, spd[j]);
+            const float f = act ? (j == i ? fsrc[0] : (j > i ? fsrc[di + sdist[j] - 2 * m] : 0.f)) : 0.f;
+            add(f, j);
+        }
+        m = INF;
+        for (int j = tend - 1; j >= a; --j) {
+            if (j < i) {
+                m = min(m, spd[j + 1]);
+                add(act ? fsrc[di + sdist[j] - 2 * m] : 0.f, j);
+            } else {
+                add(0.f, j);  // keeps the warp on one source per step (broadcast loads)
+            }
+        }
+        // warp scans of the tile's parent distances: suffix min over (i, tend - 1], prefix min over (a, i]
+        const int pd_here = act ? spd[i] : INF;
+        int suf, pre;
+        // suffix: s_lane = min pd[i + 1 .. tend - 1]
+        {
+            int v = (i + 1 < tend) ? spd[i + 1] : INF;   // element owned by this lane for the scan
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_down_sync(0xffffffffu, v, o);
+                if (lane + o < 32) v = min(v, u);
+            }
+            suf = v;
+        }
+        // prefix: p_lane = min pd[a + 1 .. i]
+        {
+            int v = (lane > 0 && act) ? pd_here : INF;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v = min(v, u);
+            }
+            pre = v;
+        }
+        // sources after the tile
+        m = suf;
+        for (int j = tend; j < ls; ++j) {
+            m = min(m, spd[j]);
+            add(act ? fsrc[di + sdist[j] - 2 * m] : 0.f, j);
+        }
+        // sources before the tile
+        m = pre;
+        for (int j = a - 1; j >= 0; --j) {
+            m = min(m, spd[j + 1]);
+            add(act ? fsrc[di + sdist[j] - 2 * m] : 0.f, j);
+        }
+        if (act) {
+            const int64_t v = leaf_vtx[lb + i];
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                if (c0 + c < d) leaf_out[v * d + c0 + c] = acc[c];
+        }
     }
 }
 

@@ -66,6 +66,10 @@ struct tfi_plan_s {
     int32_t *leaf_lo = nullptr, *leaf_hi = nullptr;
     uint8_t *in_leaf = nullptr;
     int32_t max_gs = 0, n_groups = 0;
+    // FP32-ALU leaves: groups of consecutive small leaves (one thread per target) and big leaves of
+    // at least kLeafWarpMin vertices (one warp per 32 targets, broadcast source loads)
+    int32_t *sgrp_ptr = nullptr, *big_lo = nullptr, *big_hi = nullptr;  // sgrp_ptr: [begin, end) per group
+    int32_t n_sgroups = 0, max_sgs = 1, n_big = 0, max_big = 1;
     float *ftab = nullptr;
     float2 *spectra = nullptr, *twiddle = nullptr;
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
@@ -105,8 +109,7 @@ struct tfi_plan_s {
     std::map<int, WorkLists> work;  // per channel count d
     // fork/join inside an apply: leaf terms and direct jobs run on their own
     // streams, concurrently with the bin sums and FFT jobs
-    // aux[0]: leaves (lowest priority), aux[1]: direct / Hankel jobs, aux[2]: the critical path
-    // bin sums -> FFT jobs (both highest priority)
+    // aux[0]: leaves, aux[1]: direct / Hankel jobs, aux[2]: the critical path bin sums -> FFT jobs
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev_crit = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_leaf = nullptr, ev_bucket = nullptr, ev_dir = nullptr;
@@ -169,10 +172,10 @@ struct tfi_plan_s {
 namespace {
 
 constexpr int kFftThreads = 256;
-constexpr int kFftSmemPairPoints = 1 << 12;  // points x pairs per CTA (32 KB, 4 CTAs per SM) below 2^13
+constexpr int kFftSmemPairPoints = 1 << 13;  // points x pairs per CTA (64 KB) for classes below 2^14
 
 int fft_pairs_per_cta(int lnp, int pairs) {
-    const int cap = lnp >= 12 ? 1 : (kFftSmemPairPoints >> lnp);
+    const int cap = lnp >= 13 ? 1 : (kFftSmemPairPoints >> lnp);
     return std::max(1, std::min(pairs, cap));
 }
 
@@ -249,12 +252,20 @@ constexpr int kLeafFtabSmemMax = 12288;  // f samples staged in shared memory up
 
 template <int CH, typename T>
 void launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s) {
-    if (p->n_groups == 0) return;
     const int fts = p->hp.ftab_len <= kLeafFtabSmemMax ? int(p->hp.ftab_len) : 0;
-    const size_t smem = tfi::dev::leaf_smem_bytes(p->max_gs, CH, fts);
-    dim3 grid(p->n_groups, (d + CH - 1) / CH);
-    tfi::dev::leaf_kernel<T, CH><<<grid, 256, smem, s>>>(p->lgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist,
-                                                         p->leaf_lo, p->leaf_hi, F, d, p->ftab, fts, lbuf, p->max_gs);
+    if (p->n_big > 0) {
+        const size_t smem = tfi::dev::leaf_warp_smem_bytes(p->max_big, CH, fts);
+        dim3 grid(p->n_big, (d + CH - 1) / CH);
+        tfi::dev::leaf_warp_kernel<T, CH><<<grid, 256, smem, s>>>(p->big_lo, p->big_hi, p->leaf_vtx, p->leaf_dist,
+                                                                  p->leaf_pdist, F, d, p->ftab, fts, lbuf, p->max_big);
+    }
+    if (p->n_sgroups > 0) {
+        const size_t smem = tfi::dev::leaf_smem_bytes(p->max_sgs, CH, fts);
+        dim3 grid(p->n_sgroups, (d + CH - 1) / CH);
+        tfi::dev::leaf_kernel<T, CH><<<grid, 256, smem, s>>>(p->sgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist,
+                                                             p->leaf_lo, p->leaf_hi, F, d, p->ftab, fts, lbuf,
+                                                             p->max_sgs);
+    }
 }
 
 constexpr int kLeafTcFtabSmem = 4096;  // f samples staged in shared memory by the tensor-core leaf kernel
@@ -353,6 +364,13 @@ tfi_status set_attributes() {
     LEAF_ATTR(__nv_bfloat16, 1) LEAF_ATTR(__nv_bfloat16, 2) LEAF_ATTR(__nv_bfloat16, 4)
     LEAF_ATTR(__nv_bfloat16, 8) LEAF_ATTR(__nv_bfloat16, 16)
 #undef LEAF_ATTR
+#define LEAF_WARP_ATTR(T, CH)                                                                                      \
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::leaf_warp_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  200 * 1024));
+    LEAF_WARP_ATTR(float, 1) LEAF_WARP_ATTR(float, 2) LEAF_WARP_ATTR(float, 4) LEAF_WARP_ATTR(float, 8)
+    LEAF_WARP_ATTR(float, 16) LEAF_WARP_ATTR(__nv_bfloat16, 1) LEAF_WARP_ATTR(__nv_bfloat16, 2)
+    LEAF_WARP_ATTR(__nv_bfloat16, 4) LEAF_WARP_ATTR(__nv_bfloat16, 8) LEAF_WARP_ATTR(__nv_bfloat16, 16)
+#undef LEAF_WARP_ATTR
     g_attr_done = true;
     return TFI_OK;
 }
@@ -569,6 +587,36 @@ tfi_status upload_plan(tfi_plan_t p) {
     if (tfi_status rc = p->upload(&p->leaf_hi, hp.leaf_hi)) return rc;
     if (tfi_status rc = p->upload(&p->in_leaf, hp.in_leaf)) return rc;
     p->n_groups = int32_t(hp.lgrp_ptr.size()) - 1;
+    {
+        // split the leaves: each big one alone; runs of consecutive small ones in groups of at most
+        // kLeafGroup vertices, as [begin, end) pairs (a big leaf ends the run before it)
+        std::vector<int32_t> sgrp, blo, bhi;
+        const int32_t nl = int32_t(hp.leaf_vtx.size());
+        int32_t gb = -1;
+        for (int32_t pos = 0; pos < nl;) {
+            const int32_t lo = hp.leaf_lo[size_t(pos)], hi = hp.leaf_hi[size_t(pos)];
+            if (hi - lo >= tfi::dev::kLeafWarpMin) {
+                if (gb >= 0) sgrp.insert(sgrp.end(), {gb, lo});
+                gb = -1;
+                blo.push_back(lo);
+                bhi.push_back(hi);
+                p->max_big = std::max(p->max_big, hi - lo);
+            } else if (gb < 0) {
+                gb = lo;
+            } else if (hi - gb > tfi::kLeafGroup) {
+                sgrp.insert(sgrp.end(), {gb, lo});
+                gb = lo;
+            }
+            pos = hi;
+        }
+        if (gb >= 0) sgrp.insert(sgrp.end(), {gb, nl});
+        for (size_t q = 0; q < sgrp.size(); q += 2) p->max_sgs = std::max(p->max_sgs, sgrp[q + 1] - sgrp[q]);
+        p->n_sgroups = int32_t(sgrp.size() / 2);
+        p->n_big = int32_t(blo.size());
+        if (tfi_status rc = p->upload(&p->sgrp_ptr, sgrp)) return rc;
+        if (tfi_status rc = p->upload(&p->big_lo, blo)) return rc;
+        if (tfi_status rc = p->upload(&p->big_hi, bhi)) return rc;
+    }
 
     {
         std::vector<tfi::tc::LeafTile> lt;
@@ -646,11 +694,11 @@ tfi_status upload_plan(tfi_plan_t p) {
     if (tfi_status rc = p->alloc(reinterpret_cast<void **>(&p->lbuf), size_t(hp.n) * dm * sizeof(float))) return rc;
     if (tfi_status rc = run_device_keys(p)) return rc;
     {
-        // the leaf terms are needed only by the final gather: their stream yields SMs to the bin
-        // sums and table jobs, whose chain decides when the gather can start
+        // internal streams above the caller's default priority; the bin sums are queued before the
+        // leaves so that their CTAs are dispatched first
         int least = 0, greatest = 0;
         TFI_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-        TFI_CUDA(cudaStreamCreateWithPriority(&p->aux[0], cudaStreamNonBlocking, least));
+        TFI_CUDA(cudaStreamCreateWithPriority(&p->aux[0], cudaStreamNonBlocking, greatest));
         TFI_CUDA(cudaStreamCreateWithPriority(&p->aux[1], cudaStreamNonBlocking, greatest));
         TFI_CUDA(cudaStreamCreateWithPriority(&p->aux[2], cudaStreamNonBlocking, greatest));
     }
