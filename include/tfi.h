@@ -106,6 +106,11 @@ typedef struct {
                                    channel-aware cost model (at max_channels) ranks it below
                                    direct summation and the FFT */
 #define TFI_PLAN_HANKEL_ALL 8   /* every qualifying job uses the Hankel evaluator */
+#define TFI_PLAN_SWEEP_AUTO 32  /* exponential-sum kernels: each table (a call's cross table or a
+                                   component's correction) is evaluated by the Algorithm 7 sweeps
+                                   when their cost, J (6 per bin + 4 per backbone run) per channel,
+                                   is below that of the evaluator the cost model picked otherwise;
+                                   ignored for other kernels */
 #define TFI_PLAN_LEAF_ALU   16  /* dense leaves on the FP32 ALUs for every d (by default BF16 applies
                                    with d >= 64 sum leaves as f(D) x F products on the tensor cores:
                                    tcgen05 kind::tf32, f(D) split into hi + lo; FP32 applies always

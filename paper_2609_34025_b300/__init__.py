@@ -64,6 +64,7 @@ EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_ho
                     "tfi_graph_destroy", "tfi_sinkhorn", "tfi_kernel_grad", "tfi_set_kernel", "tfi_last_error")
 STAGES = ("leaf", "bucket", "fft", "direct", "gather", "sweep", "hankel")
 HANKEL_MODES = {None: 0, False: 0, "auto": 4, "all": 8}
+SWEEP_MODES = {None: 0, False: 0, True: 2, "all": 2, "auto": 32}
 
 _lib = None
 
@@ -139,7 +140,7 @@ class Plan:
         ker = _Kernel(KERNEL_KINDS[kind], int(params.shape[0]), params.ctypes.data if params.size else None,
                       0 if tab is None else int(tab.shape[0]), None if tab is None else tab.ctypes.data)
         opt = _Options(float(delta), POLICIES[policy], int(leaf_max), int(max_channels),
-                       (1 if host_only else 0) | (2 if sweep else 0) | HANKEL_MODES[hankel] | (16 if leaf_alu else 0))
+                       (1 if host_only else 0) | SWEEP_MODES[sweep] | HANKEL_MODES[hankel] | (16 if leaf_alu else 0))
         h = ctypes.c_void_p()
         _check(lib().tfi_plan(ctypes.byref(tree), ctypes.byref(ker), ctypes.byref(opt), ctypes.byref(h)))
         self._h = h

@@ -711,9 +711,9 @@ __device__ __forceinline__ void fma2(float &a0, float &a1, float f, float x0, fl
 // ---------------------------------------------------------------------------
 constexpr int kLeafWarpMin = 64;
 
+// source rows are only read as broadcasts here, so they need no padding (stride CH)
 __host__ __device__ inline size_t leaf_warp_smem_bytes(int max_leaf, int ch, int ftab_smem) {
-    const int sv = ch >= 8 ? ch + 4 : ch;
-    return size_t(2 * max_leaf + 4) * 4 + size_t(max_leaf) * sv * 4 + size_t(ftab_smem) * 4;
+    return size_t(2 * max_leaf + 4) * 4 + size_t(max_leaf) * ch * 4 + size_t(ftab_smem) * 4;
 }
 
 template <typename T, int CH>
@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(256) leaf_warp_kernel(const int32_t *__restric
                                                         const int32_t *__restrict__ leaf_pdist, const T *__restrict__ F,
                                                         int d, const float *__restrict__ ftab, int ftab_smem,
                                                         float *__restrict__ leaf_out, int max_leaf) {
-    constexpr int SV = LeafStride<CH>::v;
+    constexpr int SV = CH;
     constexpr int INF = 0x7fffffff;
     extern __shared__ __align__(16) int smem_i[];
     const int lb = big_lo[blockIdx.x], le = big_hi[blockIdx.x], ls = le - lb;
@@ -860,6 +860,47 @@ struct SweepJobDev {
     int32_t sb, se, rb, m, cjb, cje;
 };
 
+// One warp per job and block of kSweepCH channels (blockIdx.y). Run sums are
+// reductions over keys: lanes take keys 32 apart, each accumulating the whole
+// channel block (lambda^r computed once per key and term), then a butterfly of
+// shuffles (fixed order: deterministic) leaves every lane with the totals; the
+// recurrences over the backbone runs are evaluated redundantly by all lanes.
+constexpr int kSweepCH = 16;
+
+__device__ __forceinline__ void sweep_row_acc(float *acc, const float *__restrict__ row, int nch, bool vec4, float w) {
+    if (vec4) {
+#pragma unroll
+        for (int c = 0; c < kSweepCH; c += 4) {
+            if (c < nch) {
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(row + c));
+                acc[c] = fmaf(w, q.x, acc[c]);
+                acc[c + 1] = fmaf(w, q.y, acc[c + 1]);
+                acc[c + 2] = fmaf(w, q.z, acc[c + 2]);
+                acc[c + 3] = fmaf(w, q.w, acc[c + 3]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < kSweepCH; ++c)
+            if (c < nch) acc[c] = fmaf(w, __ldg(row + c), acc[c]);
+    }
+}
+
+__device__ __forceinline__ void sweep_warp_sum(float *acc) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int c = 0; c < kSweepCH; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    }
+}
+
+// row[c] (+)= w * g[c] for the channel block
+__device__ __forceinline__ void sweep_row_out(float *__restrict__ row, const float *g, int nch, float w, bool first) {
+#pragma unroll
+    for (int c = 0; c < kSweepCH; ++c)
+        if (c < nch) row[c] = first ? w * g[c] : row[c] + w * g[c];
+}
+
 template <int WARPS>
 __global__ void sweep_g_kernel(const SweepJobDev *__restrict__ jobs, int n_jobs, const int32_t *__restrict__ key_r,
                                const int32_t *__restrict__ key_x, const int32_t *__restrict__ sw_keys,
@@ -869,41 +910,59 @@ __global__ void sweep_g_kernel(const SweepJobDev *__restrict__ jobs, int n_jobs,
     const int w = blockIdx.x * WARPS + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (w >= n_jobs) return;
     const SweepJobDev jb = jobs[w];
-    for (int c = lane; c < d; c += 32) {
-        for (int l = 0; l < J; ++l) {
-            const float b = beta[l], cl = coef[l];
-            float fw = 0.f;
-            int prev_x = 0;
-            for (int t = 0; t < jb.m; ++t) {
-                const int e0 = sw_run[jb.rb + t], e1 = sw_run[jb.rb + t + 1];
-                const int x = key_x[sw_keys[e0]];
-                float a = 0.f;
-                for (int e = e0; e < e1; ++e) {
-                    const int k = sw_keys[e];
-                    a += expf(-b * float(key_r[k])) * kbuf[int64_t(k) * d + c];
-                }
-                fw = t == 0 ? a : a + expf(-b * float(x - prev_x)) * fw;
-                scratch[(int64_t(jb.rb + t) * 2) * d + c] = fw;
-                scratch[(int64_t(jb.rb + t) * 2 + 1) * d + c] = a;
-                prev_x = x;
+    const int c0 = blockIdx.y * kSweepCH, nch = min(kSweepCH, d - c0);
+    const bool vec4 = (d % 4) == 0;
+    for (int l = 0; l < J; ++l) {
+        const float b = beta[l], cl = coef[l];
+        float fw[kSweepCH];
+        int prev_x = 0;
+        for (int t = 0; t < jb.m; ++t) {
+            const int e0 = sw_run[jb.rb + t], e1 = sw_run[jb.rb + t + 1];
+            const int x = key_x[sw_keys[e0]];
+            float a[kSweepCH];
+#pragma unroll
+            for (int c = 0; c < kSweepCH; ++c) a[c] = 0.f;
+            for (int e = e0 + lane; e < e1; e += 32) {
+                const int k = sw_keys[e];
+                sweep_row_acc(a, kbuf + int64_t(k) * d + c0, nch, vec4, expf(-b * float(key_r[k])));
             }
-            float bw = 0.f;
-            int next_x = 0;
-            for (int t = jb.m - 1; t >= 0; --t) {
-                const int e0 = sw_run[jb.rb + t], e1 = sw_run[jb.rb + t + 1];
-                const int x = key_x[sw_keys[e0]];
-                const float a = scratch[(int64_t(jb.rb + t) * 2 + 1) * d + c];
-                bw = t == jb.m - 1 ? a : a + expf(-b * float(next_x - x)) * bw;
-                const float g0 = scratch[(int64_t(jb.rb + t) * 2) * d + c] + bw - a;
-                for (int e = e0; e < e1; ++e) {
-                    const int k = sw_keys[e];
-                    const float v = cl * expf(-b * float(key_r[k])) * g0;
-                    float *dst = vbuf + int64_t(k) * d + c;
-                    *dst = l == 0 ? v : *dst + v;
-                }
-                next_x = x;
+            sweep_warp_sum(a);
+            const float dec = t == 0 ? 0.f : expf(-b * float(x - prev_x));
+#pragma unroll
+            for (int c = 0; c < kSweepCH; ++c) fw[c] = t == 0 ? a[c] : a[c] + dec * fw[c];
+            // lane c keeps channel c of (Fw, a) for the backward sweep
+            if (lane < nch) {
+                float fv = 0.f, av = 0.f;
+#pragma unroll
+                for (int c = 0; c < kSweepCH; ++c)
+                    if (c == lane) fv = fw[c], av = a[c];
+                scratch[(int64_t(jb.rb + t) * 2) * d + c0 + lane] = fv;
+                scratch[(int64_t(jb.rb + t) * 2 + 1) * d + c0 + lane] = av;
             }
+            prev_x = x;
         }
+        __syncwarp();
+        float bw[kSweepCH];
+        int next_x = 0;
+        for (int t = jb.m - 1; t >= 0; --t) {
+            const int e0 = sw_run[jb.rb + t], e1 = sw_run[jb.rb + t + 1];
+            const int x = key_x[sw_keys[e0]];
+            const float dec = t == jb.m - 1 ? 0.f : expf(-b * float(next_x - x));
+            float g0[kSweepCH];
+#pragma unroll
+            for (int c = 0; c < kSweepCH; ++c) {
+                const float av = c < nch ? scratch[(int64_t(jb.rb + t) * 2 + 1) * d + c0 + c] : 0.f;
+                const float fv = c < nch ? scratch[(int64_t(jb.rb + t) * 2) * d + c0 + c] : 0.f;
+                bw[c] = t == jb.m - 1 ? av : av + dec * bw[c];
+                g0[c] = fv + bw[c] - av;   // G_0 = Fw + Bw - a (a_s counted by both sweeps)
+            }
+            for (int e = e0 + lane; e < e1; e += 32) {
+                const int k = sw_keys[e];
+                sweep_row_out(vbuf + int64_t(k) * d + c0, g0, nch, cl * expf(-b * float(key_r[k])), l == 0);
+            }
+            next_x = x;
+        }
+        __syncwarp();
     }
 }
 
@@ -915,17 +974,18 @@ __global__ void sweep_e_kernel(const int32_t *__restrict__ ejobs, int n_jobs, co
     const int w = blockIdx.x * WARPS + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (w >= n_jobs) return;
     const JobDev jb = jobs[ejobs[w]];
-    for (int c = lane; c < d; c += 32) {
-        for (int l = 0; l < J; ++l) {
-            const float b = beta[l], cl = coef[l];
-            float e0v = 0.f;   // E_alpha[0] = sum_r lambda^r b_alpha[r]
-            for (int k = jb.kb; k < jb.ke; ++k) e0v += expf(-b * float(key_r[k])) * kbuf[int64_t(k) * d + c];
-            for (int k = jb.kb; k < jb.ke; ++k) {
-                const float v = cl * expf(-b * float(key_r[k])) * e0v;
-                float *dst = vbuf + int64_t(k) * d + c;
-                *dst = l == 0 ? v : *dst + v;
-            }
-        }
+    const int c0 = blockIdx.y * kSweepCH, nch = min(kSweepCH, d - c0);
+    const bool vec4 = (d % 4) == 0;
+    for (int l = 0; l < J; ++l) {
+        const float b = beta[l], cl = coef[l];
+        float e0v[kSweepCH];   // E_alpha[0] = sum_r lambda^r b_alpha[r]
+#pragma unroll
+        for (int c = 0; c < kSweepCH; ++c) e0v[c] = 0.f;
+        for (int k = jb.kb + lane; k < jb.ke; k += 32)
+            sweep_row_acc(e0v, kbuf + int64_t(k) * d + c0, nch, vec4, expf(-b * float(key_r[k])));
+        sweep_warp_sum(e0v);
+        for (int k = jb.kb + lane; k < jb.ke; k += 32)
+            sweep_row_out(vbuf + int64_t(k) * d + c0, e0v, nch, cl * expf(-b * float(key_r[k])), l == 0);
     }
 }
 

@@ -390,6 +390,11 @@ constexpr double kHankelMmaCost = 0.25;
 constexpr double kHankelStageCost = 1.0;
 constexpr double kHankelScanCost = 3.0;
 
+// Algorithm 7 sweeps, per exponential term and channel: lambda^r weighting in and
+// out per bin, one recurrence step per backbone run and direction.
+constexpr double kSweepCostPerKey = 6.0;
+constexpr double kSweepCostPerRun = 4.0;
+
 double hankel_cost(int32_t H, int32_t L, double ncols, double nk, int d) {
     const HankelLayout lay = hankel_layout(H, L);
     const double per_col = kHankelMmaCost * lay.NP * lay.KT + kHankelStageCost * lay.KT + kHankelScanCost * lay.S;
@@ -517,7 +522,7 @@ int sample_kernel(HostPlan &hp, std::string &err) {
     }
     hp.sw_coef.clear();
     hp.sw_beta.clear();
-    if (hp.flags & TFI_PLAN_SWEEP) {
+    if ((hp.flags & (TFI_PLAN_SWEEP | TFI_PLAN_SWEEP_AUTO)) && hp.f.kind == TFI_F_EXPSUM) {
         for (size_t i = 0; i + 1 < hp.f.params.size(); i += 2) {
             hp.sw_coef.push_back(float(hp.f.params[i]));
             hp.sw_beta.push_back(float(hp.f.params[i + 1] * hp.delta));
@@ -587,15 +592,25 @@ int flatten(HostPlan &hp, std::string &err) {
             const double cost_fft = kFftCostPerPointLog * np * std::max(1, lg) + kFftCostPerKey * nk;
             const bool fft_ok = lg <= kFftMaxLog;
             jb.mode = (fft_ok && cost_fft < nk * nk) ? 0 : 1;
+            double best = jb.mode == 0 ? cost_fft : nk * nk;
+            // occupied backbone columns (runs of equal coordinate)
+            int64_t ncols = 0;
+            if ((hp.flags & (TFI_PLAN_HANKEL | TFI_PLAN_HANKEL_ALL | TFI_PLAN_SWEEP_AUTO))) {
+                std::vector<int32_t> xs(hp.key_x.begin() + jb.kb, hp.key_x.begin() + jb.ke);
+                std::sort(xs.begin(), xs.end());
+                ncols = int64_t(std::unique(xs.begin(), xs.end()) - xs.begin());
+            }
             const bool hk_ok = (hp.flags & (TFI_PLAN_HANKEL | TFI_PLAN_HANKEL_ALL)) && hankel_fits(maxr, maxx);
             if (hk_ok) {
-                int64_t ncols = 0;  // occupied backbone columns
-                std::vector<uint8_t> seen(size_t(maxx) + 1, 0);
-                for (int64_t k = jb.kb; k < jb.ke; ++k) seen[size_t(hp.key_x[size_t(k)])] = 1;
-                for (uint8_t b : seen) ncols += b;
-                const double best = std::min(nk * nk, fft_ok ? cost_fft : nk * nk);
-                if ((hp.flags & TFI_PLAN_HANKEL_ALL) || hankel_cost(maxr, maxx, double(ncols), nk, hp.max_channels) < best)
+                const double ch = hankel_cost(maxr, maxx, double(ncols), nk, hp.max_channels);
+                if ((hp.flags & TFI_PLAN_HANKEL_ALL) || ch < best) {
                     jb.mode = 3;
+                    best = ch;
+                }
+            }
+            if ((hp.flags & TFI_PLAN_SWEEP_AUTO) && hp.f.kind == TFI_F_EXPSUM) {
+                const double J = double(hp.f.params.size() / 2);
+                if (J * (kSweepCostPerKey * nk + kSweepCostPerRun * double(ncols)) < best) jb.mode = 2;
             }
             hp.jobs[size_t(joff[c]) + j] = jb;
         }
@@ -603,10 +618,15 @@ int flatten(HostPlan &hp, std::string &err) {
         cb = CallBins();
     });
     if (hp.flags & TFI_PLAN_SWEEP) {
-        // Algorithm 7: every table of a call is produced by its sweep job
+        // Algorithm 7 for every table
         for (Job &j : hp.jobs) j.mode = 2;
+    }
+    {
+        // one sweep job per call whose cross table is evaluated by the sweeps (its
+        // components' corrections are separate jobs, swept or not by their own mode)
         for (size_t c = 0; c < C; ++c) {
             const Job &g = hp.jobs[size_t(joff[c])];
+            if (g.mode != 2) continue;
             SweepJob sj{};
             sj.sb = int32_t(hp.sw_keys.size());
             std::vector<int32_t> ks(size_t(g.ke - g.kb));

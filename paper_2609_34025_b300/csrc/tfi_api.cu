@@ -436,17 +436,21 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
             m_hk.done(1);
         }
         TFI_CUDA(cudaEventRecord(p->ev_dir, s_dir));
-        if (p->n_sweeps > 0) {
+        if (p->n_sweeps > 0 || p->n_sw_ejobs > 0) {
             StageMark m_sw(p, s_crit, TFI_STAGE_SWEEP);
             constexpr int WARPS = 4;
-            tfi::dev::sweep_g_kernel<WARPS><<<(p->n_sweeps + WARPS - 1) / WARPS, 32 * WARPS, 0, s_crit>>>(
-                p->sw_jobs, p->n_sweeps, p->key_r, p->key_x, p->sw_keys, p->sw_run, d, p->kbuf, p->vbuf,
-                p->sw_scratch, p->sw_beta, p->sw_coef, p->sw_terms);
+            const unsigned cblocks = unsigned((d + tfi::dev::kSweepCH - 1) / tfi::dev::kSweepCH);
+            if (p->n_sweeps > 0)
+                tfi::dev::sweep_g_kernel<WARPS>
+                    <<<dim3(unsigned((p->n_sweeps + WARPS - 1) / WARPS), cblocks), 32 * WARPS, 0, s_crit>>>(
+                        p->sw_jobs, p->n_sweeps, p->key_r, p->key_x, p->sw_keys, p->sw_run, d, p->kbuf, p->vbuf,
+                        p->sw_scratch, p->sw_beta, p->sw_coef, p->sw_terms);
             if (p->n_sw_ejobs > 0)
-                tfi::dev::sweep_e_kernel<WARPS><<<(p->n_sw_ejobs + WARPS - 1) / WARPS, 32 * WARPS, 0, s_crit>>>(
-                    p->sw_ejobs, p->n_sw_ejobs, p->jobs, p->key_r, d, p->kbuf, p->vbuf, p->sw_beta, p->sw_coef,
-                    p->sw_terms);
-            m_sw.done(p->n_sw_ejobs > 0 ? 2 : 1);
+                tfi::dev::sweep_e_kernel<WARPS>
+                    <<<dim3(unsigned((p->n_sw_ejobs + WARPS - 1) / WARPS), cblocks), 32 * WARPS, 0, s_crit>>>(
+                        p->sw_ejobs, p->n_sw_ejobs, p->jobs, p->key_r, d, p->kbuf, p->vbuf, p->sw_beta, p->sw_coef,
+                        p->sw_terms);
+            m_sw.done((p->n_sweeps > 0) + (p->n_sw_ejobs > 0));
         }
         StageMark m_fft(p, s_crit, TFI_STAGE_FFT);
         for (size_t c = 0; c < wl->fft_lnp.size(); ++c) {
@@ -630,16 +634,16 @@ tfi_status upload_plan(tfi_plan_t p) {
     for (int g = 0; g < p->n_groups; ++g)
         p->max_gs = std::max(p->max_gs, hp.lgrp_ptr[size_t(g) + 1] - hp.lgrp_ptr[size_t(g)]);
     if (tfi_status rc = p->upload(&p->ftab, hp.ftab)) return rc;
-    if (!hp.sweeps.empty()) {
+    std::vector<int32_t> ej;  // component corrections evaluated by the sweeps
+    for (size_t j = 0; j < hp.jobs.size(); ++j)
+        if (hp.jobs[j].is_comp && hp.jobs[j].mode == 2 && hp.jobs[j].ke > hp.jobs[j].kb) ej.push_back(int32_t(j));
+    if (!hp.sweeps.empty() || !ej.empty()) {
         if (hp.sw_beta.empty()) return fail(TFI_ERR_ARG, "exponential-sweep plan without exponential terms");
         std::vector<tfi::dev::SweepJobDev> sj(hp.sweeps.size());
         for (size_t i = 0; i < sj.size(); ++i) {
             const tfi::SweepJob &q = hp.sweeps[i];
             sj[i] = tfi::dev::SweepJobDev{q.sb, q.se, q.rb, q.m, q.cjb, q.cje};
         }
-        std::vector<int32_t> ej;
-        for (size_t j = 0; j < hp.jobs.size(); ++j)
-            if (hp.jobs[j].is_comp && hp.jobs[j].ke > hp.jobs[j].kb) ej.push_back(int32_t(j));
         if (tfi_status rc = p->upload(&p->sw_jobs, sj)) return rc;
         if (tfi_status rc = p->upload(&p->sw_keys, hp.sw_keys)) return rc;
         if (tfi_status rc = p->upload(&p->sw_run, hp.sw_run)) return rc;
@@ -647,7 +651,8 @@ tfi_status upload_plan(tfi_plan_t p) {
         if (tfi_status rc = p->upload(&p->sw_beta, hp.sw_beta)) return rc;
         if (tfi_status rc = p->upload(&p->sw_coef, hp.sw_coef)) return rc;
         void *q = nullptr;
-        if (tfi_status rc = p->alloc(&q, hp.sw_run.size() * 2 * size_t(hp.max_channels) * 4)) return rc;
+        if (tfi_status rc = p->alloc(&q, std::max<size_t>(hp.sw_run.size(), 1) * 2 * size_t(hp.max_channels) * 4))
+            return rc;
         p->sw_scratch = static_cast<float *>(q);
         p->n_sweeps = int32_t(sj.size());
         p->n_sw_ejobs = int32_t(ej.size());
@@ -753,7 +758,8 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 template <typename T>
 tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
-    if (p->n_sweeps > 0) return fail(TFI_ERR_UNSUPPORTED, "tfi_apply_static does not run exponential-sweep plans");
+    if (p->n_sweeps > 0 || p->n_sw_ejobs > 0)
+        return fail(TFI_ERR_UNSUPPORTED, "tfi_apply_static does not run exponential-sweep plans");
     if (p->n_hankel > 0) return fail(TFI_ERR_UNSUPPORTED, "tfi_apply_static does not run Hankel-evaluator plans");
     if (tfi_status rc = set_attributes()) return rc;
     // work lists for d, built on the host (same grouping as the plan-owned path)

@@ -60,3 +60,29 @@ def test_sweep_requires_expsum():
     t = W.path(10)
     with pytest.raises(tfi.TfiError):
         tfi.Plan.from_spec(t, 1.0, W.KernelSpec.gauss(0.1), sweep=True)
+
+
+@pytest.mark.parametrize("make,delta,policy,d", [
+    (lambda: W.configs.sweep("rrt", n=1 << 15, d=16)["tree"], 1 / 64, "adaptive", 16),
+    (lambda: W.configs.sweep("caterpillar", n=1 << 12, d=16)["tree"], 1 / 64, "diameter", 16),
+    (lambda: W.configs.rrt_n2000()["tree"], 1.0, "diameter", 20),
+    (lambda: W.spider(6, 300), 1.0, "adaptive", 33),
+])
+def test_sweep_auto_mixed_evaluators(make, delta, policy, d):
+    # TFI_PLAN_SWEEP_AUTO: per table the cheaper of sweeps and FFT / direct; plans mix the modes
+    t = make()
+    spec = W.KernelSpec.expsum([1.0, -0.3], [0.1, 0.7])
+    p = tfi.Plan.from_spec(t, delta, spec, policy=policy, leaf_max=16, max_channels=d, sweep="auto")
+    info = p.info()
+    assert info["n_jobs_sweep"] > 0  # the large trees also keep small tables on FFT / direct
+    F = W.normal_field(t.n, d, seed=19)
+    y = p.apply(torch.from_numpy(F).cuda()).cpu().numpy()
+    rng = np.random.default_rng(2)
+    targets = np.sort(rng.choice(t.n, size=min(t.n, 300), replace=False)).astype(np.int32)
+    ref = brute.integrate(t, delta, spec, F.astype(np.float64), targets=targets)
+    assert _err(y[targets], ref) <= 1e-4
+    # the same operator as the plan without sweeps, up to rounding
+    q = tfi.Plan.from_spec(t, delta, spec, policy=policy, leaf_max=16, max_channels=d)
+    assert q.info()["n_jobs_sweep"] == 0
+    y2 = q.apply(torch.from_numpy(F).cuda()).cpu().numpy()
+    assert _err(y2[targets], ref) <= 1e-4

@@ -128,3 +128,17 @@ def test_hankel_selection_host_only():
     big = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], leaf_max=1, host_only=True,
                              hankel="all").info()
     assert big["n_jobs_fft"] + big["n_jobs_direct"] > 0
+
+
+def test_sweep_auto_selection_host_only():
+    # exponential sums: the cost model sends large tables to the sweeps and keeps small ones direct;
+    # other kernels never use the sweeps
+    cfg = W.configs.sweep(shape="rrt", n=1 << 14, d=16, kernel="exp")
+    mk = lambda spec, **kw: tfi.Plan.from_spec(cfg["tree"], cfg["delta"], spec, leaf_max=64, max_channels=16,
+                                              host_only=True, **kw).info()
+    auto = mk(cfg["kernel"], sweep="auto")
+    plain = mk(cfg["kernel"])
+    assert auto["n_jobs_sweep"] > 0 and plain["n_jobs_sweep"] == 0
+    assert auto["n_jobs_sweep"] + auto["n_jobs_fft"] + auto["n_jobs_direct"] == plain["n_jobs_fft"] + plain["n_jobs_direct"]
+    other = mk(W.KernelSpec.rational(1.0), sweep="auto")
+    assert other["n_jobs_sweep"] == 0
