@@ -294,10 +294,21 @@ __device__ __forceinline__ void fft_pass(float2 *Z, int padnp, int npair, int ln
         const int o = g & hmask;
         const int base = ((g >> lh_lo) << (lh_lo + RL)) + o;
         float2 *Zp = Z + p * padnp;
-        const int lb = line * ls;
+        // element t sits at e0 + t H; when H is a multiple of 32 the padding
+        // grows by H / 32 per element, so its slot is padded(e0) + t (H + H / 32)
+        const int e0 = line * ls + base * es, H = es << lh_lo;
+        int adr[R];
+        if ((H & 31) == 0) {
+            const int a0 = padded(e0), st = H + (H >> 5);
+#pragma unroll
+            for (int t = 0; t < R; ++t) adr[t] = a0 + t * st;
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) adr[t] = padded(e0 + t * H);
+        }
         float2 v[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = Zp[padded(lb + (base + (t << lh_lo)) * es)];
+        for (int t = 0; t < R; ++t) v[t] = Zp[adr[t]];
         // w^k with w = exp(-2 pi i o / (R h)), from the per-level entry
         // exp(-2 pi i o / (8 h)) by squaring
         float2 tws[R];
@@ -334,7 +345,7 @@ __device__ __forceinline__ void fft_pass(float2 *Z, int padnp, int npair, int ln
             idft_dit<RL>(v);
         }
 #pragma unroll
-        for (int t = 0; t < R; ++t) Zp[padded(lb + (base + (t << lh_lo)) * es)] = v[t];
+        for (int t = 0; t < R; ++t) Zp[adr[t]] = v[t];
     }
     __syncthreads();
 }
@@ -393,17 +404,26 @@ __device__ __forceinline__ void fused_bottom_pass(float2 *Z, int padnp, int npai
         const int p = w >> (llog + glog);
         float2 *Zp = Z + p * padnp;
         const int e0 = line * ls + (g << RL) * es;
+        int adr[R];
+        if ((es & 31) == 0) {
+            const int a0 = padded(e0), st = es + (es >> 5);
+#pragma unroll
+            for (int t = 0; t < R; ++t) adr[t] = a0 + t * st;
+        } else {
+#pragma unroll
+            for (int t = 0; t < R; ++t) adr[t] = padded(e0 + t * es);
+        }
         float2 sp[R], v[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) sp[q] = __ldg(S + e0 + q * es);
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = Zp[padded(e0 + t * es)];
+        for (int t = 0; t < R; ++t) v[t] = Zp[adr[t]];
         dft_dif<RL>(v);
 #pragma unroll
         for (int q = 0; q < R; ++q) v[q] = cmul(v[q], sp[q]);
         idft_dit<RL>(v);
 #pragma unroll
-        for (int t = 0; t < R; ++t) Zp[padded(e0 + t * es)] = v[t];
+        for (int t = 0; t < R; ++t) Zp[adr[t]] = v[t];
     }
     __syncthreads();
 }
@@ -428,16 +448,29 @@ __global__ void fft_kernel(const FftItem *__restrict__ items, const JobDev *__re
     const int NP = 1 << lnp, P1 = 1 << lp1, P2 = 1 << lp2;
     const int padnp = padded_size(NP);
     const int npair = it.npair;
-    for (int i = threadIdx.x; i < npair * padnp; i += blockDim.x) Z[i] = make_float2(0.f, 0.f);
+    {
+        // 16-byte stores over the pairs of slots, then the odd last slot if any
+        float4 *Z4 = reinterpret_cast<float4 *>(Z);
+        const int nz = npair * padnp;
+        for (int i = threadIdx.x; i < (nz >> 1); i += blockDim.x) Z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((nz & 1) && threadIdx.x == 0) Z[nz - 1] = make_float2(0.f, 0.f);
+    }
     __syncthreads();
+    const bool pair_io = (d & 1) == 0;   // channel pairs as one 8-byte access
     const int nk = jb.ke - jb.kb;
     // scatter bin sums; depth reversed so the depth correlation becomes a convolution
     for (int t = threadIdx.x; t < nk * npair; t += blockDim.x) {
         const int kk = t / npair, p = t - kk * npair;
         const int k = jb.kb + kk;
         const int ch = 2 * (it.pair0 + p);
-        const float re = kbuf[int64_t(k) * d + ch];
-        const float im = (ch + 1 < d) ? kbuf[int64_t(k) * d + ch + 1] : 0.f;
+        float re, im;
+        if (pair_io) {
+            const float2 q = __ldg(reinterpret_cast<const float2 *>(kbuf + int64_t(k) * d + ch));
+            re = q.x, im = q.y;
+        } else {
+            re = kbuf[int64_t(k) * d + ch];
+            im = (ch + 1 < d) ? kbuf[int64_t(k) * d + ch + 1] : 0.f;
+        }
         const int pos = ((P1 - key_r[k]) & (P1 - 1)) * P2 + key_x[k];
         Z[p * padnp + padded(pos)] = make_float2(re, im);
     }
@@ -463,8 +496,12 @@ __global__ void fft_kernel(const FftItem *__restrict__ items, const JobDev *__re
         const int k = jb.kb + kk;
         const int ch = 2 * (it.pair0 + p);
         const float2 v = Z[p * padnp + padded(key_r[k] * P2 + key_x[k])];
-        vbuf[int64_t(k) * d + ch] = v.x;
-        if (ch + 1 < d) vbuf[int64_t(k) * d + ch + 1] = v.y;
+        if (pair_io) {
+            *reinterpret_cast<float2 *>(vbuf + int64_t(k) * d + ch) = v;
+        } else {
+            vbuf[int64_t(k) * d + ch] = v.x;
+            if (ch + 1 < d) vbuf[int64_t(k) * d + ch + 1] = v.y;
+        }
     }
 }
 
