@@ -842,33 +842,44 @@ __global__ void __launch_bounds__(256) leaf_warp_kernel(const int32_t *__restric
             }
             pre = v;
         }
-        // sources after the tile, two per step (both f lookups in flight)
+        // sources after the tile, then before it, eight per step: the running
+        // minima are a cheap chain, so all eight f lookups are in flight together
+        constexpr int U = 8;
         m = suf;
         int j = tend;
-        for (; j + 1 < ls; j += 2) {
-            const int m0 = min(m, spd[j]);
-            m = min(m0, spd[j + 1]);
-            const float f0 = act ? fsrc[di + sdist[j] - 2 * m0] : 0.f;
-            const float f1 = act ? fsrc[di + sdist[j + 1] - 2 * m] : 0.f;
-            add(f0, j);
-            add(f1, j + 1);
+        for (; j + U <= ls; j += U) {
+            int mm[U];
+            float f[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                m = min(m, spd[j + u]);
+                mm[u] = m;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) f[u] = act ? fsrc[di + sdist[j + u] - 2 * mm[u]] : 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u) add(f[u], j + u);
         }
-        if (j < ls) {
+        for (; j < ls; ++j) {
             m = min(m, spd[j]);
             add(act ? fsrc[di + sdist[j] - 2 * m] : 0.f, j);
         }
-        // sources before the tile, two per step
         m = pre;
         j = a - 1;
-        for (; j >= 1; j -= 2) {
-            const int m0 = min(m, spd[j + 1]);
-            m = min(m0, spd[j]);
-            const float f0 = act ? fsrc[di + sdist[j] - 2 * m0] : 0.f;
-            const float f1 = act ? fsrc[di + sdist[j - 1] - 2 * m] : 0.f;
-            add(f0, j);
-            add(f1, j - 1);
+        for (; j - U + 1 >= 0; j -= U) {
+            int mm[U];
+            float f[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                m = min(m, spd[j - u + 1]);
+                mm[u] = m;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) f[u] = act ? fsrc[di + sdist[j - u] - 2 * mm[u]] : 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u) add(f[u], j - u);
         }
-        if (j >= 0) {
+        for (; j >= 0; --j) {
             m = min(m, spd[j + 1]);
             add(act ? fsrc[di + sdist[j] - 2 * m] : 0.f, j);
         }
