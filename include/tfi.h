@@ -309,9 +309,12 @@ tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t 
 #define TFI_STAGE_HANKEL 6   /* Hankel-matrix products on tensor cores (TFI_PLAN_HANKEL plans) */
 #define TFI_N_STAGES     7
 
-/* Per-stage timing with CUDA events recorded on the apply's stream. enable != 0
- * starts recording (and clears previous totals); 0 stops. Adds two event
- * records per stage per apply. */
+/* Per-stage timing with CUDA events recorded on the stream each stage runs on.
+ * enable = 1 starts recording (and clears previous totals); 2 does the same and
+ * also serialises the stages of every apply on the caller's stream (no side
+ * streams), so that each stage's time is its time alone on the GPU (a
+ * measurement mode: results are unchanged, the apply is slower); 0 stops and
+ * restores the concurrent schedule. Adds two event records per stage per apply. */
 tfi_status tfi_profile_enable(tfi_plan_t plan, int32_t enable);
 
 /* Synchronise the recorded events and return, per stage, the summed device time

@@ -250,9 +250,10 @@ class Plan:
         _check(lib().tfi_plan_get_info(self._h, ctypes.byref(inf)))
         return {name: getattr(inf, name) for name, _ in _Info._fields_}
 
-    def profile(self, enable: bool = True):
-        """Start (clearing totals) or stop per-stage CUDA-event timing."""
-        _check(lib().tfi_profile_enable(self._h, 1 if enable else 0))
+    def profile(self, enable: bool = True, serialize: bool = False):
+        """Start (clearing totals) or stop per-stage CUDA-event timing; serialize runs every stage
+        on the caller's stream, so each stage is timed alone."""
+        _check(lib().tfi_profile_enable(self._h, (2 if serialize else 1) if enable else 0))
 
     def profile_read(self) -> dict:
         """{stage: (milliseconds, launches)} summed since profiling was enabled (synchronises)."""

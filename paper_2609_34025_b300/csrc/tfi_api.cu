@@ -115,6 +115,7 @@ struct tfi_plan_s {
     cudaEvent_t ev_fork = nullptr, ev_leaf = nullptr, ev_bucket = nullptr, ev_dir = nullptr;
     // stage profiling (CUDA events on the apply stream)
     bool profiling = false;
+    bool serialize = false;  // profiling mode 2: every stage on the caller's stream
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     struct StageRec {
@@ -401,6 +402,7 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     if (tfi_status rc = set_attributes()) return rc;
     const int n = p->hp.n;
     cudaStream_t s_leaf = p->aux[0], s_dir = p->aux[1], s_crit = p->aux[2];
+    if (p->serialize) s_leaf = s_dir = s_crit = s;  // measurement mode: stages one after another
     // fork: everything on the side streams starts after the work already queued on s
     TFI_CUDA(cudaEventRecord(p->ev_fork, s));
     TFI_CUDA(cudaStreamWaitEvent(s_crit, p->ev_fork, 0));
@@ -1424,6 +1426,7 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info) {
 tfi_status tfi_profile_enable(tfi_plan_t plan, int32_t enable) {
     if (!plan) return fail(TFI_ERR_ARG, "null plan");
     plan->profiling = enable != 0;
+    plan->serialize = enable == 2;
     plan->prof.clear();
     plan->ev_used = 0;
     return TFI_OK;
