@@ -614,23 +614,51 @@ __global__ void gather_kernel(int n, const int32_t *__restrict__ vrec_ptr, const
         const int64_t u = t / chunks;
         const int c = int(t - u * chunks) * V;
         float acc[V];
-        const bool has_leaf = in_leaf[u] != 0;
+        if (in_leaf[u] != 0) {
+            load_row<float, V>(leaf + u * d + c, acc);
+        } else {
 #pragma unroll
-        for (int i = 0; i < V; ++i) acc[i] = has_leaf ? leaf[u * d + c + i] : 0.f;
+            for (int i = 0; i < V; ++i) acc[i] = 0.f;
+        }
         const int e1 = vrec_ptr[u + 1];
-        for (int e = vrec_ptr[u]; e < e1; ++e) {
-            const float *g = vbuf + int64_t(akey[e]) * d + c;
+        // up to four records at a time: their key and row loads are in flight together;
+        // the sum still runs in record order
+        for (int e = vrec_ptr[u]; e < e1; e += 4) {
+            int ka[4], kb[4];
 #pragma unroll
-            for (int i = 0; i < V; ++i) acc[i] += g[i];
-            const int b = bkey[e];
-            if (b >= 0) {
-                const float *h = vbuf + int64_t(b) * d + c;
+            for (int q = 0; q < 4; ++q) {
+                const bool ok = e + q < e1;
+                ka[q] = ok ? __ldg(akey + e + q) : -1;
+                kb[q] = ok ? __ldg(bkey + e + q) : -1;
+            }
+            float g[4][V], h[4][V];
 #pragma unroll
-                for (int i = 0; i < V; ++i) acc[i] -= h[i];
+            for (int q = 0; q < 4; ++q) {
+                load_row<float, V>(vbuf + int64_t(ka[q] < 0 ? ka[0] : ka[q]) * d + c, g[q]);
+                if (kb[q] >= 0) {
+                    load_row<float, V>(vbuf + int64_t(kb[q]) * d + c, h[q]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < V; ++i) h[q][i] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (ka[q] < 0) break;
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    acc[i] += g[q][i];
+                    if (kb[q] >= 0) acc[i] -= h[q][i];
+                }
             }
         }
+        T *dst = out + u * d + c;
+        if constexpr (V == 4 && sizeof(T) == 4) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        } else {
 #pragma unroll
-        for (int i = 0; i < V; ++i) out[u * d + c + i] = from_f<T>(acc[i]);
+            for (int i = 0; i < V; ++i) dst[i] = from_f<T>(acc[i]);
+        }
     }
 }
 

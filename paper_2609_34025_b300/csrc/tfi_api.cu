@@ -473,7 +473,7 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     // join, then (a6) gather
     TFI_CUDA(cudaStreamWaitEvent(s, p->ev_leaf, 0));
     StageMark m_gather(p, s, TFI_STAGE_GATHER);
-    if (d % 4 == 0)
+    if (d % 4 == 0 && (reinterpret_cast<uintptr_t>(out) % (4 * sizeof(T))) == 0)
         tfi::dev::gather_kernel<T, 4><<<grid_for(int64_t(n) * (d / 4), 256), 256, 0, s>>>(
             n, p->vrec_ptr, p->vrec_akey, p->vrec_bkey, p->vbuf, p->lbuf, p->in_leaf, d, out);
     else
