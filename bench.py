@@ -117,19 +117,32 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
+# source section of each stage's kernels in kernels.cuh (from one section header to the next)
+STAGE_SOURCE = {"fft": ("// FFT job kernel", "// direct job kernel")}
+
+
+def stage_source_hash(kernel_stage: str):
+    import hashlib
+
+    marks = STAGE_SOURCE.get(kernel_stage)
+    if marks is None:
+        return None
+    text = open(os.path.join(ROOT, "paper_2609_34025_b300", "csrc", "kernels.cuh")).read()
+    a, b = text.index(marks[0]), text.index(marks[1])
+    return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
+
+
 def ncu_traffic(kernel_stage: str):
     """DRAM bytes per apply for a stage from a committed ncu summary, if it was
-    taken on the current kernel sources; otherwise None."""
+    taken on the current source of that stage's kernels; otherwise None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
     except OSError:
         return None
-    import hashlib
-    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2609_34025_b300", "csrc", "kernels.cuh"), "rb").read())
     ent = rec.get(kernel_stage)
-    if not ent or ent.get("kernels_sha256") != h.hexdigest()[:16]:
+    if not ent or ent.get("source_sha256") != stage_source_hash(kernel_stage):
         return None
     return ent.get("bytes_per_apply")
 

@@ -761,20 +761,25 @@ __device__ __forceinline__ void fma2(float &a0, float &a1, float f, float x0, fl
 }
 
 // ---------------------------------------------------------------------------
-// dense leaves of at least kLeafWarpMin vertices: one CTA per big leaf, one
-// warp per tile of 32 consecutive targets. All lanes of a warp visit the same
-// source at the same time, so every field-row and parent-distance load is a
-// shared-memory broadcast serving 32 pairs (the per-target walk above spends one
-// load per pair and is bound by shared-memory bandwidth). With the tile
-// [a, a + 32):
-//   sources after the tile, ascending: m_i = min(m_i, pd[j]) from
-//     m_i = min pd over (i, a + 31] (a warp suffix minimum);
-//   sources before the tile, descending: m_i = min(m_i, pd[j + 1]) from
-//     m_i = min pd over (a, i] (a warp prefix minimum);
-//   sources inside the tile: one ascending sweep for j > i and one descending
+// dense leaves of at least kLeafWarpMin vertices: one CTA of eight warps per
+// big leaf, one warp per block of 32 kLeafWarpTargets consecutive targets, each
+// lane holding the targets a + lane + 32k (k < kLeafWarpTargets). All lanes
+// visit the same source at the same time, so every field-row and
+// parent-distance load is a shared-memory broadcast, and each row a lane loads
+// feeds all its targets (shared memory delivers 128 bytes per cycle to the
+// lanes whatever the addresses, so the reuse in registers is what lifts the
+// kernel off that limit; two targets per lane measured faster than one or four,
+// which cost occupancy and masked work on the block diagonal). With the block
+// [a, e):
+//   sources after the block, ascending: m_i = min(m_i, pd[j]) from
+//     m_i = min pd over (i, e - 1] (chunked warp suffix minima);
+//   sources before the block, descending: m_i = min(m_i, pd[j + 1]) from
+//     m_i = min pd over (a, i] (chunked warp prefix minima);
+//   sources inside the block: one ascending sweep for j > i and one descending
 //   sweep for j < i, each starting from an empty minimum.
 // ---------------------------------------------------------------------------
 constexpr int kLeafWarpMin = 64;
+constexpr int kLeafWarpTargets = 2;  // targets per lane in leaf_warp_kernel (a warp covers 64)
 
 // source rows are only read as broadcasts here, so they need no padding (stride CH)
 __host__ __device__ inline size_t leaf_warp_smem_bytes(int max_leaf, int ch, int ftab_smem) {
@@ -791,6 +796,7 @@ __global__ void __launch_bounds__(256) leaf_warp_kernel(const int32_t *__restric
                                                         float *__restrict__ leaf_out, int max_leaf) {
     constexpr int SV = CH;
     constexpr int INF = 0x7fffffff;
+    constexpr int TT = kLeafWarpTargets;  // targets per lane, 32 apart
     extern __shared__ __align__(16) int smem_i[];
     const int lb = big_lo[blockIdx.x], le = big_hi[blockIdx.x], ls = le - lb;
     const int c0 = blockIdx.y * CH;
@@ -809,113 +815,178 @@ __global__ void __launch_bounds__(256) leaf_warp_kernel(const int32_t *__restric
     __syncthreads();
     const float *fsrc = ftab_smem > 0 ? sf : ftab;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int a = warp * 32; a < ls; a += nwarps * 32) {
-        const int i = a + lane;
-        const bool act = i < ls;
-        const int tend = min(a + 32, ls);                 // the tile is [a, tend)
-        const int di = act ? sdist[i] : 0;
-        float acc[CH];
+    constexpr int BLK = 32 * TT;  // targets of one warp
+    for (int a = warp * BLK; a < ls; a += nwarps * BLK) {
+        const int bend = min(a + BLK, ls);  // the warp's targets are [a, bend)
+        int ti[TT], D[TT], m[TT];
+        bool act[TT];
+        float acc[TT][CH];
 #pragma unroll
-        for (int c = 0; c < CH; ++c) acc[c] = 0.f;
-        auto add = [&](float f, int j) {
+        for (int k = 0; k < TT; ++k) {
+            ti[k] = a + 32 * k + lane;
+            act[k] = ti[k] < ls;
+            D[k] = act[k] ? sdist[ti[k]] : 0;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) acc[k][c] = 0.f;
+        }
+        // one source row for all targets of the lane: f[k] x row
+        auto add = [&](const float *f, int j) {
             const float *x = sx + j * SV;
             if (CH % 4 == 0) {
 #pragma unroll
                 for (int c = 0; c < CH; c += 4) {
                     const float4 q = *reinterpret_cast<const float4 *>(x + c);
-                    fma2(acc[c], acc[c + 1], f, q.x, q.y);
-                    fma2(acc[c + 2], acc[c + 3], f, q.z, q.w);
+#pragma unroll
+                    for (int k = 0; k < TT; ++k) {
+                        fma2(acc[k][c], acc[k][c + 1], f[k], q.x, q.y);
+                        fma2(acc[k][c + 2], acc[k][c + 3], f[k], q.z, q.w);
+                    }
                 }
             } else {
 #pragma unroll
-                for (int c = 0; c < CH; ++c) acc[c] = fmaf(f, x[c], acc[c]);
+                for (int c = 0; c < CH; ++c) {
+                    const float q = x[c];
+#pragma unroll
+                    for (int k = 0; k < TT; ++k) acc[k][c] = fmaf(f[k], q, acc[k][c]);
+                }
             }
         };
-        // inside the tile: j > i ascending, then j < i descending
-        int m = INF;
-        for (int j = a; j < tend; ++j) {
-            if (j > i) m = min(m, spd[j]);
-            const float f = act ? (j == i ? fsrc[0] : (j > i ? fsrc[di + sdist[j] - 2 * m] : 0.f)) : 0.f;
+        // sources inside the block: j > i ascending, then j < i descending
+#pragma unroll
+        for (int k = 0; k < TT; ++k) m[k] = INF;
+        for (int j = a; j < bend; ++j) {
+            const int p = spd[j], dj = sdist[j];
+            float f[TT];
+#pragma unroll
+            for (int k = 0; k < TT; ++k) {
+                if (j > ti[k]) m[k] = min(m[k], p);
+                f[k] = !act[k] ? 0.f : j == ti[k] ? fsrc[0] : j > ti[k] ? fsrc[D[k] + dj - 2 * m[k]] : 0.f;
+            }
             add(f, j);
         }
-        m = INF;
-        for (int j = tend - 1; j >= a; --j) {
-            if (j < i) {
-                m = min(m, spd[j + 1]);
-                add(act ? fsrc[di + sdist[j] - 2 * m] : 0.f, j);
-            } else {
-                add(0.f, j);  // keeps the warp on one source per step (broadcast loads)
-            }
-        }
-        // warp scans of the tile's parent distances: suffix min over (i, tend - 1], prefix min over (a, i]
-        const int pd_here = act ? spd[i] : INF;
-        int suf, pre;
-        // suffix: s_lane = min pd[i + 1 .. tend - 1]
-        {
-            int v = (i + 1 < tend) ? spd[i + 1] : INF;   // element owned by this lane for the scan
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_down_sync(0xffffffffu, v, o);
-                if (lane + o < 32) v = min(v, u);
-            }
-            suf = v;
-        }
-        // prefix: p_lane = min pd[a + 1 .. i]
-        {
-            int v = (lane > 0 && act) ? pd_here : INF;
+        for (int k = 0; k < TT; ++k) m[k] = INF;
+        for (int j = bend - 1; j >= a; --j) {
+            const int p = spd[j + 1 < ls ? j + 1 : j], dj = sdist[j];
+            float f[TT];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v = min(v, u);
+            for (int k = 0; k < TT; ++k) {
+                if (j < ti[k]) m[k] = min(m[k], p);
+                f[k] = (act[k] && j < ti[k]) ? fsrc[D[k] + dj - 2 * m[k]] : 0.f;
             }
-            pre = v;
+            add(f, j);
         }
-        // sources after the tile, then before it, eight per step: the running
-        // minima are a cheap chain, so all eight f lookups are in flight together
-        constexpr int U = 8;
-        m = suf;
-        int j = tend;
+        // carries at the block edges from chunked warp scans of the block's parent
+        // distances P[t] = pd[a + t]: suffix min over (i, bend - 1], prefix min over (a, i]
+        int suf[TT], pre[TT];
+        {
+            int cmin[TT], cpre[TT];
+#pragma unroll
+            for (int k = 0; k < TT; ++k) {
+                const int t = 32 * k + lane;
+                // suffix within chunk k over elements t + 1 .. 32k + 31
+                int v = (a + t + 1 < bend && lane < 31) ? spd[a + t + 1] : INF;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_down_sync(0xffffffffu, v, o);
+                    if (lane + o < 32) v = min(v, u);
+                }
+                suf[k] = v;
+                // prefix within chunk k over elements 32k .. t, element 0 excluded
+                int w = (a + t < bend && t > 0) ? spd[a + t] : INF;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, w, o);
+                    if (lane >= o) w = min(w, u);
+                }
+                pre[k] = w;
+                cpre[k] = __shfl_sync(0xffffffffu, w, 31);   // min over the whole chunk (element 0 excluded)
+                const int e = (a + t < bend) ? spd[a + t] : INF;
+                int cm = e;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cm = min(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+                cmin[k] = cm;                                 // min over all of chunk k
+            }
+            // combine chunks: suffix adds the chunks after k (their first element
+            // included), prefix adds the chunks before k
+            int after = INF;
+#pragma unroll
+            for (int k = TT - 1; k >= 0; --k) {
+                suf[k] = min(suf[k], after);
+                after = min(after, cmin[k]);
+            }
+            int before = INF;
+#pragma unroll
+            for (int k = 0; k < TT; ++k) {
+                pre[k] = min(pre[k], before);
+                before = min(before, cpre[k]);
+            }
+        }
+        // sources after the block
+        constexpr int U = 4;
+#pragma unroll
+        for (int k = 0; k < TT; ++k) m[k] = suf[k];
+        int j = bend;
         for (; j + U <= ls; j += U) {
-            int mm[U];
-            float f[U];
+            float f[U][TT];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                m = min(m, spd[j + u]);
-                mm[u] = m;
-            }
+                const int p = spd[j + u], dj = sdist[j + u];
 #pragma unroll
-            for (int u = 0; u < U; ++u) f[u] = act ? fsrc[di + sdist[j + u] - 2 * mm[u]] : 0.f;
+                for (int k = 0; k < TT; ++k) {
+                    m[k] = min(m[k], p);
+                    f[u][k] = act[k] ? fsrc[D[k] + dj - 2 * m[k]] : 0.f;
+                }
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) add(f[u], j + u);
         }
         for (; j < ls; ++j) {
-            m = min(m, spd[j]);
-            add(act ? fsrc[di + sdist[j] - 2 * m] : 0.f, j);
+            const int p = spd[j], dj = sdist[j];
+            float f[TT];
+#pragma unroll
+            for (int k = 0; k < TT; ++k) {
+                m[k] = min(m[k], p);
+                f[k] = act[k] ? fsrc[D[k] + dj - 2 * m[k]] : 0.f;
+            }
+            add(f, j);
         }
-        m = pre;
+        // sources before the block
+#pragma unroll
+        for (int k = 0; k < TT; ++k) m[k] = pre[k];
         j = a - 1;
         for (; j - U + 1 >= 0; j -= U) {
-            int mm[U];
-            float f[U];
+            float f[U][TT];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                m = min(m, spd[j - u + 1]);
-                mm[u] = m;
-            }
+                const int p = spd[j - u + 1], dj = sdist[j - u];
 #pragma unroll
-            for (int u = 0; u < U; ++u) f[u] = act ? fsrc[di + sdist[j - u] - 2 * mm[u]] : 0.f;
+                for (int k = 0; k < TT; ++k) {
+                    m[k] = min(m[k], p);
+                    f[u][k] = act[k] ? fsrc[D[k] + dj - 2 * m[k]] : 0.f;
+                }
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) add(f[u], j - u);
         }
         for (; j >= 0; --j) {
-            m = min(m, spd[j + 1]);
-            add(act ? fsrc[di + sdist[j] - 2 * m] : 0.f, j);
-        }
-        if (act) {
-            const int64_t v = leaf_vtx[lb + i];
+            const int p = spd[j + 1], dj = sdist[j];
+            float f[TT];
 #pragma unroll
-            for (int c = 0; c < CH; ++c)
-                if (c0 + c < d) leaf_out[v * d + c0 + c] = acc[c];
+            for (int k = 0; k < TT; ++k) {
+                m[k] = min(m[k], p);
+                f[k] = act[k] ? fsrc[D[k] + dj - 2 * m[k]] : 0.f;
+            }
+            add(f, j);
+        }
+#pragma unroll
+        for (int k = 0; k < TT; ++k) {
+            if (act[k]) {
+                float *dst = leaf_out + int64_t(leaf_vtx[lb + ti[k]]) * d;
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    if (c0 + c < d) dst[c0 + c] = acc[k][c];
+            }
         }
     }
 }
