@@ -80,11 +80,12 @@ def main():
             for st, g in zip(streams, graphs):
                 st.wait_event(start)
                 g.launch(stream=st)
+            if a.grad:
+                # dL/df per head on its stream, parameter gradients left on the device
+                for p, g, x, st in zip(plans, G, X, streams):
+                    p.kernel_grad(g, x, stream=st, device_dtheta=True)
             for st in streams:
                 cur.wait_stream(st)
-            if a.grad:
-                for p, g, x in zip(plans, G, X):
-                    p.kernel_grad(g, x)
         return run
 
     results = {}

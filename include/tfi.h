@@ -224,9 +224,10 @@ tfi_status tfi_sinkhorn(tfi_plan_t plan, const float *a, const float *b, float *
  * grad_out and F (channels summed in the frequency domain), per leaf its pair
  * histogram; every sum runs in a fixed order (deterministic).
  *   grad_out, F: device, n x d, dtype. C: device FP64 array of C_len >=
- *   tfi_plan_info.hist_len entries, or NULL. dtheta: host FP64 array of
- *   n_params entries, or NULL (a TFI_F_TABLE kernel has no parameters); when
- *   given, the call synchronises `stream`. The first call allocates the
+ *   tfi_plan_info.hist_len entries, or NULL. dtheta: FP64 array of n_params
+ *   entries, or NULL (a TFI_F_TABLE kernel has no parameters). In device memory
+ *   it is written on `stream` (no synchronisation); in host memory the call
+ *   synchronises `stream` to copy it back. The first call allocates the
  *   gradient workspace. Needs every table of the plan to fit one shared-memory
  *   transform (P1 P2 <= 2^13), else TFI_ERR_UNSUPPORTED. */
 tfi_status tfi_kernel_grad(tfi_plan_t plan, const void *grad_out, const void *F, int32_t d, int32_t dtype, double *C,

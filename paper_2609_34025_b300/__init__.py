@@ -201,19 +201,33 @@ class Plan:
                                   int(iters), float(delta_reg), _stream_handle(stream)))
         return u, v
 
-    def kernel_grad(self, grad_out, F, stream=None):
-        """(C, dtheta): C[k] = dL/df(k delta) (CUDA float64) and dL/dtheta (numpy) for grad_out = dL/dout."""
+    def kernel_grad(self, grad_out, F, stream=None, device_dtheta=False):
+        """(C, dtheta): C[k] = dL/df(k delta) (CUDA float64) and dL/dtheta for grad_out = dL/dout;
+        dtheta is a numpy array (the call synchronises), or with device_dtheta a CUDA float64 tensor
+        written on the stream (no synchronisation)."""
         import torch
 
         for t in (grad_out, F):
             if not t.is_cuda or t.dim() != 2 or t.shape[0] != self.n or not t.is_contiguous():
                 raise ValueError("grad_out and F must be contiguous CUDA tensors of shape (n, d)")
-        L = self.info()["hist_len"]
+        if getattr(self, "_hist_len", None) is None:
+            self._hist_len = self.info()["hist_len"]
+        L = self._hist_len
         C = torch.empty(L, dtype=torch.float64, device=grad_out.device)
-        th = np.zeros(max(1, self.n_params), dtype=np.float64)
+        if device_dtheta:
+            th = torch.zeros(max(1, self.n_params), dtype=torch.float64, device=grad_out.device)
+            th_ptr = ctypes.c_void_p(th.data_ptr()) if self.n_params else None
+        else:
+            th = np.zeros(max(1, self.n_params), dtype=np.float64)
+            th_ptr = th.ctypes.data if self.n_params else None
         _check(lib().tfi_kernel_grad(self._h, ctypes.c_void_p(grad_out.data_ptr()), ctypes.c_void_p(F.data_ptr()),
                                      int(F.shape[1]), _dtype_code(F), ctypes.c_void_p(C.data_ptr()), L,
-                                     th.ctypes.data if self.n_params else None, _stream_handle(stream)))
+                                     th_ptr, _stream_handle(stream)))
+        if stream is not None:
+            # written on `stream`: keep the caching allocator from reusing them before it is done
+            C.record_stream(stream)
+            if device_dtheta:
+                th.record_stream(stream)
         return C, th[: self.n_params]
 
     def set_kernel(self, params=None, table=None):

@@ -30,25 +30,34 @@ using dev::padded_size;
 
 struct GradJob {
     int32_t kb, ke, lp1, lp2, maxr, maxx;
-    int64_t hoff;   // offset of this job's histogram (length 2 maxr + maxx + 1)
+    int64_t hoff;   // offset of this job's histograms: one per channel block, each 2 maxr + maxx + 1 long
+    int32_t mode;   // 0: FFT correlation per channel block; 1: direct (pair dot products, then binning)
+    int32_t pad;
+    int64_t moff;   // direct jobs: offset of the nk x nk pair dot products
 };
+
+constexpr int kGradCB = 32;  // channels per CTA of grad_fft_kernel (blockIdx.y = channel block)
 
 __device__ __forceinline__ int brev_bits(int v, int bits) { return bits ? int(__brev(uint32_t(v)) >> (32 - bits)) : 0; }
 
-// One CTA per job; shared memory: Z and ACC, padded_size(P1 P2) complex each.
+// One CTA per job and block of kGradCB channels; shared memory: Z and ACC,
+// padded_size(P1 P2) complex each. Each channel block bins its own histogram
+// (the transforms are linear, so the blocks' histograms add up to the job's).
 __global__ void grad_fft_kernel(const GradJob *__restrict__ jobs, const int32_t *__restrict__ key_r,
                                 const int32_t *__restrict__ key_x, int d, const float *__restrict__ gsum,
                                 const float *__restrict__ fsum, const float2 *__restrict__ tw,
                                 float *__restrict__ hist) {
     extern __shared__ float2 smz[];
     const GradJob jb = jobs[blockIdx.x];
+    if (jb.mode != 0) return;  // evaluated by grad_pair_dots / grad_direct_bin
     const int lp1 = jb.lp1, lp2 = jb.lp2, lnp = lp1 + lp2;
     const int NP = 1 << lnp, P1 = 1 << lp1, P2 = 1 << lp2;
     const int padnp = padded_size(NP);
     float2 *Z = smz, *ACC = smz + padnp;
     for (int i = threadIdx.x; i < padnp; i += blockDim.x) ACC[i] = make_float2(0.f, 0.f);
     const int nk = jb.ke - jb.kb;
-    for (int c = 0; c < d; ++c) {
+    const int cb0 = blockIdx.y * kGradCB, cb1 = min(d, cb0 + kGradCB);
+    for (int c = cb0; c < cb1; ++c) {
         for (int i = threadIdx.x; i < padnp; i += blockDim.x) Z[i] = make_float2(0.f, 0.f);
         __syncthreads();
         for (int t = threadIdx.x; t < nk; t += blockDim.x) {
@@ -82,8 +91,10 @@ __global__ void grad_fft_kernel(const GradJob *__restrict__ jobs, const int32_t 
     dev::fft_axis<true>(ACC, padnp, 1, lp1, P2, lp2, 1, true, tw, false);
     dev::fft_axis<true>(ACC, padnp, 1, lp2, 1, lp1, P2, false, tw, false);
     // H[j][b] = ACC / NP (real); bin j + min(b, P2 - b) = k
+    __syncthreads();
     const float inv = 1.f / float(NP);
     const int K = 2 * jb.maxr + jb.maxx + 1;
+    float *hblk = hist + int64_t(blockIdx.y) * K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         float acc = 0.f;
         const int j0 = max(0, k - jb.maxx), j1 = min(k, 2 * jb.maxr);
@@ -92,7 +103,91 @@ __global__ void grad_fft_kernel(const GradJob *__restrict__ jobs, const int32_t 
             acc += ACC[padded(j * P2 + (b & (P2 - 1)))].x;
             if (b > 0 && b < P2 - b) acc += ACC[padded(j * P2 + P2 - b)].x;
         }
-        hist[jb.hoff + k] = acc * inv;
+        hblk[jb.hoff + k] = acc * inv;
+    }
+}
+
+// The job's histogram (block 0's slot) = its first nblk channel blocks' histograms added in block order.
+__global__ void grad_block_reduce(const GradJob *__restrict__ jobs, int n_jobs, int nblk, float *__restrict__ hist) {
+    const GradJob jb = jobs[blockIdx.x];
+    if (jb.mode != 0) return;
+    const int K = 2 * jb.maxr + jb.maxx + 1;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        float acc = hist[jb.hoff + k];
+        for (int b = 1; b < nblk; ++b) acc += hist[jb.hoff + int64_t(b) * K + k];
+        hist[jb.hoff + k] = acc;
+    }
+}
+
+// Direct jobs, pass 1: M[i][l] = <gsum_i, fsum_l> over the d channels for all
+// pairs of the job's bins, a small nk x nk x d product: one CTA per (job, 32 x 32
+// tile, block of kGradDotCB channels; blockIdx.y), channels streamed through
+// shared memory in chunks of 32 (fixed order). Each channel block writes its own
+// partial product, at moff + blockIdx.y * nk * nk.
+constexpr int kGradDotCB = 512;
+
+__global__ void __launch_bounds__(256) grad_pair_dots(const GradJob *__restrict__ jobs,
+                                                      const int64_t *__restrict__ items, int d,
+                                                      const float *__restrict__ gsum, const float *__restrict__ fsum,
+                                                      float *__restrict__ M) {
+    __shared__ float As[32][33], Bs[32][33];
+    const int64_t it = items[blockIdx.x];  // job index << 16 | tile index (ti << 8 | tl)
+    const GradJob jb = jobs[it >> 16];
+    const int nk = jb.ke - jb.kb;
+    const int i0 = int((it >> 8) & 255) * 32, l0 = int(it & 255) * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // ty: 0..7, four rows each
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int cb0 = blockIdx.y * kGradDotCB, cb1 = min(d, cb0 + kGradDotCB);
+    for (int c0 = cb0; c0 < cb1; c0 += 32) {
+        for (int q = threadIdx.x; q < 32 * 32; q += 256) {
+            const int r = q >> 5, c = q & 31;
+            const bool cok = c0 + c < cb1;
+            As[r][c] = (i0 + r < nk && cok) ? gsum[int64_t(jb.kb + i0 + r) * d + c0 + c] : 0.f;
+            Bs[r][c] = (l0 + r < nk && cok) ? fsum[int64_t(jb.kb + l0 + r) * d + c0 + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int c = 0; c < 32; ++c) {
+            const float b = Bs[tx][c];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = fmaf(As[ty * 4 + u][c], b, acc[u]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + ty * 4 + u, l = l0 + tx;
+        if (i < nk && l < nk) M[jb.moff + int64_t(blockIdx.y) * nk * nk + int64_t(i) * nk + l] = acc[u];
+    }
+}
+
+// Direct jobs, pass 2: M[i][l] = sum of the ncb channel blocks' partials (in
+// block order), then H[k] = sum over pairs (i, l) in order with
+// r_i + r_l + |x_i - x_l| = k of M[i][l]; one CTA per job, one thread per k.
+__global__ void grad_direct_bin(const GradJob *__restrict__ jobs, const int32_t *__restrict__ djobs, int ncb,
+                                const int32_t *__restrict__ key_r, const int32_t *__restrict__ key_x,
+                                float *__restrict__ M, float *__restrict__ hist) {
+    const GradJob jb = jobs[djobs[blockIdx.x]];
+    const int nk = jb.ke - jb.kb;
+    const int K = 2 * jb.maxr + jb.maxx + 1;
+    const int64_t nn = int64_t(nk) * nk;
+    for (int64_t q = threadIdx.x; q < nn; q += blockDim.x) {
+        float acc = M[jb.moff + q];
+        for (int b = 1; b < ncb; ++b) acc += M[jb.moff + b * nn + q];
+        M[jb.moff + q] = acc;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        float acc = 0.f;
+        for (int i = 0; i < nk; ++i) {
+            const int ri = __ldg(key_r + jb.kb + i), xi = __ldg(key_x + jb.kb + i);
+            if (ri > k) continue;
+            for (int l = 0; l < nk; ++l) {
+                const int dd = ri + __ldg(key_r + jb.kb + l) + abs(xi - __ldg(key_x + jb.kb + l));
+                if (dd == k) acc += M[jb.moff + int64_t(i) * nk + l];
+            }
+        }
+        hist[jb.hoff + k] = acc;
     }
 }
 
@@ -104,7 +199,9 @@ template <>
 __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 
 // Leaves, pass 1: for every ordered pair (i, j) of a leaf, its distance and
-// <g_i, F_j>, at pair_off[leaf] + (i - lo) * s + (j - lo).
+// <g_i, F_j>, at pair_off[leaf] + (i - lo) * s + (j - lo). One warp per pair at a
+// time: lanes take channels 32 apart, then a butterfly of shuffles (fixed order)
+// adds the lanes' partial sums.
 template <typename T>
 __global__ void grad_leaf_pairs(const int32_t *__restrict__ leaf_ptr, const int64_t *__restrict__ pair_off,
                                 const int32_t *__restrict__ leaf_vtx, const int32_t *__restrict__ leaf_dist,
@@ -113,32 +210,27 @@ __global__ void grad_leaf_pairs(const int32_t *__restrict__ leaf_ptr, const int6
     const int lf = blockIdx.x;
     const int lo = leaf_ptr[lf], hi = leaf_ptr[lf + 1], s = hi - lo;
     const int64_t base = pair_off[lf];
-    for (int ii = threadIdx.x; ii < s; ii += blockDim.x) {
-        const int i = lo + ii;
-        const int64_t vi = leaf_vtx[i];
-        const int di = leaf_dist[i];
-        // self, then j = i+1 .. hi-1 (min over (i, j] grows), then j = i-1 .. lo (min over (j, i] grows)
-        int m = 0x7fffffff;
-        for (int step = 0; step < s; ++step) {
-            int j, dist;
-            if (step == 0) {
-                j = i;
-                dist = 0;
-            } else if (i + step < hi) {
-                j = i + step;
-                m = min(m, leaf_pdist[j]);
-                dist = di + leaf_dist[j] - 2 * m;
-            } else {
-                j = i - (step - (hi - 1 - i));
-                if (j == i - 1) m = 0x7fffffff;
-                m = min(m, leaf_pdist[j + 1]);
-                dist = di + leaf_dist[j] - 2 * m;
-            }
-            const int64_t vj = leaf_vtx[j];
-            float acc = 0.f;
-            for (int c = 0; c < d; ++c) acc = fmaf(ldf<T>(G + vi * d + c), ldf<T>(F + vj * d + c), acc);
-            pval[base + int64_t(ii) * s + (j - lo)] = acc;
-            pdst[base + int64_t(ii) * s + (j - lo)] = dist;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t q = warp; q < int64_t(s) * s; q += nw) {
+        const int ii = int(q / s), jj = int(q - int64_t(ii) * s);
+        const int i = lo + ii, j = lo + jj;
+        // dhat(i, j) = D(i) + D(j) - 2 min over (min(i, j), max(i, j)] of the parent distances
+        int dist = 0;
+        if (i != j) {
+            int m = 0x7fffffff;
+            for (int w = min(i, j) + 1 + lane; w <= max(i, j); w += 32) m = min(m, leaf_pdist[w]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+            dist = leaf_dist[i] + leaf_dist[j] - 2 * m;
+        }
+        const int64_t vi = leaf_vtx[i], vj = leaf_vtx[j];
+        float acc = 0.f;
+        for (int c = lane; c < d; c += 32) acc = fmaf(ldf<T>(G + vi * d + c), ldf<T>(F + vj * d + c), acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            pval[base + q] = acc;
+            pdst[base + q] = dist;
         }
     }
 }
@@ -160,15 +252,21 @@ __global__ void grad_leaf_hist(const int32_t *__restrict__ leaf_ptr, const int64
     }
 }
 
-// C[k] = sum over segments (fixed order) of sign * hist_segment[k], in FP64.
+// C[k] = sum over segments (fixed order) of sign * hist_segment[k], in FP64. One
+// warp per k: lanes take segments 32 apart, then a butterfly of shuffles (fixed
+// order) adds the lanes' partial sums.
 __global__ void grad_reduce(int n_seg, const int64_t *__restrict__ seg_off, const int32_t *__restrict__ seg_len,
                             const float *__restrict__ seg_sign, const float *__restrict__ hist, int64_t len,
                             double *__restrict__ C) {
-    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < len; k += int64_t(gridDim.x) * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5); k < len; k += warps) {
         double acc = 0.0;
-        for (int sgm = 0; sgm < n_seg; ++sgm)
+        for (int sgm = lane; sgm < n_seg; sgm += 32)
             if (k < seg_len[sgm]) acc += double(seg_sign[sgm]) * double(hist[seg_off[sgm] + k]);
-        C[k] = acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) C[k] = acc;
     }
 }
 

@@ -80,7 +80,10 @@ struct tfi_plan_s {
     float *sk_buf = nullptr;  // Sinkhorn: K x (n x max_channels), allocated on first use
     // kernel gradient (built on first use)
     bool grad_ready = false;
-    int32_t n_gjobs = 0, n_gleaves = 0, n_gseg = 0, g_max_lnp = 0;
+    int32_t n_gjobs = 0, n_gleaves = 0, n_gseg = 0, g_max_lnp = 0, g_nblk = 1;
+    int64_t *g_ditems = nullptr;
+    int32_t *g_djobs = nullptr, n_gditems = 0, n_gdjobs = 0;
+    float *g_M = nullptr;
     tfi::grad::GradJob *g_jobs = nullptr;
     int32_t *g_leaf_ptr = nullptr, *g_hist_len = nullptr, *g_seg_len = nullptr, *g_pdst = nullptr;
     int64_t *g_pair_off = nullptr, *g_hist_off = nullptr, *g_seg_off = nullptr;
@@ -996,18 +999,37 @@ tfi_status build_grad(tfi_plan_t p) {
     std::vector<int64_t> seg_off;
     std::vector<int32_t> seg_len;
     std::vector<float> seg_sign;
-    int64_t hoff = 0;
+    int64_t hoff = 0, moff = 0;
     int max_lnp = 0;
+    const int nblk = (hp.max_channels + tfi::grad::kGradCB - 1) / tfi::grad::kGradCB;
+    const int64_t ncb_max = (hp.max_channels + tfi::grad::kGradDotCB - 1) / tfi::grad::kGradDotCB;
+    std::vector<int64_t> ditems;  // direct jobs: (job << 16 | row tile << 8 | column tile) items
+    std::vector<int32_t> djobs;   // and the direct jobs' indices
     for (const tfi::Job &j : hp.jobs) {
         if (j.ke == j.kb) continue;
         if (j.lp1 + j.lp2 > 13)
             return fail(TFI_ERR_UNSUPPORTED, "kernel gradient needs every table to fit one shared-memory transform (P1 P2 <= 2^13)");
         const int32_t len = 2 * j.maxr + j.maxx + 1;
-        gj.push_back(tfi::grad::GradJob{int32_t(j.kb), int32_t(j.ke), j.lp1, j.lp2, j.maxr, j.maxx, hoff});
+        // direct evaluation (pair dot products over the channels, then binning) when it is cheaper
+        // than one FFT correlation per channel at max_channels
+        const double nk = double(j.ke - j.kb), D = double(hp.max_channels);
+        const double np = std::ldexp(1.0, j.lp1 + j.lp2);
+        const double cost_direct = 2 * nk * nk * D + double(len) * nk * nk;
+        const double cost_fft = D * (5 * np * std::max(1, j.lp1 + j.lp2) + 10 * np);
+        const int32_t mode = (nk <= 32 * 255 && cost_direct < cost_fft) ? 1 : 0;
+        gj.push_back(tfi::grad::GradJob{int32_t(j.kb), int32_t(j.ke), j.lp1, j.lp2, j.maxr, j.maxx, hoff, mode, 0,
+                                        mode ? moff : 0});
+        if (mode) {
+            const int32_t nt = int32_t((j.ke - j.kb + 31) / 32);
+            for (int32_t a = 0; a < nt; ++a)
+                for (int32_t b = 0; b < nt; ++b) ditems.push_back((int64_t(gj.size() - 1) << 16) | (a << 8) | b);
+            djobs.push_back(int32_t(gj.size() - 1));
+            moff += int64_t(j.ke - j.kb) * (j.ke - j.kb) * ncb_max;  // one partial product per channel block
+        }
         seg_off.push_back(hoff);
         seg_len.push_back(len);
         seg_sign.push_back(j.is_comp ? -1.f : 1.f);
-        hoff += len;
+        hoff += int64_t(len) * nblk;  // one histogram per channel block; the job's sum lands in the first
         max_lnp = std::max(max_lnp, j.lp1 + j.lp2);
     }
     std::vector<int32_t> leaf_ptr(1, 0), hist_len;
@@ -1051,6 +1073,13 @@ tfi_status build_grad(tfi_plan_t p) {
     p->n_gleaves = int32_t(hp.leaves.size());
     p->n_gseg = int32_t(seg_off.size());
     p->g_max_lnp = max_lnp;
+    p->g_nblk = nblk;
+    if (tfi_status rc = p->upload(&p->g_ditems, ditems)) return rc;
+    if (tfi_status rc = p->upload(&p->g_djobs, djobs)) return rc;
+    if (tfi_status rc = p->alloc(&q, size_t(std::max<int64_t>(moff, 1)) * 4)) return rc;
+    p->g_M = static_cast<float *>(q);
+    p->n_gditems = int32_t(ditems.size());
+    p->n_gdjobs = int32_t(djobs.size());
     p->grad_ready = true;
     return TFI_OK;
 }
@@ -1070,8 +1099,17 @@ tfi_status kernel_grad_impl(tfi_plan_t p, const T *G, const T *F, int d, double 
         const size_t smem = 2 * size_t(tfi::dev::padded_size(1 << p->g_max_lnp)) * sizeof(float2);
         TFI_CUDA(cudaFuncSetAttribute(tfi::grad::grad_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       int(std::max<size_t>(smem, 1024))));
-        tfi::grad::grad_fft_kernel<<<p->n_gjobs, 256, smem, s>>>(p->g_jobs, p->key_r, p->key_x, d, p->g_gbuf, p->kbuf,
-                                                                 p->twiddle, p->g_hist);
+        const int nb = (d + tfi::grad::kGradCB - 1) / tfi::grad::kGradCB;  // channel blocks with channels
+        tfi::grad::grad_fft_kernel<<<dim3(unsigned(p->n_gjobs), unsigned(nb)), 256, smem, s>>>(
+            p->g_jobs, p->key_r, p->key_x, d, p->g_gbuf, p->kbuf, p->twiddle, p->g_hist);
+        if (nb > 1) tfi::grad::grad_block_reduce<<<p->n_gjobs, 128, 0, s>>>(p->g_jobs, p->n_gjobs, nb, p->g_hist);
+        if (p->n_gditems > 0) {
+            const int ncb = (d + tfi::grad::kGradDotCB - 1) / tfi::grad::kGradDotCB;
+            tfi::grad::grad_pair_dots<<<dim3(unsigned(p->n_gditems), unsigned(ncb)), 256, 0, s>>>(
+                p->g_jobs, p->g_ditems, d, p->g_gbuf, p->kbuf, p->g_M);
+            tfi::grad::grad_direct_bin<<<p->n_gdjobs, 128, 0, s>>>(p->g_jobs, p->g_djobs, ncb, p->key_r, p->key_x,
+                                                                   p->g_M, p->g_hist);
+        }
     }
     if (p->n_gleaves > 0) {
         tfi::grad::grad_leaf_pairs<T><<<p->n_gleaves, 256, 0, s>>>(p->g_leaf_ptr, p->g_pair_off, p->leaf_vtx,
@@ -1081,17 +1119,24 @@ tfi_status kernel_grad_impl(tfi_plan_t p, const T *G, const T *F, int d, double 
                                                                p->g_hist_len, p->g_pval, p->g_pdst, p->g_hist);
     }
     double *Cd = C ? C : p->g_C;
-    tfi::grad::grad_reduce<<<grid_for(hp.hist_len, 256), 256, 0, s>>>(p->n_gseg, p->g_seg_off, p->g_seg_len,
-                                                                       p->g_seg_sign, p->g_hist, hp.hist_len, Cd);
+    tfi::grad::grad_reduce<<<grid_for(hp.hist_len * 32, 256), 256, 0, s>>>(p->n_gseg, p->g_seg_off, p->g_seg_len,
+                                                                            p->g_seg_sign, p->g_hist, hp.hist_len, Cd);
     TFI_CUDA(cudaGetLastError());
     if (dtheta && hp.f.kind != TFI_F_TABLE && !hp.f.params.empty()) {
         const int np = int(hp.f.params.size());
+        // dtheta in device memory: written on the stream, no synchronisation
+        cudaPointerAttributes attr{};
+        const bool on_dev = cudaPointerGetAttributes(&attr, dtheta) == cudaSuccess &&
+                            (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+        cudaGetLastError();  // a plain host pointer may leave an error from the query
         TFI_CUDA(cudaMemcpyAsync(p->g_params, hp.f.params.data(), size_t(np) * 8, cudaMemcpyHostToDevice, s));
         tfi::grad::grad_params<<<np, 256, 0, s>>>(hp.f.kind, p->g_params, np, hp.delta, Cd, hp.hist_len,
-                                                  p->g_dtheta);
+                                                  on_dev ? dtheta : p->g_dtheta);
         TFI_CUDA(cudaGetLastError());
-        TFI_CUDA(cudaMemcpyAsync(dtheta, p->g_dtheta, size_t(np) * 8, cudaMemcpyDeviceToHost, s));
-        TFI_CUDA(cudaStreamSynchronize(s));
+        if (!on_dev) {
+            TFI_CUDA(cudaMemcpyAsync(dtheta, p->g_dtheta, size_t(np) * 8, cudaMemcpyDeviceToHost, s));
+            TFI_CUDA(cudaStreamSynchronize(s));
+        }
     }
     return TFI_OK;
 }

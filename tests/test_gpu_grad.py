@@ -85,3 +85,37 @@ def test_set_kernel_and_learnable_autograd():
     p.set_kernel(params=new)
     y2 = p.apply(F.detach()).cpu().numpy()
     assert _nerr(y2, brute.integrate(t, 1.0, W.KernelSpec("expsum", new), Fn)) <= 1e-4
+
+
+@pytest.mark.parametrize("d,dtype,tol", [(100, torch.float32, 1e-4), (256, torch.bfloat16, 1e-4)])
+def test_grad_many_channel_blocks(d, dtype, tol):
+    # channels are split over CTAs in blocks of 32 and the blocks' histograms added in order:
+    # a ragged last block (d = 100) and the attention trees' width class (bf16, d = 256)
+    cfg = W.configs.attention(heads=1)
+    h = cfg["heads"][0]
+    p = _grad_case(h["tree"], 1.0, h["kernel"], d, 1, dtype=dtype, tol=tol)
+    # a later call with fewer channels ignores the blocks of the wider call
+    G = torch.from_numpy(W.normal_field(h["tree"].n, 8, seed=41)).cuda().to(dtype)
+    F = torch.from_numpy(W.normal_field(h["tree"].n, 8, seed=42)).cuda().to(dtype)
+    C, _ = p.kernel_grad(G, F)
+    ref = brute.corr_hist(h["tree"], 1.0, G.double().cpu().numpy(), F.double().cpu().numpy())
+    c = C.cpu().numpy()
+    ref = np.concatenate([ref, np.zeros(len(c) - len(ref))])
+    assert _nerr(c, ref) <= tol
+
+
+def test_grad_device_dtheta_on_a_side_stream():
+    # dtheta left on the device (no synchronisation) equals the host copy
+    cfg = W.configs.attention(heads=1)
+    h = cfg["heads"][0]
+    p = tfi.Plan.from_spec(h["tree"], 1.0, h["kernel"], leaf_max=4, max_channels=64)
+    G = torch.from_numpy(W.normal_field(h["tree"].n, 64, seed=51)).cuda()
+    F = torch.from_numpy(W.normal_field(h["tree"].n, 64, seed=52)).cuda()
+    C0, th0 = p.kernel_grad(G, F)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    C1, th1 = p.kernel_grad(G, F, stream=st, device_dtheta=True)
+    torch.cuda.current_stream().wait_stream(st)
+    torch.cuda.synchronize()
+    assert th1.is_cuda and np.array_equal(th1.cpu().numpy(), th0)
+    assert torch.equal(C0, C1)
