@@ -33,6 +33,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--heads", type=int, default=12)
     ap.add_argument("--grad", action="store_true", help="include the learnable-f gradient in the step")
+    ap.add_argument("--modes", default="default,auto,all,alu_leaf", help="comma-separated variants to run")
+    ap.add_argument("--s0", type=int, default=0, help="fixed leaf cutoff (0: tune per variant)")
+    ap.add_argument("--no-dense", dest="dense", action="store_false", help="skip the dense tensor-core path")
     a = ap.parse_args()
     import torch
 
@@ -89,9 +92,9 @@ def main():
         return run
 
     results = {}
-    for mode in ("default", "auto", "all", "alu_leaf"):
+    for mode in a.modes.split(","):
         best = None
-        for s0 in (1, 4, 16, 64, 196):
+        for s0 in ((a.s0,) if a.s0 > 0 else (1, 4, 16, 64, 196)):
             plans = make(mode, s0)
             graphs = [tfi.Graph(p, x, y, g, gx) for p, x, y, g, gx in zip(plans, X, Y, G, GX)]
             ms = timed(step_fn(plans, graphs), max(3, a.steps // 4), 2)
@@ -131,13 +134,16 @@ def main():
         for g in graphs:
             g.close()
     # dense f(D) F on tensor cores, forward and backward per head (synchronises per call)
-    plans = make("default", 64)
-    dense_ms = timed(lambda: [(p.dense_apply(x, y), p.dense_apply(g, gx)) for p, x, y, g, gx in
-                              zip(plans, X, Y, G, GX)], a.steps, a.warmup)
+    dense_ms = None
+    if a.dense:
+        plans = make("default", 64)
+        dense_ms = timed(lambda: [(p.dense_apply(x, y), p.dense_apply(g, gx)) for p, x, y, g, gx in
+                                  zip(plans, X, Y, G, GX)], a.steps, a.warmup)
     out = dict(metric="vertex.channel integrations/s (fwd+bwd" + (" + f grad" if a.grad else "") + ")",
                unit="vertex.channel/s", workload=f"attention_{a.heads}heads_n{n}_d{d}_bf16_expsum8",
                dtype="bf16", data="synthetic", evaluators=results,
-               dense_tensor_core=dict(ms_per_step=dense_ms, value=a.heads * n * d / (dense_ms * 1e-3)))
+               dense_tensor_core=None if dense_ms is None else
+               dict(ms_per_step=dense_ms, value=a.heads * n * d / (dense_ms * 1e-3)))
     print(json.dumps(out))
 
 
