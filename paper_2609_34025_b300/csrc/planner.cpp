@@ -717,13 +717,10 @@ int flatten(HostPlan &hp, std::string &err) {
             hp.lgrp_ptr.push_back(int32_t(lf.begin));
             gstart = lf.begin;
         }
-        int32_t dmax = 0;
         for (int64_t i = lf.begin; i < lf.end; ++i) {
             hp.leaf_lo[size_t(i)] = int32_t(lf.begin);
             hp.leaf_hi[size_t(i)] = int32_t(lf.end);
-            dmax = std::max(dmax, hp.leaf_dist[size_t(i)]);
         }
-        (void)dmax;
         need_leaf = std::max<int64_t>(need_leaf, lf.diam);
     }
     if (int64_t(hp.leaf_vtx.size()) > gstart) hp.lgrp_ptr.push_back(int32_t(hp.leaf_vtx.size()));

@@ -1534,10 +1534,9 @@ tfi_status tfi_stage_model(tfi_plan_t plan, int32_t d, int32_t dtype, double *by
     }
     bytes[TFI_STAGE_FFT] = kf * (2 * D * 4 + 8);
     bytes[TFI_STAGE_DIRECT] = kd * (2 * D * 4 + 8);
+    // per record two indices; per vertex its record range and leaf flag; every table row once (the
+    // rows a vertex reads are shared with the other vertices of its bin); leaf rows; output rows
     const double R = double(hp.recs.size());
-    double nb = 0;
-    for (int32_t b : hp.vrec_bkey) nb += b >= 0;
-    (void)nb;
     bytes[TFI_STAGE_GATHER] = R * 8 + double(hp.n) * (4 + 1) + K * D * 4 + nleaf * D * 4 + double(hp.n) * D * sin;
     return TFI_OK;
 }
