@@ -86,3 +86,19 @@ def test_sweep_auto_mixed_evaluators(make, delta, policy, d):
     assert q.info()["n_jobs_sweep"] == 0
     y2 = q.apply(torch.from_numpy(F).cuda()).cpu().numpy()
     assert _err(y2[targets], ref) <= 1e-4
+
+
+def test_sweep_auto_plan_in_a_cuda_graph():
+    # a captured fwd+bwd step of a mixed sweep / FFT / direct plan equals the eager applies
+    cfg = W.configs.sweep("rrt", n=1 << 14, d=16)
+    t = cfg["tree"]
+    p = tfi.Plan.from_spec(t, cfg["delta"], cfg["kernel"], leaf_max=64, max_channels=16, sweep="auto")
+    assert p.info()["n_jobs_sweep"] > 0
+    F = torch.from_numpy(W.normal_field(t.n, 16, seed=61)).cuda()
+    G = torch.from_numpy(W.normal_field(t.n, 16, seed=62)).cuda()
+    out, gF = torch.empty_like(F), torch.empty_like(F)
+    g = tfi.Graph(p, F, out, G, gF)
+    for _ in range(2):
+        g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(out, p.apply(F)) and torch.equal(gF, p.apply(G))
