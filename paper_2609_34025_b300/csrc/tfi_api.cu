@@ -16,6 +16,7 @@
 #include "hankel_tc.cuh"
 #include "leaf_tc.cuh"
 #include "kernels.cuh"
+#include "fft_x2.cuh"
 #include "planner.hpp"
 #include "tfi.h"
 
@@ -355,6 +356,7 @@ bool g_attr_done = false;
 tfi_status set_attributes() {
     if (g_attr_done) return TFI_OK;
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_x2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
     TFI_CUDA(cudaFuncSetAttribute(tfi::tc::hankel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
 #define LEAF_TC_ATTR(T, NB)                                                                                 \
     TFI_CUDA(cudaFuncSetAttribute(tfi::tc::leaf_tc_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
@@ -459,10 +461,19 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
         }
         StageMark m_fft(p, s_crit, TFI_STAGE_FFT);
         for (size_t c = 0; c < wl->fft_lnp.size(); ++c) {
-            const size_t smem = size_t(wl->fft_npair[c]) * size_t(tfi::dev::padded_size(1 << wl->fft_lnp[c])) *
-                                sizeof(float2);
-            tfi::dev::fft_kernel<<<wl->fft_count[c], kFftThreads, smem, s_crit>>>(
-                wl->d_fft + wl->fft_off[c], p->jobs, p->key_r, p->key_x, d, p->kbuf, p->vbuf, p->spectra, p->twiddle);
+            const int np = wl->fft_npair[c];
+            if (np >= 2) {
+                // two channel pairs per shared-memory element
+                const size_t smem = size_t((np + 1) / 2) * (size_t(1) << wl->fft_lnp[c]) * sizeof(ulonglong2);
+                tfi::dev::fft_x2_kernel<<<wl->fft_count[c], kFftThreads, smem, s_crit>>>(
+                    wl->d_fft + wl->fft_off[c], p->jobs, p->key_r, p->key_x, d, p->kbuf, p->vbuf, p->spectra,
+                    p->twiddle);
+            } else {
+                const size_t smem = size_t(np) * size_t(tfi::dev::padded_size(1 << wl->fft_lnp[c])) * sizeof(float2);
+                tfi::dev::fft_kernel<<<wl->fft_count[c], kFftThreads, smem, s_crit>>>(
+                    wl->d_fft + wl->fft_off[c], p->jobs, p->key_r, p->key_x, d, p->kbuf, p->vbuf, p->spectra,
+                    p->twiddle);
+            }
         }
         m_fft.done(int(wl->fft_lnp.size()));
         TFI_CUDA(cudaEventRecord(p->ev_crit, s_crit));
