@@ -118,18 +118,29 @@ def measured_peaks():
 
 
 # source section of each stage's kernels in kernels.cuh (from one section header to the next)
-STAGE_SOURCE = {"fft": ("// FFT job kernel", "// direct job kernel")}
+# source sections (file, first marker, end marker; None = whole file) that decide a
+# stage's DRAM traffic: a recorded ncu figure counts only while these are unchanged
+STAGE_SOURCE = {
+    "fft": [("kernels.cuh", "// FFT job kernel", "// direct job kernel"), ("fft_x2.cuh", None, None)],
+    "leaf": [("kernels.cuh", "// dense leaves of fewer than kLeafWarpMin", "// Exponential-sum sweeps"),
+             ("tfi_api.cu", "constexpr int kLeafWarpThreads", "constexpr int kLeafTcFtabSmem")],
+}
 
 
 def stage_source_hash(kernel_stage: str):
     import hashlib
 
-    marks = STAGE_SOURCE.get(kernel_stage)
-    if marks is None:
+    secs = STAGE_SOURCE.get(kernel_stage)
+    if secs is None:
         return None
-    text = open(os.path.join(ROOT, "paper_2609_34025_b300", "csrc", "kernels.cuh")).read()
-    a, b = text.index(marks[0]), text.index(marks[1])
-    return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for fname, first, end in secs:
+        text = open(os.path.join(ROOT, "paper_2609_34025_b300", "csrc", fname)).read()
+        if first is not None:
+            text = text[text.index(first):text.index(end)]
+        h.update(fname.encode())
+        h.update(text.encode())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_stage: str):

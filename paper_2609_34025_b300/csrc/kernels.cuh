@@ -761,9 +761,13 @@ __device__ __forceinline__ void fma2(float &a0, float &a1, float f, float x0, fl
 }
 
 // ---------------------------------------------------------------------------
-// dense leaves of at least kLeafWarpMin vertices: one CTA of eight warps per
-// big leaf, one warp per block of 32 kLeafWarpTargets consecutive targets, each
-// lane holding the targets a + lane + 32k (k < kLeafWarpTargets). All lanes
+// dense leaves of at least kLeafWarpMin vertices: CTAs of eight warps, each
+// running one or more big leaves packed on the host (a leaf takes ceil(size / 64)
+// warps, all eight when it is alone; the CTA stages its leaves one after
+// another), one warp per block of 32 kLeafWarpTargets consecutive targets, each
+// lane holding the targets a + lane + 32k (k < kLeafWarpTargets). Packing keeps
+// every warp busy where one CTA per leaf left the warps of a leaf below 512
+// vertices idle. Registers are capped for three CTAs per SM. All lanes
 // visit the same source at the same time, so every field-row and
 // parent-distance load is a shared-memory broadcast, and each row a lane loads
 // feeds all its targets (shared memory delivers 128 bytes per cycle to the
@@ -787,35 +791,61 @@ __host__ __device__ inline size_t leaf_warp_smem_bytes(int max_leaf, int ch, int
 }
 
 template <typename T, int CH>
-__global__ void __launch_bounds__(256) leaf_warp_kernel(const int32_t *__restrict__ big_lo,
-                                                        const int32_t *__restrict__ big_hi,
-                                                        const int32_t *__restrict__ leaf_vtx,
-                                                        const int32_t *__restrict__ leaf_dist,
-                                                        const int32_t *__restrict__ leaf_pdist, const T *__restrict__ F,
-                                                        int d, const float *__restrict__ ftab, int ftab_smem,
-                                                        float *__restrict__ leaf_out, int max_leaf) {
+__global__ void __launch_bounds__(256, 3) leaf_warp_kernel(const int32_t *__restrict__ big_ptr,
+                                                           const int32_t *__restrict__ big_lo,
+                                                           const int32_t *__restrict__ big_hi,
+                                                           const int32_t *__restrict__ leaf_vtx,
+                                                           const int32_t *__restrict__ leaf_dist,
+                                                           const int32_t *__restrict__ leaf_pdist, const T *__restrict__ F,
+                                                           int d, const float *__restrict__ ftab, int ftab_smem,
+                                                           float *__restrict__ leaf_out, int max_leaf) {
     constexpr int SV = CH;
     constexpr int INF = 0x7fffffff;
     constexpr int TT = kLeafWarpTargets;  // targets per lane, 32 apart
+    constexpr int BLK = 32 * TT;          // targets of one warp
     extern __shared__ __align__(16) int smem_i[];
-    const int lb = big_lo[blockIdx.x], le = big_hi[blockIdx.x], ls = le - lb;
+    // the CTA's leaves big_lo/hi[q0 .. q1), staged one after another (at most max_leaf vertices)
+    const int q0 = big_ptr[blockIdx.x], q1 = big_ptr[blockIdx.x + 1];
     const int c0 = blockIdx.y * CH;
     int *sdist = smem_i;
     int *spd = sdist + max_leaf;
     float *sx = reinterpret_cast<float *>(smem_i + ((2 * max_leaf + 3) & ~3));
     float *sf = sx + max_leaf * SV;
-    for (int i = threadIdx.x; i < ls; i += blockDim.x) {
-        sdist[i] = leaf_dist[lb + i];
-        spd[i] = leaf_pdist[lb + i];
-        const int64_t v = leaf_vtx[lb + i];
+    for (int q = q0, off = 0; q < q1; ++q) {
+        const int lo = big_lo[q], n = big_hi[q] - lo;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            sdist[off + i] = leaf_dist[lo + i];
+            spd[off + i] = leaf_pdist[lo + i];
+            const int64_t v = leaf_vtx[lo + i];
 #pragma unroll
-        for (int c = 0; c < CH; ++c) sx[i * SV + c] = (c0 + c < d) ? to_f<T>(F[v * d + c0 + c]) : 0.f;
+            for (int c = 0; c < CH; ++c) sx[(off + i) * SV + c] = (c0 + c < d) ? to_f<T>(F[v * d + c0 + c]) : 0.f;
+        }
+        off += n;
     }
     for (int i = threadIdx.x; i < ftab_smem; i += blockDim.x) sf[i] = ftab[i];
     __syncthreads();
     const float *fsrc = ftab_smem > 0 ? sf : ftab;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    constexpr int BLK = 32 * TT;  // targets of one warp
+    // this warp's leaf: the leaves take consecutive warps, ceil(size / BLK) each, or all
+    // warps when a leaf is alone; warps past the last leaf have nothing to do
+    const int lane = threadIdx.x & 31, cw = threadIdx.x >> 5, cwarps = blockDim.x >> 5;
+    int lb = 0, ls = 0, warp = -1, nwarps = 1, off = 0;
+    for (int q = q0, w0 = 0, o = 0; q < q1; ++q) {
+        const int n = big_hi[q] - big_lo[q];
+        const int W = q1 - q0 == 1 ? cwarps : min(cwarps - w0, (n + BLK - 1) / BLK);
+        if (cw >= w0 && cw < w0 + W) {
+            lb = big_lo[q];
+            ls = n;
+            warp = cw - w0;
+            nwarps = W;
+            off = o;
+        }
+        w0 += W;
+        o += n;
+    }
+    if (warp < 0) return;  // no block-wide barrier follows
+    sdist += off;
+    spd += off;
+    sx += off * SV;
     for (int a = warp * BLK; a < ls; a += nwarps * BLK) {
         const int bend = min(a + BLK, ls);  // the warp's targets are [a, bend)
         int ti[TT], D[TT], m[TT];

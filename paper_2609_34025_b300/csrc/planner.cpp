@@ -733,6 +733,7 @@ int flatten(HostPlan &hp, std::string &err) {
         if (j.mode == 1 || j.mode == 3) need = std::max(need, top);
     }
     hp.ftab_len = need + 1;
+    hp.leaf_ftab_len = need_leaf + 1;
     hp.hist_len = std::max(need_any, need_leaf) + 1;
     // FFT size classes in first-use order; their spectra depend on f
     hp.spec_class_off.assign(16 * 16, -1);

@@ -106,6 +106,7 @@ struct HostPlan {
     std::vector<SweepJob> sweeps;
     std::vector<float> sw_beta, sw_coef;                   // per term: decay per grid unit, coefficient
     int64_t ftab_len = 0;
+    int64_t leaf_ftab_len = 1;                             // samples a dense leaf reads: its largest diameter + 1
     int64_t hist_len = 0;                                  // 1 + largest grid distance any pair of a call can have
     std::vector<float> ftab;
     // FFT spectra per (lp1, lp2) class, bit-reversed order, scaled by 1/(P1 P2), interleaved re/im

@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <numeric>
+#include <cstdint>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -71,6 +73,9 @@ struct tfi_plan_s {
     // at least kLeafWarpMin vertices (one warp per 32 targets, broadcast source loads)
     int32_t *sgrp_ptr = nullptr, *big_lo = nullptr, *big_hi = nullptr;  // sgrp_ptr: [begin, end) per group
     int32_t n_sgroups = 0, max_sgs = 1, n_big = 0, max_big = 1;
+    // big leaves packed into CTAs of leaf_warp_kernel: CTA b runs leaves big_lo/hi[big_ptr[b] ..
+    // big_ptr[b + 1]), at most 8 warps of 64 targets and max_big vertices in all
+    int32_t *big_ptr = nullptr;
     float *ftab = nullptr;
     float2 *spectra = nullptr, *twiddle = nullptr;
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
@@ -253,16 +258,71 @@ int grid_for(int64_t work, int threads) {
     return int(std::max<int64_t>(1, std::min<int64_t>(b, 148 * 32)));
 }
 
+constexpr int kLeafWarpThreads = 256;  // leaf_warp_kernel CTAs: 8 warps
+
+// Packs the big leaves into CTAs of leaf_warp_kernel, largest leaf first: each leaf
+// needs ceil(size / 64) warps (64 targets per warp); a CTA takes leaves while their
+// warps fit in its 8 and their vertices in max(largest leaf, 512), best fit by free
+// warps among the open CTAs. Leaves larger than 512 vertices get a CTA of their own.
+void pack_big_leaves(const std::vector<int32_t> &lo, const std::vector<int32_t> &hi, std::vector<int32_t> &bptr,
+                     std::vector<int32_t> &blo, std::vector<int32_t> &bhi, int32_t *cap_out) {
+    constexpr int kWarps = kLeafWarpThreads / 32, kPer = 32 * tfi::dev::kLeafWarpTargets;
+    const size_t nl = lo.size();
+    std::vector<size_t> ord(nl);
+    std::iota(ord.begin(), ord.end(), size_t(0));
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return hi[a] - lo[a] > hi[b] - lo[b]; });
+    int32_t cap = kWarps * kPer;
+    for (size_t i = 0; i < nl; ++i) cap = std::max(cap, hi[i] - lo[i]);
+    struct Bin {
+        int warps, verts;
+        std::vector<size_t> leaves;
+    };
+    std::vector<Bin> bins;
+    std::vector<std::vector<size_t>> open(kWarps);  // open[r]: bins with r free warps (r >= 1)
+    for (size_t i : ord) {
+        const int n = hi[i] - lo[i];
+        const int w = std::min(kWarps, (n + kPer - 1) / kPer);
+        size_t pick = SIZE_MAX;
+        for (int r = w; r < kWarps && pick == SIZE_MAX; ++r)
+            if (!open[r].empty() && bins[open[r].back()].verts + n <= cap) {
+                pick = open[r].back();
+                open[r].pop_back();
+            }
+        if (pick == SIZE_MAX) {
+            pick = bins.size();
+            bins.push_back(Bin{0, 0, {}});
+        }
+        Bin &b = bins[pick];
+        b.warps += w;
+        b.verts += n;
+        b.leaves.push_back(i);
+        if (n <= kWarps * kPer && b.warps < kWarps) open[kWarps - b.warps].push_back(pick);
+    }
+    bptr.assign(1, 0);
+    blo.clear();
+    bhi.clear();
+    for (const Bin &b : bins) {
+        for (size_t i : b.leaves) {
+            blo.push_back(lo[i]);
+            bhi.push_back(hi[i]);
+        }
+        bptr.push_back(int32_t(blo.size()));
+    }
+    *cap_out = cap;
+}
+
 constexpr int kLeafFtabSmemMax = 12288;  // f samples staged in shared memory up to this many
 
 template <int CH, typename T>
 void launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s) {
-    const int fts = p->hp.ftab_len <= kLeafFtabSmemMax ? int(p->hp.ftab_len) : 0;
+    // leaves look f up at their own pair distances only: stage that prefix of the samples
+    const int fts = p->hp.leaf_ftab_len <= kLeafFtabSmemMax ? int(p->hp.leaf_ftab_len) : 0;
     if (p->n_big > 0) {
         const size_t smem = tfi::dev::leaf_warp_smem_bytes(p->max_big, CH, fts);
         dim3 grid(p->n_big, (d + CH - 1) / CH);
-        tfi::dev::leaf_warp_kernel<T, CH><<<grid, 256, smem, s>>>(p->big_lo, p->big_hi, p->leaf_vtx, p->leaf_dist,
-                                                                  p->leaf_pdist, F, d, p->ftab, fts, lbuf, p->max_big);
+        tfi::dev::leaf_warp_kernel<T, CH><<<grid, kLeafWarpThreads, smem, s>>>(
+            p->big_ptr, p->big_lo, p->big_hi, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, F, d, p->ftab, fts, lbuf,
+            p->max_big);
     }
     if (p->n_sgroups > 0) {
         const size_t smem = tfi::dev::leaf_smem_bytes(p->max_sgs, CH, fts);
@@ -285,7 +345,7 @@ size_t leaf_tc_smem(int fts) {
 
 template <typename T, int NB>
 void launch_leaf_tc_nb(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s) {
-    const int fts = p->hp.ftab_len <= kLeafTcFtabSmem ? int(p->hp.ftab_len) : 0;
+    const int fts = p->hp.leaf_ftab_len <= kLeafTcFtabSmem ? int(p->hp.leaf_ftab_len) : 0;
     dim3 grid(unsigned(p->n_leaf_tiles), unsigned((d + NB - 1) / NB));
     tfi::tc::leaf_tc_kernel<T, NB><<<grid, 256, leaf_tc_smem<T, NB>(fts), s>>>(
         p->leaf_tiles, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, p->leaf_lo, p->leaf_hi, F, d, p->ftab, fts, lbuf,
@@ -610,7 +670,7 @@ tfi_status upload_plan(tfi_plan_t p) {
     {
         // split the leaves: each big one alone; runs of consecutive small ones in groups of at most
         // kLeafGroup vertices, as [begin, end) pairs (a big leaf ends the run before it)
-        std::vector<int32_t> sgrp, blo, bhi;
+        std::vector<int32_t> sgrp, leaf_lo_big, leaf_hi_big;
         const int32_t nl = int32_t(hp.leaf_vtx.size());
         int32_t gb = -1;
         for (int32_t pos = 0; pos < nl;) {
@@ -618,9 +678,8 @@ tfi_status upload_plan(tfi_plan_t p) {
             if (hi - lo >= tfi::dev::kLeafWarpMin) {
                 if (gb >= 0) sgrp.insert(sgrp.end(), {gb, lo});
                 gb = -1;
-                blo.push_back(lo);
-                bhi.push_back(hi);
-                p->max_big = std::max(p->max_big, hi - lo);
+                leaf_lo_big.push_back(lo);
+                leaf_hi_big.push_back(hi);
             } else if (gb < 0) {
                 gb = lo;
             } else if (hi - gb > tfi::kLeafGroup) {
@@ -632,7 +691,10 @@ tfi_status upload_plan(tfi_plan_t p) {
         if (gb >= 0) sgrp.insert(sgrp.end(), {gb, nl});
         for (size_t q = 0; q < sgrp.size(); q += 2) p->max_sgs = std::max(p->max_sgs, sgrp[q + 1] - sgrp[q]);
         p->n_sgroups = int32_t(sgrp.size() / 2);
-        p->n_big = int32_t(blo.size());
+        std::vector<int32_t> bptr, blo, bhi;
+        pack_big_leaves(leaf_lo_big, leaf_hi_big, bptr, blo, bhi, &p->max_big);
+        p->n_big = int32_t(bptr.size()) - 1;
+        if (tfi_status rc = p->upload(&p->big_ptr, bptr)) return rc;
         if (tfi_status rc = p->upload(&p->sgrp_ptr, sgrp)) return rc;
         if (tfi_status rc = p->upload(&p->big_lo, blo)) return rc;
         if (tfi_status rc = p->upload(&p->big_hi, bhi)) return rc;
