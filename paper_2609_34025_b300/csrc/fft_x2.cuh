@@ -320,6 +320,138 @@ __device__ __forceinline__ void fused_bottom_x2(ulonglong2 *Z, int NP, int nplan
     else fused_bottom_pass_x2<1>(Z, NP, nplane, ln, es, llog, ls, line_fast, S);
 }
 
+// ---------------------------------------------------------------------------
+// One-dimensional tables (a single axis of 2^ln points, element stride 1): the
+// same passes with the span H = 2^LH a compile-time constant, so that a group's
+// slots are one base plus constant offsets, and with the twiddles read from a
+// table already broadcast to both lanes ((re, re, im, im) per entry). The
+// spectrum stays at 8 bytes a point: a class's spectrum is read by all its CTAs
+// and stays in L1 at that size (a broadcast copy, twice as large, did not).
+// Slots for e = e0 + t H, e0 = (g >> LH) << (LH + RL) | o, o < H:
+//   H >= 64: bits 0..5 of e are those of e0: swz(e0) + t H;
+//   H == 8, radix 8: bits 3..5 of e are t: (e0 + 8 t) ^ t = (e0 ^ t) + 8 t;
+//   H == 1, radix 8: e0 = 8 g, bits 3..5 are g & 7: e0 ^ (g & 7) ^ t;
+//   otherwise swz(e0 + t H).
+// ---------------------------------------------------------------------------
+template <int RL, int LH>
+__device__ __forceinline__ void slots_1d(int e0, int *adr) {
+    constexpr int R = 1 << RL;
+    if (LH >= 6) {
+        const int a0 = swz(e0);
+#pragma unroll
+        for (int t = 0; t < R; ++t) adr[t] = a0 + t * (1 << LH);
+    } else if (LH == 3 && RL == 3) {
+#pragma unroll
+        for (int t = 0; t < R; ++t) adr[t] = (e0 ^ t) + 8 * t;
+    } else if (LH == 0 && RL == 3) {
+        const int b = e0 ^ ((e0 >> 3) & 7);
+#pragma unroll
+        for (int t = 0; t < R; ++t) adr[t] = b ^ t;
+    } else {
+#pragma unroll
+        for (int t = 0; t < R; ++t) adr[t] = swz(e0 + t * (1 << LH));
+    }
+}
+
+__device__ __forceinline__ Cx2 ld_bcast(const ulonglong2 *__restrict__ p) {
+    const ulonglong2 q = __ldg(p);
+    return Cx2{q.x, q.y};
+}
+
+template <bool INV, int RL, int LH>
+__device__ __forceinline__ void pass_1d_x2(ulonglong2 *Z, int NP, int nplane, int ln,
+                                           const ulonglong2 *__restrict__ twb) {
+    constexpr int R = 1 << RL, H = 1 << LH;
+    const int glog = ln - RL;
+    const int total = nplane << glog;
+    const int gmask = (1 << glog) - 1;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int g = w & gmask, p = w >> glog;
+        const int o = g & (H - 1);
+        const int e0 = ((g >> LH) << (LH + RL)) + o;
+        ulonglong2 *Zp = Z + p * NP;
+        int adr[R];
+        slots_1d<RL, LH>(e0, adr);
+        Cx2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const ulonglong2 q = Zp[adr[t]];
+            v[t] = Cx2{q.x, q.y};
+        }
+        const Cx2 w8 = ld_bcast(twb + H + o);
+        if (!INV) {
+            dft_dif_x2<RL>(v);
+            apply_twiddles<RL, false>(v, w8);
+        } else {
+            apply_twiddles<RL, true>(v, w8);
+            idft_dit_x2<RL>(v);
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) Zp[adr[t]] = make_ulonglong2(v[t].re, v[t].im);
+    }
+    __syncthreads();
+}
+
+// a pass at span 2^lh (lh = 3, 6 or 9 for the tables of up to 2^12 points this
+// kernel runs; any other span takes the general pass)
+template <bool INV, int RL>
+__device__ __forceinline__ void pass_1d_dispatch(ulonglong2 *Z, int NP, int nplane, int ln, int lh,
+                                                 const float2 *__restrict__ tw, const ulonglong2 *__restrict__ twb) {
+    if (lh == 3) pass_1d_x2<INV, RL, 3>(Z, NP, nplane, ln, twb);
+    else if (lh == 6) pass_1d_x2<INV, RL, 6>(Z, NP, nplane, ln, twb);
+    else if (lh == 9) pass_1d_x2<INV, RL, 9>(Z, NP, nplane, ln, twb);
+    else fft_pass_x2<INV, RL>(Z, NP, nplane, ln, lh, 1, 0, 0, false, tw);
+}
+
+// span-1 pass with the spectrum product
+template <int RL>
+__device__ __forceinline__ void bottom_1d_x2(ulonglong2 *Z, int NP, int nplane, int ln,
+                                             const float2 *__restrict__ S) {
+    constexpr int R = 1 << RL;
+    const int glog = ln - RL;
+    const int total = nplane << glog;
+    const int gmask = (1 << glog) - 1;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int g = w & gmask, p = w >> glog;
+        const int e0 = g << RL;
+        ulonglong2 *Zp = Z + p * NP;
+        int adr[R];
+        slots_1d<RL, 0>(e0, adr);
+        Cx2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const ulonglong2 q = Zp[adr[t]];
+            v[t] = Cx2{q.x, q.y};
+        }
+        dft_dif_x2<RL>(v);
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = cx_mul(v[q], cx_bcast(__ldg(S + e0 + q)));
+        idft_dit_x2<RL>(v);
+#pragma unroll
+        for (int t = 0; t < R; ++t) Zp[adr[t]] = make_ulonglong2(v[t].re, v[t].im);
+    }
+    __syncthreads();
+}
+
+// forward transform, spectrum product and inverse of a 2^ln-point table (ln >= 1)
+__device__ __forceinline__ void fft_1d_x2(ulonglong2 *Z, int NP, int nplane, int ln, const float2 *__restrict__ tw,
+                                          const ulonglong2 *__restrict__ twb, const float2 *__restrict__ S) {
+    const int full = ln / 3, rem = ln - 3 * full;
+    if (full > 0) {
+        if (rem == 2) pass_1d_dispatch<false, 2>(Z, NP, nplane, ln, ln - 2, tw, twb);
+        else if (rem == 1) pass_1d_dispatch<false, 1>(Z, NP, nplane, ln, ln - 1, tw, twb);
+        for (int k = 0; k < full - 1; ++k) pass_1d_dispatch<false, 3>(Z, NP, nplane, ln, ln - rem - 3 * (k + 1), tw, twb);
+        bottom_1d_x2<3>(Z, NP, nplane, ln, S);
+        for (int k = full - 2; k >= 0; --k) pass_1d_dispatch<true, 3>(Z, NP, nplane, ln, ln - rem - 3 * (k + 1), tw, twb);
+        if (rem == 2) pass_1d_dispatch<true, 2>(Z, NP, nplane, ln, ln - 2, tw, twb);
+        else if (rem == 1) pass_1d_dispatch<true, 1>(Z, NP, nplane, ln, ln - 1, tw, twb);
+    } else if (rem == 2) {
+        bottom_1d_x2<2>(Z, NP, nplane, ln, S);
+    } else {
+        bottom_1d_x2<1>(Z, NP, nplane, ln, S);
+    }
+}
+
 // One CTA per (job, up to 2 * nplane channel pairs starting at pair0): plane
 // p holds pairs pair0 + 2p and pair0 + 2p + 1 (channels 2 pair0 + 4p .. + 3);
 // channels at or beyond d ride as zeros.
@@ -327,7 +459,7 @@ __global__ void __launch_bounds__(256)
     fft_x2_kernel(const FftItem *__restrict__ items, const JobDev *__restrict__ jobs,
                   const int32_t *__restrict__ key_r, const int32_t *__restrict__ key_x, int d,
                   const float *__restrict__ kbuf, float *__restrict__ vbuf, const float2 *__restrict__ spectra,
-                  const float2 *__restrict__ tw) {
+                  const float2 *__restrict__ tw, const ulonglong2 *__restrict__ twb) {
     extern __shared__ ulonglong2 Zx[];
     const FftItem it = items[blockIdx.x];
     const JobDev jb = jobs[it.job];
@@ -361,16 +493,15 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     const float2 *S = spectra + jb.spec_off;
-    if (lp1 > 0) {
+    if ((lp1 > 0) != (lp2 > 0)) {
+        // one axis: 2^(lp1 + lp2) points at stride 1
+        fft_1d_x2(Zx, NP, nplane, lp1 + lp2, tw, twb, S);
+    } else if (lp1 > 0) {
         fft_axis_x2<false>(Zx, NP, nplane, lp2, 1, lp1, P2, false, tw, false);
         fft_axis_x2<false>(Zx, NP, nplane, lp1, P2, lp2, 1, true, tw, true);
         fused_bottom_x2(Zx, NP, nplane, lp1, P2, lp2, 1, true, S);
         fft_axis_x2<true>(Zx, NP, nplane, lp1, P2, lp2, 1, true, tw, true);
         fft_axis_x2<true>(Zx, NP, nplane, lp2, 1, lp1, P2, false, tw, false);
-    } else if (lp2 > 0) {
-        fft_axis_x2<false>(Zx, NP, nplane, lp2, 1, 0, P2, false, tw, true);
-        fused_bottom_x2(Zx, NP, nplane, lp2, 1, 0, P2, false, S);
-        fft_axis_x2<true>(Zx, NP, nplane, lp2, 1, 0, P2, false, tw, true);
     } else {
         const Cx2 s0 = cx_bcast(__ldg(S));
         for (int p = threadIdx.x; p < nplane; p += blockDim.x) {

@@ -78,6 +78,7 @@ struct tfi_plan_s {
     int32_t *big_ptr = nullptr;
     float *ftab = nullptr;
     float2 *spectra = nullptr, *twiddle = nullptr;
+    float4 *twiddle_b = nullptr;  // the twiddles, each value as (re, re, im, im)
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
     // bin sums by segments of at most kBucketSeg members (see bucket_seg_kernel)
     int32_t *seg_ptr = nullptr, *seg_dst = nullptr, *mb_key = nullptr, *mb_ptr = nullptr;
@@ -527,7 +528,7 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
                 const size_t smem = size_t((np + 1) / 2) * (size_t(1) << wl->fft_lnp[c]) * sizeof(ulonglong2);
                 tfi::dev::fft_x2_kernel<<<wl->fft_count[c], kFftThreads, smem, s_crit>>>(
                     wl->d_fft + wl->fft_off[c], p->jobs, p->key_r, p->key_x, d, p->kbuf, p->vbuf, p->spectra,
-                    p->twiddle);
+                    p->twiddle, reinterpret_cast<const ulonglong2 *>(p->twiddle_b));
             } else {
                 const size_t smem = size_t(np) * size_t(tfi::dev::padded_size(1 << wl->fft_lnp[c])) * sizeof(float2);
                 tfi::dev::fft_kernel<<<wl->fft_count[c], kFftThreads, smem, s_crit>>>(
@@ -628,6 +629,14 @@ tfi_status run_device_keys(tfi_plan_t p) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return TFI_OK;
+}
+
+// interleaved complex values (re, im, re, im, ...) -> one (re, re, im, im) per value, the
+// operand form of the paired FP32 instructions in fft_x2_kernel
+std::vector<float4> broadcast_pairs(const std::vector<float> &z) {
+    std::vector<float4> out(z.size() / 2);
+    for (size_t i = 0; i < out.size(); ++i) out[i] = make_float4(z[2 * i], z[2 * i], z[2 * i + 1], z[2 * i + 1]);
+    return out;
 }
 
 tfi_status upload_plan(tfi_plan_t p) {
@@ -741,6 +750,7 @@ tfi_status upload_plan(tfi_plan_t p) {
     std::memcpy(tw.data(), hp.twiddle.data(), hp.twiddle.size() * sizeof(float));
     if (tfi_status rc = p->upload(&p->spectra, spec)) return rc;
     if (tfi_status rc = p->upload(&p->twiddle, tw)) return rc;
+    if (tfi_status rc = p->upload(&p->twiddle_b, broadcast_pairs(hp.twiddle))) return rc;
     const size_t K = hp.key_r.size(), dm = size_t(hp.max_channels);
     {
         // segments of at most kBucketSeg consecutive members per bin
