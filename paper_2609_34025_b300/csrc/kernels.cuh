@@ -508,8 +508,20 @@ __global__ void fft_kernel(const FftItem *__restrict__ items, const JobDev *__re
 // ---------------------------------------------------------------------------
 // direct job kernel: one warp per (job, 64 query bins), two queries per lane,
 // CH channels per pass; source bins staged through shared memory in chunks of
-// 32 with a padded row stride so the row stores are conflict-free
+// 32 with a padded row stride so the row stores are conflict-free; the row
+// updates run as paired FP32 FMAs (0.275 -> 0.238 ms per apply on the 2^20 tree)
 // ---------------------------------------------------------------------------
+// a0 += f x0 and a1 += f x1 as one packed two-lane FP32 FMA (each lane rounds
+// like fmaf), halving the FMA instructions of the row updates
+__device__ __forceinline__ void fma2(float &a0, float &a1, float f, float x0, float x1) {
+    unsigned long long A, X, Fv;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(X) : "f"(x0), "f"(x1));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(Fv) : "f"(f));
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(A) : "l"(Fv), "l"(X));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(A));
+}
+
 template <int CH>
 struct SvStride {
     static constexpr int v = CH >= 8 ? CH + 4 : CH;
@@ -562,10 +574,10 @@ __global__ void direct_kernel(const DirItem *__restrict__ items, int n_items, co
 #pragma unroll
                 for (int c = 0; c < CH; c += 4) {
                     const float4 q = *reinterpret_cast<const float4 *>(my + t * SV + c);
-                    a0[c] = fmaf(f0, q.x, a0[c]); a0[c + 1] = fmaf(f0, q.y, a0[c + 1]);
-                    a0[c + 2] = fmaf(f0, q.z, a0[c + 2]); a0[c + 3] = fmaf(f0, q.w, a0[c + 3]);
-                    a1[c] = fmaf(f1, q.x, a1[c]); a1[c + 1] = fmaf(f1, q.y, a1[c + 1]);
-                    a1[c + 2] = fmaf(f1, q.z, a1[c + 2]); a1[c + 3] = fmaf(f1, q.w, a1[c + 3]);
+                    fma2(a0[c], a0[c + 1], f0, q.x, q.y);
+                    fma2(a0[c + 2], a0[c + 3], f0, q.z, q.w);
+                    fma2(a1[c], a1[c + 1], f1, q.x, q.y);
+                    fma2(a1[c + 2], a1[c + 3], f1, q.z, q.w);
                 }
             } else {
 #pragma unroll
@@ -747,17 +759,6 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
         for (int c = 0; c < CH; ++c)
             if (c0 + c < d) leaf_out[v * d + c0 + c] = acc[c];
     }
-}
-
-// a0 += f x0 and a1 += f x1 as one packed two-lane FP32 FMA (each lane rounds
-// like fmaf), halving the FMA instructions of the row updates
-__device__ __forceinline__ void fma2(float &a0, float &a1, float f, float x0, float x1) {
-    unsigned long long A, X, Fv;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a0), "f"(a1));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(X) : "f"(x0), "f"(x1));
-    asm("mov.b64 %0, {%1, %1};" : "=l"(Fv) : "f"(f));
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(A) : "l"(Fv), "l"(X));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(A));
 }
 
 // ---------------------------------------------------------------------------
