@@ -695,7 +695,11 @@ __host__ __device__ inline size_t leaf_smem_bytes(int max_gs, int ch, int ftab_s
     return size_t(2 * max_gs + 4) * 4 + size_t(max_gs) * sv * 4 + size_t(ftab_smem) * 4;
 }
 
-template <typename T, int CH>
+// FS: the f samples are staged in shared memory (ftab_smem > 0). As a template
+// argument it lets the compiler emit shared-memory loads for the f lookups; a
+// pointer chosen at run time between shared and global memory makes them
+// generic loads.
+template <typename T, int CH, bool FS>
 __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__restrict__ leaf_vtx,
                             const int32_t *__restrict__ leaf_dist, const int32_t *__restrict__ leaf_pdist,
                             const int32_t *__restrict__ leaf_lo, const int32_t *__restrict__ leaf_hi,
@@ -718,7 +722,7 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
     }
     for (int i = threadIdx.x; i < ftab_smem; i += blockDim.x) sf[i] = ftab[i];
     __syncthreads();
-    const float *fsrc = ftab_smem > 0 ? sf : ftab;
+    const float *fsrc = FS ? sf : ftab;
     for (int i = threadIdx.x; i < gs; i += blockDim.x) {
         const int lo = leaf_lo[gb + i] - gb, hi = leaf_hi[gb + i] - gb;
         const int di = sdist[i];
@@ -791,7 +795,7 @@ __host__ __device__ inline size_t leaf_warp_smem_bytes(int max_leaf, int ch, int
     return size_t(2 * max_leaf + 4) * 4 + size_t(max_leaf) * ch * 4 + size_t(ftab_smem) * 4;
 }
 
-template <typename T, int CH>
+template <typename T, int CH, bool FS>  // FS as in leaf_kernel
 __global__ void __launch_bounds__(256, 3) leaf_warp_kernel(const int32_t *__restrict__ big_ptr,
                                                            const int32_t *__restrict__ big_lo,
                                                            const int32_t *__restrict__ big_hi,
@@ -825,7 +829,7 @@ __global__ void __launch_bounds__(256, 3) leaf_warp_kernel(const int32_t *__rest
     }
     for (int i = threadIdx.x; i < ftab_smem; i += blockDim.x) sf[i] = ftab[i];
     __syncthreads();
-    const float *fsrc = ftab_smem > 0 ? sf : ftab;
+    const float *fsrc = FS ? sf : ftab;
     // this warp's leaf: the leaves take consecutive warps, ceil(size / BLK) each, or all
     // warps when a leaf is alone; warps past the last leaf have nothing to do
     const int lane = threadIdx.x & 31, cw = threadIdx.x >> 5, cwarps = blockDim.x >> 5;
@@ -954,7 +958,7 @@ __global__ void __launch_bounds__(256, 3) leaf_warp_kernel(const int32_t *__rest
             }
         }
         // sources after the block
-        constexpr int U = 4;
+        constexpr int U = 2;  // sources per step (four spill at the 80-register cap)
 #pragma unroll
         for (int k = 0; k < TT; ++k) m[k] = suf[k];
         int j = bend;

@@ -321,16 +321,16 @@ void launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s) {
     if (p->n_big > 0) {
         const size_t smem = tfi::dev::leaf_warp_smem_bytes(p->max_big, CH, fts);
         dim3 grid(p->n_big, (d + CH - 1) / CH);
-        tfi::dev::leaf_warp_kernel<T, CH><<<grid, kLeafWarpThreads, smem, s>>>(
-            p->big_ptr, p->big_lo, p->big_hi, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, F, d, p->ftab, fts, lbuf,
-            p->max_big);
+        auto k = fts > 0 ? tfi::dev::leaf_warp_kernel<T, CH, true> : tfi::dev::leaf_warp_kernel<T, CH, false>;
+        k<<<grid, kLeafWarpThreads, smem, s>>>(p->big_ptr, p->big_lo, p->big_hi, p->leaf_vtx, p->leaf_dist,
+                                               p->leaf_pdist, F, d, p->ftab, fts, lbuf, p->max_big);
     }
     if (p->n_sgroups > 0) {
         const size_t smem = tfi::dev::leaf_smem_bytes(p->max_sgs, CH, fts);
         dim3 grid(p->n_sgroups, (d + CH - 1) / CH);
-        tfi::dev::leaf_kernel<T, CH><<<grid, 256, smem, s>>>(p->sgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist,
-                                                             p->leaf_lo, p->leaf_hi, F, d, p->ftab, fts, lbuf,
-                                                             p->max_sgs);
+        auto k = fts > 0 ? tfi::dev::leaf_kernel<T, CH, true> : tfi::dev::leaf_kernel<T, CH, false>;
+        k<<<grid, 256, smem, s>>>(p->sgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, p->leaf_lo, p->leaf_hi, F, d,
+                                  p->ftab, fts, lbuf, p->max_sgs);
     }
 }
 
@@ -424,19 +424,23 @@ tfi_status set_attributes() {
                                   227 * 1024));
     LEAF_TC_ATTR(__nv_bfloat16, 64) LEAF_TC_ATTR(__nv_bfloat16, 128) LEAF_TC_ATTR(__nv_bfloat16, 256)
 #undef LEAF_TC_ATTR
-#define LEAF_ATTR(T, CH)                                                                                      \
-    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::leaf_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+#define LEAF_ATTR(T, CH, FS)                                                                                    \
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::leaf_kernel<T, CH, FS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   200 * 1024));
-    LEAF_ATTR(float, 1) LEAF_ATTR(float, 2) LEAF_ATTR(float, 4) LEAF_ATTR(float, 8) LEAF_ATTR(float, 16)
-    LEAF_ATTR(__nv_bfloat16, 1) LEAF_ATTR(__nv_bfloat16, 2) LEAF_ATTR(__nv_bfloat16, 4)
-    LEAF_ATTR(__nv_bfloat16, 8) LEAF_ATTR(__nv_bfloat16, 16)
+#define LEAF_ATTR2(T, CH) LEAF_ATTR(T, CH, true) LEAF_ATTR(T, CH, false)
+    LEAF_ATTR2(float, 1) LEAF_ATTR2(float, 2) LEAF_ATTR2(float, 4) LEAF_ATTR2(float, 8) LEAF_ATTR2(float, 16)
+    LEAF_ATTR2(__nv_bfloat16, 1) LEAF_ATTR2(__nv_bfloat16, 2) LEAF_ATTR2(__nv_bfloat16, 4)
+    LEAF_ATTR2(__nv_bfloat16, 8) LEAF_ATTR2(__nv_bfloat16, 16)
+#undef LEAF_ATTR2
 #undef LEAF_ATTR
-#define LEAF_WARP_ATTR(T, CH)                                                                                      \
-    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::leaf_warp_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+#define LEAF_WARP_ATTR(T, CH, FS)                                                                                    \
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::leaf_warp_kernel<T, CH, FS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   200 * 1024));
-    LEAF_WARP_ATTR(float, 1) LEAF_WARP_ATTR(float, 2) LEAF_WARP_ATTR(float, 4) LEAF_WARP_ATTR(float, 8)
-    LEAF_WARP_ATTR(float, 16) LEAF_WARP_ATTR(__nv_bfloat16, 1) LEAF_WARP_ATTR(__nv_bfloat16, 2)
-    LEAF_WARP_ATTR(__nv_bfloat16, 4) LEAF_WARP_ATTR(__nv_bfloat16, 8) LEAF_WARP_ATTR(__nv_bfloat16, 16)
+#define LEAF_WARP_ATTR2(T, CH) LEAF_WARP_ATTR(T, CH, true) LEAF_WARP_ATTR(T, CH, false)
+    LEAF_WARP_ATTR2(float, 1) LEAF_WARP_ATTR2(float, 2) LEAF_WARP_ATTR2(float, 4) LEAF_WARP_ATTR2(float, 8)
+    LEAF_WARP_ATTR2(float, 16) LEAF_WARP_ATTR2(__nv_bfloat16, 1) LEAF_WARP_ATTR2(__nv_bfloat16, 2)
+    LEAF_WARP_ATTR2(__nv_bfloat16, 4) LEAF_WARP_ATTR2(__nv_bfloat16, 8) LEAF_WARP_ATTR2(__nv_bfloat16, 16)
+#undef LEAF_WARP_ATTR2
 #undef LEAF_WARP_ATTR
     g_attr_done = true;
     return TFI_OK;
