@@ -613,18 +613,22 @@ __global__ void direct_kernel(const DirItem *__restrict__ items, int n_items, co
 }
 
 // ---------------------------------------------------------------------------
-// gather: out[u] = leaf[u] + sum_calls (val[A-bin] - val[b-bin])
+// gather: out[u] = leaf[u] + sum_calls (val[A-bin] - val[b-bin]), vertices taken
+// in a depth-first order of the tree
 // ---------------------------------------------------------------------------
 template <typename T, int V>
-__global__ void gather_kernel(int n, const int32_t *__restrict__ vrec_ptr, const int32_t *__restrict__ akey,
-                              const int32_t *__restrict__ bkey, const float *__restrict__ vbuf,
-                              const float *__restrict__ leaf, const uint8_t *__restrict__ in_leaf, int d,
-                              T *__restrict__ out) {
+__global__ void gather_kernel(int n, const int32_t *__restrict__ order, const int32_t *__restrict__ vrec_ptr,
+                              const int32_t *__restrict__ akey, const int32_t *__restrict__ bkey,
+                              const float *__restrict__ vbuf, const float *__restrict__ leaf,
+                              const uint8_t *__restrict__ in_leaf, int d, T *__restrict__ out) {
     const int chunks = d / V;
     const int64_t total = int64_t(n) * chunks;
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t u = t / chunks;
-        const int c = int(t - u * chunks) * V;
+        const int64_t i = t / chunks;
+        const int c = int(t - i * chunks) * V;
+        // vertices in depth-first order: neighbouring threads share most of their
+        // calls' table rows, which then come from L2 rather than DRAM
+        const int64_t u = order[i];
         float acc[V];
         if (in_leaf[u] != 0) {
             load_row<float, V>(leaf + u * d + c, acc);

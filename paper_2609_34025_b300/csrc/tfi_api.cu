@@ -68,6 +68,7 @@ struct tfi_plan_s {
     int32_t *lgrp_ptr = nullptr, *leaf_vtx = nullptr, *leaf_dist = nullptr, *leaf_pdist = nullptr;
     int32_t *leaf_lo = nullptr, *leaf_hi = nullptr;
     uint8_t *in_leaf = nullptr;
+    int32_t *gorder = nullptr;  // vertices in depth-first preorder of the forest (gather order)
     int32_t max_gs = 0, n_groups = 0;
     // FP32-ALU leaves: groups of consecutive small leaves (one thread per target) and big leaves of
     // at least kLeafWarpMin vertices (one warp per 32 targets, broadcast source loads)
@@ -554,10 +555,10 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     StageMark m_gather(p, s, TFI_STAGE_GATHER);
     if (d % 4 == 0 && (reinterpret_cast<uintptr_t>(out) % (4 * sizeof(T))) == 0)
         tfi::dev::gather_kernel<T, 4><<<grid_for(int64_t(n) * (d / 4), 256), 256, 0, s>>>(
-            n, p->vrec_ptr, p->vrec_akey, p->vrec_bkey, p->vbuf, p->lbuf, p->in_leaf, d, out);
+            n, p->gorder, p->vrec_ptr, p->vrec_akey, p->vrec_bkey, p->vbuf, p->lbuf, p->in_leaf, d, out);
     else
         tfi::dev::gather_kernel<T, 1><<<grid_for(int64_t(n) * d, 256), 256, 0, s>>>(
-            n, p->vrec_ptr, p->vrec_akey, p->vrec_bkey, p->vbuf, p->lbuf, p->in_leaf, d, out);
+            n, p->gorder, p->vrec_ptr, p->vrec_akey, p->vrec_bkey, p->vbuf, p->lbuf, p->in_leaf, d, out);
     m_gather.done(1);
     TFI_CUDA(cudaGetLastError());
     return TFI_OK;
@@ -679,6 +680,31 @@ tfi_status upload_plan(tfi_plan_t p) {
     if (tfi_status rc = p->upload(&p->leaf_lo, hp.leaf_lo)) return rc;
     if (tfi_status rc = p->upload(&p->leaf_hi, hp.leaf_hi)) return rc;
     if (tfi_status rc = p->upload(&p->in_leaf, hp.in_leaf)) return rc;
+    {
+        // depth-first preorder of the forest, tree by tree
+        std::vector<int32_t> order;
+        order.reserve(size_t(hp.n));
+        std::vector<uint8_t> seen(size_t(hp.n), 0);
+        std::vector<int32_t> stack;
+        for (int32_t r = 0; r < hp.n; ++r) {
+            if (seen[size_t(r)]) continue;
+            seen[size_t(r)] = 1;
+            stack.push_back(r);
+            while (!stack.empty()) {
+                const int32_t v = stack.back();
+                stack.pop_back();
+                order.push_back(v);
+                for (int64_t e = hp.ptr[size_t(v)]; e < hp.ptr[size_t(v) + 1]; ++e) {
+                    const int32_t w = hp.adj[size_t(e)];
+                    if (!seen[size_t(w)]) {
+                        seen[size_t(w)] = 1;
+                        stack.push_back(w);
+                    }
+                }
+            }
+        }
+        if (tfi_status rc = p->upload(&p->gorder, order)) return rc;
+    }
     p->n_groups = int32_t(hp.lgrp_ptr.size()) - 1;
     {
         // split the leaves: each big one alone; runs of consecutive small ones in groups of at most
@@ -926,7 +952,7 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
         }
     }
     tfi::dev::gather_kernel<T, 1><<<grid_for(int64_t(n) * d, 256), 256, 0, s>>>(
-        int(n), p->vrec_ptr, p->vrec_akey, p->vrec_bkey, vbuf, lbuf, p->in_leaf, d, out);
+        int(n), p->gorder, p->vrec_ptr, p->vrec_akey, p->vrec_bkey, vbuf, lbuf, p->in_leaf, d, out);
     TFI_CUDA(cudaGetLastError());
     return TFI_OK;
 }
