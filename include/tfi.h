@@ -283,12 +283,22 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
  *                       X = D(p_1) + D(pi u) - 2 D(lca(p_1, pi u)) (Eq. "stad-depth",
  *                       Eq. "projection"); they must equal the host planner's bit for bit.
  *                       Needs a device plan.
+ *   TFI_EXPORT_LEAF_PACKS 4 per dense leaf of at least 64 vertices, in launch order: the CTA of
+ *                       the big-leaf kernel that runs it, its [begin, end) range of leaf
+ *                       positions, and the CTA's vertex capacity. A CTA has 8 warps; a leaf takes
+ *                       ceil(size / 64) of them, a CTA holds leaves while their warps fit in 8 and
+ *                       their vertices in the capacity (largest leaf first). The paper has no
+ *                       counterpart: this is a launch layout (base case of Algorithm 5).
+ *   TFI_EXPORT_GATHER_ORDER the n vertices in the order the output gather takes them: a
+ *                       depth-first preorder of the forest, tree by tree. Launch layout only.
  * If dst is NULL (or cap too small) only *len (number of int64 values) is set. */
 #define TFI_EXPORT_CALLS    0
 #define TFI_EXPORT_BACKBONE 1
 #define TFI_EXPORT_RECORDS  2
 #define TFI_EXPORT_LEAVES   3
 #define TFI_EXPORT_DEVICE_KEYS 4
+#define TFI_EXPORT_LEAF_PACKS  5
+#define TFI_EXPORT_GATHER_ORDER 6
 tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t cap, int64_t *len);
 
 /* Stages of an apply, in launch order, for profiling and the roofline model:

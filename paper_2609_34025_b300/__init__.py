@@ -25,7 +25,8 @@ _STATUS = {0: "OK", 1: "ARG", 2: "NOT_TREE", 3: "WEIGHT", 4: "GRID_OVERFLOW", 5:
 KERNEL_KINDS = {"table": 0, "expsum": 1, "gauss": 2, "rational": 3, "powexp": 4}
 POLICIES = {"adaptive": 0, "diameter": 1, "centroid": 2}
 DTYPE_F32, DTYPE_BF16 = 0, 1
-EXPORTS = {"calls": (0, 7), "backbone": (1, 1), "records": (2, 5), "leaves": (3, 3), "device_keys": (4, 4)}
+EXPORTS = {"calls": (0, 7), "backbone": (1, 1), "records": (2, 5), "leaves": (3, 3), "device_keys": (4, 4),
+           "leaf_packs": (5, 4), "gather_order": (6, 1)}
 
 
 class TfiError(RuntimeError):

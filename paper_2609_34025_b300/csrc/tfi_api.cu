@@ -636,6 +636,59 @@ tfi_status run_device_keys(tfi_plan_t p) {
     return TFI_OK;
 }
 
+// The dense leaves in launch form: runs of consecutive leaves of fewer than
+// kLeafWarpMin vertices in groups of at most kLeafGroup vertices, as [begin, end)
+// pairs of leaf_vtx positions (a big leaf ends the run before it), and the big
+// leaves' ranges in plan order.
+void split_leaves(const tfi::HostPlan &hp, std::vector<int32_t> &sgrp, std::vector<int32_t> &big_lo,
+                  std::vector<int32_t> &big_hi) {
+    const int32_t nl = int32_t(hp.leaf_vtx.size());
+    int32_t gb = -1;
+    for (int32_t pos = 0; pos < nl;) {
+        const int32_t lo = hp.leaf_lo[size_t(pos)], hi = hp.leaf_hi[size_t(pos)];
+        if (hi - lo >= tfi::dev::kLeafWarpMin) {
+            if (gb >= 0) sgrp.insert(sgrp.end(), {gb, lo});
+            gb = -1;
+            big_lo.push_back(lo);
+            big_hi.push_back(hi);
+        } else if (gb < 0) {
+            gb = lo;
+        } else if (hi - gb > tfi::kLeafGroup) {
+            sgrp.insert(sgrp.end(), {gb, lo});
+            gb = lo;
+        }
+        pos = hi;
+    }
+    if (gb >= 0) sgrp.insert(sgrp.end(), {gb, nl});
+}
+
+// Depth-first preorder of the forest, tree by tree from the smallest unvisited
+// vertex: the order in which the gather takes the vertices.
+std::vector<int32_t> depth_first_order(const tfi::HostPlan &hp) {
+    std::vector<int32_t> order;
+    order.reserve(size_t(hp.n));
+    std::vector<uint8_t> seen(size_t(hp.n), 0);
+    std::vector<int32_t> stack;
+    for (int32_t r = 0; r < hp.n; ++r) {
+        if (seen[size_t(r)]) continue;
+        seen[size_t(r)] = 1;
+        stack.push_back(r);
+        while (!stack.empty()) {
+            const int32_t v = stack.back();
+            stack.pop_back();
+            order.push_back(v);
+            for (int64_t e = hp.ptr[size_t(v)]; e < hp.ptr[size_t(v) + 1]; ++e) {
+                const int32_t w = hp.adj[size_t(e)];
+                if (!seen[size_t(w)]) {
+                    seen[size_t(w)] = 1;
+                    stack.push_back(w);
+                }
+            }
+        }
+    }
+    return order;
+}
+
 // interleaved complex values (re, im, re, im, ...) -> one (re, re, im, im) per value, the
 // operand form of the paired FP32 instructions in fft_x2_kernel
 std::vector<float4> broadcast_pairs(const std::vector<float> &z) {
@@ -681,53 +734,13 @@ tfi_status upload_plan(tfi_plan_t p) {
     if (tfi_status rc = p->upload(&p->leaf_hi, hp.leaf_hi)) return rc;
     if (tfi_status rc = p->upload(&p->in_leaf, hp.in_leaf)) return rc;
     {
-        // depth-first preorder of the forest, tree by tree
-        std::vector<int32_t> order;
-        order.reserve(size_t(hp.n));
-        std::vector<uint8_t> seen(size_t(hp.n), 0);
-        std::vector<int32_t> stack;
-        for (int32_t r = 0; r < hp.n; ++r) {
-            if (seen[size_t(r)]) continue;
-            seen[size_t(r)] = 1;
-            stack.push_back(r);
-            while (!stack.empty()) {
-                const int32_t v = stack.back();
-                stack.pop_back();
-                order.push_back(v);
-                for (int64_t e = hp.ptr[size_t(v)]; e < hp.ptr[size_t(v) + 1]; ++e) {
-                    const int32_t w = hp.adj[size_t(e)];
-                    if (!seen[size_t(w)]) {
-                        seen[size_t(w)] = 1;
-                        stack.push_back(w);
-                    }
-                }
-            }
-        }
+        const std::vector<int32_t> order = depth_first_order(hp);
         if (tfi_status rc = p->upload(&p->gorder, order)) return rc;
     }
     p->n_groups = int32_t(hp.lgrp_ptr.size()) - 1;
     {
-        // split the leaves: each big one alone; runs of consecutive small ones in groups of at most
-        // kLeafGroup vertices, as [begin, end) pairs (a big leaf ends the run before it)
         std::vector<int32_t> sgrp, leaf_lo_big, leaf_hi_big;
-        const int32_t nl = int32_t(hp.leaf_vtx.size());
-        int32_t gb = -1;
-        for (int32_t pos = 0; pos < nl;) {
-            const int32_t lo = hp.leaf_lo[size_t(pos)], hi = hp.leaf_hi[size_t(pos)];
-            if (hi - lo >= tfi::dev::kLeafWarpMin) {
-                if (gb >= 0) sgrp.insert(sgrp.end(), {gb, lo});
-                gb = -1;
-                leaf_lo_big.push_back(lo);
-                leaf_hi_big.push_back(hi);
-            } else if (gb < 0) {
-                gb = lo;
-            } else if (hi - gb > tfi::kLeafGroup) {
-                sgrp.insert(sgrp.end(), {gb, lo});
-                gb = lo;
-            }
-            pos = hi;
-        }
-        if (gb >= 0) sgrp.insert(sgrp.end(), {gb, nl});
+        split_leaves(hp, sgrp, leaf_lo_big, leaf_hi_big);
         for (size_t q = 0; q < sgrp.size(); q += 2) p->max_sgs = std::max(p->max_sgs, sgrp[q + 1] - sgrp[q]);
         p->n_sgroups = int32_t(sgrp.size() / 2);
         std::vector<int32_t> bptr, blo, bhi;
@@ -1697,6 +1710,23 @@ tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t 
                     v.insert(v.end(), row, row + 4);
                 }
             }
+            break;
+        }
+        case TFI_EXPORT_LEAF_PACKS: {
+            std::vector<int32_t> sgrp, lo, hi, bptr, blo, bhi;
+            split_leaves(hp, sgrp, lo, hi);
+            int32_t cap = 0;
+            pack_big_leaves(lo, hi, bptr, blo, bhi, &cap);
+            for (size_t b = 0; b + 1 < bptr.size(); ++b)
+                for (int32_t q = bptr[b]; q < bptr[b + 1]; ++q) {
+                    const int64_t row[4] = {int64_t(b), blo[size_t(q)], bhi[size_t(q)], cap};
+                    v.insert(v.end(), row, row + 4);
+                }
+            break;
+        }
+        case TFI_EXPORT_GATHER_ORDER: {
+            const std::vector<int32_t> order = depth_first_order(hp);
+            v.assign(order.begin(), order.end());
             break;
         }
         default:
