@@ -76,6 +76,21 @@ def test_paper_families_unit_weights(make, policy):
     assert _err(y, ref) <= TOL["f32"]
 
 
+@pytest.mark.parametrize("make", [lambda: W.spider(8, 60), lambda: W.spider(8, 100),
+                                  lambda: W.toothed_spine(200, 2), lambda: W.toothed_spine(256, 3)],
+                         ids=["1d_2^7", "1d_2^8", "2d_2^3x2^9", "2d_2^3x2^10"])
+@pytest.mark.parametrize("d", [3, 8, 16])
+def test_fft_table_shapes(make, d):
+    # FFT tables the larger workloads do not produce: one-dimensional tables of 2^7 and 2^8
+    # points (radix-2 / radix-4 first passes) and two-dimensional ones (the general passes of the
+    # two-pair kernel, and the one-pair kernel at 2^13 points), at 2, 4 and 8 channel pairs
+    t = make()
+    F = W.normal_field(t.n, d, seed=5)
+    p, y, ref = _run(t, 1.0, W.KernelSpec.exp(0.05), F, leaf_max=8)
+    assert p.info()["n_jobs_fft"] > 0
+    assert _err(y, ref) <= TOL["f32"]
+
+
 def test_forest_uneven_batch_small():
     cfg = W.configs.uneven_batch(count=40, lo=8, hi=3000, d=16)
     F = W.normal_field(cfg["tree"].n, 16, seed=123)

@@ -12,6 +12,7 @@ from .trees import (  # noqa: F401
     spider,
     caterpillar_leaves,
     caterpillar_hanging_paths,
+    toothed_spine,
     comb,
     broom,
     double_broom,

@@ -106,6 +106,12 @@ def caterpillar_hanging_paths(ell: int) -> Tree:
     return _spine_with(ell, lambda t: [ell])
 
 
+def toothed_spine(ell: int, h: int, teeth: int = 2) -> Tree:
+    """Spine of ell vertices with `teeth` chains of h edges at each spine vertex
+    (n = ell (1 + teeth h)): dense two-dimensional bin tables of depth h."""
+    return _spine_with(ell, lambda t: [h] * teeth)
+
+
 def comb(ell: int) -> Tree:
     return caterpillar_leaves(ell, leaves=2)
 
