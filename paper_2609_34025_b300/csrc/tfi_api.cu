@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dense_tc.cuh"
 #include "grad.cuh"
 #include "hankel_tc.cuh"
@@ -447,17 +449,31 @@ tfi_status set_attributes() {
     return TFI_OK;
 }
 
+// NVTX names of the stages (TFI_STAGE_* order): each stage's launches form one
+// range on the host timeline, visible to nsys and usable as an ncu --nvtx filter
+// (no cost unless a tool is attached)
+const char *const kStageName[] = {"tfi.leaf", "tfi.bucket", "tfi.fft", "tfi.direct", "tfi.gather", "tfi.sweep",
+                                  "tfi.hankel"};
+
 struct StageMark {
     tfi_plan_t p;
     cudaStream_t s;
     int stage;
     cudaEvent_t a = nullptr;
+    nvtxRangeId_t range = 0;
+    bool open = true;
     StageMark(tfi_plan_t p_, cudaStream_t s_, int st) : p(p_), s(s_), stage(st) {
+        range = nvtxRangeStartA(kStageName[st]);
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         cudaStreamIsCapturing(s, &cs);
         if (p->profiling && cs == cudaStreamCaptureStatusNone && (a = p->next_event())) cudaEventRecord(a, s);
     }
+    ~StageMark() {
+        if (open) nvtxRangeEnd(range);
+    }
     void done(int launches) {
+        nvtxRangeEnd(range);
+        open = false;
         if (!a) return;
         cudaEvent_t b = p->next_event();
         if (!b) return;
@@ -468,6 +484,10 @@ struct StageMark {
 
 template <typename T>
 tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
+    struct ApplyRange {  // the whole apply as one NVTX range
+        nvtxRangeId_t id = nvtxRangeStartA("tfi.apply");
+        ~ApplyRange() { nvtxRangeEnd(id); }
+    } apply_range;
     WorkLists *wl = nullptr;
     if (tfi_status rc = build_work(p, d, &wl)) return rc;
     if (tfi_status rc = set_attributes()) return rc;
