@@ -85,9 +85,36 @@ void fft64(std::complex<double> *a, int lg, int64_t stride) {
     }
 }
 
+// Run fn(i) for i in [0, n) on all hardware threads (dynamic scheduling).
+template <typename Fn>
+void parallel_for(size_t n, Fn fn) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nth = std::min<size_t>(n, hw);
+    std::atomic<size_t> next(0);
+    auto worker = [&]() {
+        for (;;) {
+            const size_t i = next.fetch_add(1);
+            if (i >= n) break;
+            fn(i);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < nth; ++t) pool.emplace_back(worker);
+    if (n) worker();
+    for (std::thread &th : pool) th.join();
+}
+
+// The recursion of Algorithm 5, level by level: every call of a level is
+// decomposed (or, at most s0 vertices, laid out as a dense leaf) independently
+// of the others, in parallel when `parallel` is set, and the results are
+// appended to the plan in call order, so the plan is the same as a one-call-
+// at-a-time breadth-first recursion. Calls of one level hold disjoint vertex
+// sets: the vertex-indexed scratch arrays are touched only at a call's own
+// members (membership is set for the whole level before it starts), and the
+// traversal tokens are unique across threads.
 class Builder {
 public:
-    explicit Builder(HostPlan &hp) : hp_(hp), n_(hp.n) {
+    Builder(HostPlan &hp, bool parallel) : hp_(hp), n_(hp.n), parallel_(parallel) {
         member_.assign(size_t(n_), 0);
         onp_.assign(size_t(n_), 0);
         seen_.assign(size_t(n_), 0);
@@ -99,101 +126,141 @@ public:
 
     int run(std::string &err) {
         // top-level calls: the trees of the forest, in order of their smallest vertex
-        std::deque<std::pair<int32_t, std::vector<int32_t>>> work;
+        std::vector<Item> cur;
         std::fill(member_.begin(), member_.end(), 1);
-        int32_t all_tok = 1;
         std::vector<char> done(size_t(n_), 0);
+        std::vector<int32_t> order;
         for (int32_t s = 0; s < n_; ++s) {
             if (done[size_t(s)]) continue;
-            traverse(s, all_tok);
-            std::vector<int32_t> comp(order_.begin(), order_.end());
-            for (int32_t v : comp) done[size_t(v)] = 1;
-            work.emplace_back(0, std::move(comp));
+            traverse(s, 1, order);
+            for (int32_t v : order) done[size_t(v)] = 1;
+            cur.push_back(Item{0, order, 0});
         }
-        tok_member_ = 1;
-        Decomp dd, dc;
-        while (!work.empty()) {
-            int32_t level = work.front().first;
-            std::vector<int32_t> S = std::move(work.front().second);
-            work.pop_front();
-            const int32_t mtok = ++tok_member_;
-            for (int32_t v : S) member_[size_t(v)] = mtok;
-            hp_.n_levels = std::max(hp_.n_levels, level + 1);
-            const int32_t minv = *std::min_element(S.begin(), S.end());
-            if (int64_t(S.size()) <= hp_.leaf_max) {
-                if (int rc = emit_leaf(level, minv, mtok, err)) return rc;
-                continue;
+        int32_t tok_member = 1;
+        std::vector<Result> res;
+        std::vector<Item> next;
+        while (!cur.empty()) {
+            for (Item &it : cur) {
+                it.mtok = ++tok_member;
+                for (int32_t v : it.S) member_[size_t(v)] = it.mtok;
             }
-            Decomp *D = nullptr;
-            int32_t kind = 0;
-            if (hp_.policy == TFI_POLICY_CENTROID) {
-                decompose(mtok, {centroid(minv, int64_t(S.size()), mtok)}, dc);
-                D = &dc;
-                kind = 1;
-            } else if (hp_.policy == TFI_POLICY_DIAMETER) {
-                decompose(mtok, diameter(minv, mtok), dd);
-                D = &dd;
-            } else {
-                decompose(mtok, diameter(minv, mtok), dd);
-                decompose(mtok, {centroid(minv, int64_t(S.size()), mtok)}, dc);
-                // the centroid wins only with a strictly smaller score (Algorithm 6)
-                if (score(int64_t(S.size()), dc) < score(int64_t(S.size()), dd)) {
-                    D = &dc;
-                    kind = 1;
-                } else {
-                    D = &dd;
+            res.assign(cur.size(), Result{});
+            auto one = [&](size_t i) { solve(cur[i], res[i]); };
+            if (parallel_) parallel_for(cur.size(), one);
+            else for (size_t i = 0; i < cur.size(); ++i) one(i);
+            next.clear();
+            for (size_t i = 0; i < cur.size(); ++i) {
+                const Item &it = cur[i];
+                Result &r = res[i];
+                hp_.n_levels = std::max(hp_.n_levels, it.level + 1);
+                if (r.rc) {
+                    err = r.err;
+                    return r.rc;
                 }
+                if (r.leaf) {
+                    r.lf.begin = int64_t(hp_.leaf_vtx.size());
+                    hp_.leaf_vtx.insert(hp_.leaf_vtx.end(), r.lvtx.begin(), r.lvtx.end());
+                    hp_.leaf_dist.insert(hp_.leaf_dist.end(), r.ldist.begin(), r.ldist.end());
+                    hp_.leaf_pdist.insert(hp_.leaf_pdist.end(), r.lpdist.begin(), r.lpdist.end());
+                    r.lf.end = int64_t(hp_.leaf_vtx.size());
+                    hp_.leaves.push_back(r.lf);
+                    continue;
+                }
+                emit_call(it.level, r.minv, int32_t(it.S.size()), r.kind, r.D);
+                for (size_t a = 0; a + 1 < r.D.cptr.size(); ++a)
+                    next.push_back(Item{it.level + 1,
+                                        std::vector<int32_t>(r.D.cv.begin() + r.D.cptr[a], r.D.cv.begin() + r.D.cptr[a + 1]),
+                                        0});
             }
-            if (D->H >= kGridMax || D->X.back() >= kGridMax) {
-                err = "grid distance beyond 2^30 in a decomposition (choose a larger delta)";
-                return TFI_ERR_GRID_OVERFLOW;
-            }
-            emit_call(level, minv, int32_t(S.size()), kind, *D);
-            for (size_t a = 0; a + 1 < D->cptr.size(); ++a) {
-                work.emplace_back(level + 1,
-                                  std::vector<int32_t>(D->cv.begin() + D->cptr[a], D->cv.begin() + D->cptr[a + 1]));
-            }
+            cur.swap(next);
         }
         return TFI_OK;
     }
 
 private:
-    // Traverse the members of S (member == mtok) from s: order_, dist_, par_.
-    void traverse(int32_t s, int32_t mtok) {
+    struct Item {
+        int32_t level;
+        std::vector<int32_t> S;
+        int32_t mtok;
+    };
+    struct Result {
+        int rc = 0;
+        std::string err;
+        int32_t minv = 0, kind = 0;
+        bool leaf = false;
+        Decomp D;
+        Leaf lf;
+        std::vector<int32_t> lvtx, ldist, lpdist;
+    };
+
+    // One call: its decomposition (Algorithm 6 choice, Algorithm 1), or its dense leaf.
+    void solve(const Item &it, Result &r) {
+        const int32_t mtok = it.mtok;
+        const int64_t nS = int64_t(it.S.size());
+        r.minv = *std::min_element(it.S.begin(), it.S.end());
+        std::vector<int32_t> order;
+        if (nS <= hp_.leaf_max) {
+            r.leaf = true;
+            r.rc = leaf(it.level, r.minv, mtok, r, order);
+            return;
+        }
+        if (hp_.policy == TFI_POLICY_CENTROID) {
+            decompose(mtok, {centroid(r.minv, nS, mtok, order)}, r.D);
+            r.kind = 1;
+        } else if (hp_.policy == TFI_POLICY_DIAMETER) {
+            decompose(mtok, diameter(r.minv, mtok, order), r.D);
+        } else {
+            Decomp dc;
+            decompose(mtok, diameter(r.minv, mtok, order), r.D);
+            decompose(mtok, {centroid(r.minv, nS, mtok, order)}, dc);
+            // the centroid wins only with a strictly smaller score (Algorithm 6)
+            if (score(nS, dc) < score(nS, r.D)) {
+                r.D = std::move(dc);
+                r.kind = 1;
+            }
+        }
+        if (r.D.H >= kGridMax || r.D.X.back() >= kGridMax) {
+            r.err = "grid distance beyond 2^30 in a decomposition (choose a larger delta)";
+            r.rc = TFI_ERR_GRID_OVERFLOW;
+        }
+    }
+
+    // Traverse the members of S (member == mtok) from s into order: dist_, par_.
+    void traverse(int32_t s, int32_t mtok, std::vector<int32_t> &order) {
         const int32_t tok = ++tok_seen_;
-        order_.clear();
-        order_.push_back(s);
+        order.clear();
+        order.push_back(s);
         seen_[size_t(s)] = tok;
         dist_[size_t(s)] = 0;
         par_[size_t(s)] = -1;
-        for (size_t h = 0; h < order_.size(); ++h) {
-            const int32_t a = order_[h];
+        for (size_t h = 0; h < order.size(); ++h) {
+            const int32_t a = order[h];
             for (int64_t e = hp_.ptr[size_t(a)]; e < hp_.ptr[size_t(a) + 1]; ++e) {
                 const int32_t b = hp_.adj[size_t(e)];
                 if (member_[size_t(b)] == mtok && seen_[size_t(b)] != tok) {
                     seen_[size_t(b)] = tok;
                     dist_[size_t(b)] = dist_[size_t(a)] + hp_.qlen[size_t(e)];
                     par_[size_t(b)] = a;
-                    order_.push_back(b);
+                    order.push_back(b);
                 }
             }
         }
     }
 
-    int32_t farthest() const {
-        int32_t best = order_[0];
-        for (int32_t v : order_) {
+    int32_t farthest(const std::vector<int32_t> &order) const {
+        int32_t best = order[0];
+        for (int32_t v : order) {
             if (dist_[size_t(v)] > dist_[size_t(best)] || (dist_[size_t(v)] == dist_[size_t(best)] && v < best)) best = v;
         }
         return best;
     }
 
     // Weighted diameter path by two traversals and parent pointers (Algorithm 6, first step).
-    std::vector<int32_t> diameter(int32_t minv, int32_t mtok) {
-        traverse(minv, mtok);
-        const int32_t a = farthest();
-        traverse(a, mtok);
-        const int32_t b = farthest();
+    std::vector<int32_t> diameter(int32_t minv, int32_t mtok, std::vector<int32_t> &order) {
+        traverse(minv, mtok, order);
+        const int32_t a = farthest(order);
+        traverse(a, mtok, order);
+        const int32_t b = farthest(order);
         std::vector<int32_t> path;
         for (int32_t v = b; v != -1; v = par_[size_t(v)]) path.push_back(v);
         std::reverse(path.begin(), path.end());
@@ -201,19 +268,19 @@ private:
     }
 
     // Centroid by a rooted traversal and subtree sizes (Algorithm 6, second step).
-    int32_t centroid(int32_t minv, int64_t nS, int32_t mtok) {
-        traverse(minv, mtok);
-        for (int32_t v : order_) {
+    int32_t centroid(int32_t minv, int64_t nS, int32_t mtok, std::vector<int32_t> &order) {
+        traverse(minv, mtok, order);
+        for (int32_t v : order) {
             sz_[size_t(v)] = 1;
             maxchild_[size_t(v)] = 0;
         }
-        for (size_t i = order_.size(); i-- > 1;) {
-            const int32_t v = order_[i], p = par_[size_t(v)];
+        for (size_t i = order.size(); i-- > 1;) {
+            const int32_t v = order[i], p = par_[size_t(v)];
             sz_[size_t(p)] += sz_[size_t(v)];
             maxchild_[size_t(p)] = std::max(maxchild_[size_t(p)], sz_[size_t(v)]);
         }
         int32_t best = -1;
-        for (int32_t v : order_) {
+        for (int32_t v : order) {
             const int64_t big = std::max<int64_t>(nS - sz_[size_t(v)], maxchild_[size_t(v)]);
             if (2 * big <= nS && (best < 0 || v < best)) best = v;
         }
@@ -312,31 +379,28 @@ private:
     }
 
     // Dense leaf: vertices in preorder from the smallest vertex, children ascending,
-    // with grid distances from that root (subtrees are contiguous ranges).
-    int emit_leaf(int32_t level, int32_t minv, int32_t mtok, std::string &err) {
-        Leaf lf;
-        lf.level = level;
-        lf.minv = minv;
-        lf.begin = int64_t(hp_.leaf_vtx.size());
+    // with grid distances from that root (subtrees are contiguous ranges), and the
+    // leaf's diameter; begin / end are set when it is appended to the plan.
+    int leaf(int32_t level, int32_t minv, int32_t mtok, Result &r, std::vector<int32_t> &order) {
+        r.lf.level = level;
+        r.lf.minv = minv;
         const int32_t tok = ++tok_seen_;
-        std::vector<int32_t> &stack = stack_;
-        stack.clear();
+        std::vector<int32_t> stack, kids;
         stack.push_back(minv);
         seen_[size_t(minv)] = tok;
         dist_[size_t(minv)] = 0;
         par_[size_t(minv)] = -1;
-        std::vector<int32_t> kids;
         while (!stack.empty()) {
             const int32_t v = stack.back();
             stack.pop_back();
             if (dist_[size_t(v)] >= kGridMax / 2) {
-                err = "grid distance beyond 2^29 inside a leaf (choose a larger delta)";
+                r.err = "grid distance beyond 2^29 inside a leaf (choose a larger delta)";
                 return TFI_ERR_GRID_OVERFLOW;
             }
-            hp_.leaf_vtx.push_back(v);
-            hp_.leaf_dist.push_back(int32_t(dist_[size_t(v)]));
+            r.lvtx.push_back(v);
+            r.ldist.push_back(int32_t(dist_[size_t(v)]));
             const int32_t p = par_[size_t(v)];
-            hp_.leaf_pdist.push_back(p >= 0 ? int32_t(dist_[size_t(p)]) : 0);
+            r.lpdist.push_back(p >= 0 ? int32_t(dist_[size_t(p)]) : 0);
             kids.clear();
             for (int64_t e = hp_.ptr[size_t(v)]; e < hp_.ptr[size_t(v) + 1]; ++e) {
                 const int32_t b = hp_.adj[size_t(e)];
@@ -350,28 +414,27 @@ private:
             // adjacency is ascending; push in reverse so the smallest child comes next
             for (size_t k = kids.size(); k-- > 0;) stack.push_back(kids[k]);
         }
-        lf.end = int64_t(hp_.leaf_vtx.size());
         // leaf diameter by a second traversal from the vertex farthest from the root
         int32_t far = minv;
         int64_t best = -1;
-        for (int64_t i = lf.begin; i < lf.end; ++i) {
-            if (hp_.leaf_dist[size_t(i)] > best) {
-                best = hp_.leaf_dist[size_t(i)];
-                far = hp_.leaf_vtx[size_t(i)];
+        for (size_t i = 0; i < r.lvtx.size(); ++i) {
+            if (r.ldist[i] > best) {
+                best = r.ldist[i];
+                far = r.lvtx[i];
             }
         }
-        traverse(far, mtok);
-        lf.diam = 0;
-        for (int32_t v : order_) lf.diam = std::max(lf.diam, dist_[size_t(v)]);
-        hp_.leaves.push_back(lf);
+        traverse(far, mtok, order);
+        r.lf.diam = 0;
+        for (int32_t v : order) r.lf.diam = std::max(r.lf.diam, dist_[size_t(v)]);
         return TFI_OK;
     }
 
     HostPlan &hp_;
     int32_t n_;
-    std::vector<int32_t> member_, onp_, seen_, par_, order_, stack_;
+    bool parallel_;
+    std::vector<int32_t> member_, onp_, seen_, par_;
     std::vector<int64_t> dist_, sz_, maxchild_;
-    int32_t tok_member_ = 0, tok_onp_ = 0, tok_seen_ = 0;
+    std::atomic<int32_t> tok_onp_{0}, tok_seen_{0};
 };
 
 // Cost model of the two evaluators, per channel, in units of one direct
@@ -401,24 +464,6 @@ double hankel_cost(int32_t H, int32_t L, double ncols, double nk, int d) {
     return ncols * per_col * 128.0 / double(std::min(d, 128)) + 2 * nk;
 }
 
-// Run fn(i) for i in [0, n) on all hardware threads (dynamic scheduling).
-template <typename Fn>
-void parallel_for(size_t n, Fn fn) {
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const size_t nth = std::min<size_t>(n, hw);
-    std::atomic<size_t> next(0);
-    auto worker = [&]() {
-        for (;;) {
-            const size_t i = next.fetch_add(1);
-            if (i >= n) break;
-            fn(i);
-        }
-    };
-    std::vector<std::thread> pool;
-    for (size_t t = 1; t < nth; ++t) pool.emplace_back(worker);
-    if (n) worker();
-    for (std::thread &th : pool) th.join();
-}
 
 // Bins of one call: its A-bins (distinct (depth, coordinate)) and each
 // component's b-bins (distinct depth), members ascending by vertex id.
@@ -799,7 +844,7 @@ int plan_forest(HostPlan &hp, const std::vector<std::vector<int32_t>> &trees, st
                     lp.qlen[size_t(o)] = hp.qlen[size_t(e)];
                 }
             }
-            Builder b(lp);
+            Builder b(lp, false);
             rcs[t] = b.run(errs[t]);
             lp.ptr.clear();
             lp.ptr.shrink_to_fit();
@@ -951,7 +996,7 @@ int build_plan(HostPlan &hp, int32_t n, int32_t m, const int32_t *u, const int32
         std::sort(vs.begin(), vs.end());
     }
     if (trees.size() <= 1) {
-        Builder b(hp);
+        Builder b(hp, true);
         if (int rc = b.run(err)) return rc;
     } else if (int rc = plan_forest(hp, trees, err)) {
         return rc;
