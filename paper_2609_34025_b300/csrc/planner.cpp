@@ -578,7 +578,8 @@ int sample_kernel(HostPlan &hp, std::string &err) {
 
 namespace {
 
-int flatten(HostPlan &hp, std::string &err) {
+// roots: the smallest vertex of each tree of the forest
+int flatten(HostPlan &hp, const std::vector<int32_t> &roots, std::string &err) {
     const int64_t R = int64_t(hp.recs.size());
     std::vector<int32_t> rec_akey(size_t(R), -1), rec_bkey(size_t(R), -1);
     const size_t C = hp.calls.size();
@@ -699,31 +700,56 @@ int flatten(HostPlan &hp, std::string &err) {
         return TFI_ERR_UNSUPPORTED;
     }
     // per vertex: its (A-key, b-key) in every non-leaf call, in level order
+    // (a counting sort by vertex, stable in record order: slots are claimed in any
+    // order in parallel, then each vertex's few slots are put back in record order)
     hp.vrec_ptr.assign(size_t(hp.n) + 1, 0);
-    for (const Rec &rc : hp.recs) hp.vrec_ptr[size_t(rc.v) + 1]++;
-    for (int32_t v = 0; v < hp.n; ++v) hp.vrec_ptr[size_t(v) + 1] += hp.vrec_ptr[size_t(v)];
-    hp.vrec_akey.assign(size_t(R), 0);
-    hp.vrec_bkey.assign(size_t(R), 0);
+    constexpr int64_t kRecBlock = int64_t(1) << 16;
+    const size_t nrb = size_t((R + kRecBlock - 1) / kRecBlock);
     {
-        std::vector<int32_t> fill(hp.vrec_ptr.begin(), hp.vrec_ptr.end() - 1);
-        for (int64_t i = 0; i < R; ++i) {
-            const int32_t v = hp.recs[size_t(i)].v;
-            const int32_t slot = fill[size_t(v)]++;
-            hp.vrec_akey[size_t(slot)] = rec_akey[size_t(i)];
-            hp.vrec_bkey[size_t(slot)] = rec_bkey[size_t(i)];
-        }
+        std::vector<std::atomic<int32_t>> cnt(size_t(hp.n));
+        for (auto &c : cnt) c.store(0, std::memory_order_relaxed);
+        parallel_for(nrb, [&](size_t b) {
+            const int64_t i1 = std::min(R, int64_t(b + 1) * kRecBlock);
+            for (int64_t i = int64_t(b) * kRecBlock; i < i1; ++i)
+                cnt[size_t(hp.recs[size_t(i)].v)].fetch_add(1, std::memory_order_relaxed);
+        });
+        for (int32_t v = 0; v < hp.n; ++v)
+            hp.vrec_ptr[size_t(v) + 1] = hp.vrec_ptr[size_t(v)] + cnt[size_t(v)].load(std::memory_order_relaxed);
+        for (int32_t v = 0; v < hp.n; ++v) cnt[size_t(v)].store(hp.vrec_ptr[size_t(v)], std::memory_order_relaxed);
+        std::vector<int32_t> rec_of(static_cast<size_t>(R));
+        parallel_for(nrb, [&](size_t b) {
+            const int64_t i1 = std::min(R, int64_t(b + 1) * kRecBlock);
+            for (int64_t i = int64_t(b) * kRecBlock; i < i1; ++i)
+                rec_of[size_t(cnt[size_t(hp.recs[size_t(i)].v)].fetch_add(1, std::memory_order_relaxed))] = int32_t(i);
+        });
+        hp.vrec_akey.assign(size_t(R), 0);
+        hp.vrec_bkey.assign(size_t(R), 0);
+        constexpr int32_t kVBlock = 1 << 14;
+        parallel_for(size_t((hp.n + kVBlock - 1) / kVBlock), [&](size_t b) {
+            const int32_t v0 = int32_t(b) * kVBlock, v1 = std::min(hp.n, v0 + kVBlock);
+            for (int32_t v = v0; v < v1; ++v) {
+                const int32_t s0 = hp.vrec_ptr[size_t(v)], s1 = hp.vrec_ptr[size_t(v) + 1];
+                std::sort(rec_of.begin() + s0, rec_of.begin() + s1);
+                for (int32_t k = s0; k < s1; ++k) {
+                    hp.vrec_akey[size_t(k)] = rec_akey[size_t(rec_of[size_t(k)])];
+                    hp.vrec_bkey[size_t(k)] = rec_bkey[size_t(rec_of[size_t(k)])];
+                }
+            }
+        });
     }
-    // rooted forest for the device distance pass: each tree rooted at its smallest vertex
+    // rooted forest for the device distance pass: each tree rooted at its smallest
+    // vertex (parent, edge length and hop depth do not depend on the traversal order,
+    // so the trees are traversed in parallel)
     {
         hp.k1_parent.assign(size_t(hp.n), -1);
         hp.k1_qpar.assign(size_t(hp.n), 0);
-        std::vector<int32_t> hop(size_t(hp.n), 0), queue;
-        queue.reserve(size_t(hp.n));
-        for (int32_t s0 = 0; s0 < hp.n; ++s0) {
-            if (hp.k1_parent[size_t(s0)] >= 0) continue;
+        std::vector<int32_t> hop(size_t(hp.n), 0);
+        std::vector<int32_t> tree_maxhop(roots.size(), 0);
+        parallel_for(roots.size(), [&](size_t t) {
+            const int32_t s0 = roots[t];
+            std::vector<int32_t> queue{s0};
             hp.k1_parent[size_t(s0)] = s0;
-            queue.clear();
-            queue.push_back(s0);
+            int32_t mh = 0;
             for (size_t h = 0; h < queue.size(); ++h) {
                 const int32_t a = queue[h];
                 for (int64_t e = hp.ptr[size_t(a)]; e < hp.ptr[size_t(a) + 1]; ++e) {
@@ -732,14 +758,17 @@ int flatten(HostPlan &hp, std::string &err) {
                     hp.k1_parent[size_t(b)] = a;
                     hp.k1_qpar[size_t(b)] = int32_t(hp.qlen[size_t(e)]);
                     hop[size_t(b)] = hop[size_t(a)] + 1;
-                    hp.k1_maxhop = std::max(hp.k1_maxhop, hop[size_t(b)]);
+                    mh = std::max(mh, hop[size_t(b)]);
                     queue.push_back(b);
                 }
             }
-        }
+            tree_maxhop[t] = mh;
+        });
+        for (int32_t mh : tree_maxhop) hp.k1_maxhop = std::max(hp.k1_maxhop, mh);
         hp.rec_anchor.resize(hp.recs.size());
         hp.rec_p1.resize(hp.recs.size());
-        for (const Call &c : hp.calls) {
+        parallel_for(hp.calls.size(), [&](size_t ci) {
+            const Call &c = hp.calls[ci];
             const int32_t p1 = hp.bb[size_t(c.bb_begin)];
             for (int64_t i = c.rec_begin; i < c.rec_end; ++i) {
                 const Rec &rc = hp.recs[size_t(i)];
@@ -747,7 +776,7 @@ int flatten(HostPlan &hp, std::string &err) {
                     rc.comp >= 0 ? hp.bb[size_t(c.bb_begin + hp.comps[size_t(rc.comp)].anchor_idx)] : rc.v;
                 hp.rec_p1[size_t(i)] = p1;
             }
-        }
+        });
     }
     hp.in_leaf.assign(size_t(hp.n), 0);
     for (int32_t v : hp.leaf_vtx) hp.in_leaf[size_t(v)] = 1;
@@ -866,46 +895,69 @@ int plan_forest(HostPlan &hp, const std::vector<std::vector<int32_t>> &trees, st
             return rcs[t];
         }
     }
-    // merge in tree order, mapping local ids back to global ones
+    // merge in tree order, mapping local ids back to global ones: offsets of each
+    // tree's part by prefix sums, then the trees copied in parallel
+    struct Off {
+        int64_t call, bb, rec, comp, leaf, lv;
+    };
+    std::vector<Off> off(T + 1, Off{0, 0, 0, 0, 0, 0});
     for (size_t t = 0; t < T; ++t) {
+        const HostPlan &lp = local[t];
+        off[t + 1] = Off{off[t].call + int64_t(lp.calls.size()), off[t].bb + int64_t(lp.bb.size()),
+                         off[t].rec + int64_t(lp.recs.size()), off[t].comp + int64_t(lp.comps.size()),
+                         off[t].leaf + int64_t(lp.leaves.size()), off[t].lv + int64_t(lp.leaf_vtx.size())};
+        hp.n_levels = std::max(hp.n_levels, lp.n_levels);
+    }
+    hp.calls.resize(size_t(off[T].call));
+    hp.bb.resize(size_t(off[T].bb));
+    hp.recs.resize(size_t(off[T].rec));
+    hp.comps.resize(size_t(off[T].comp));
+    hp.leaves.resize(size_t(off[T].leaf));
+    hp.leaf_vtx.resize(size_t(off[T].lv));
+    hp.leaf_dist.resize(size_t(off[T].lv));
+    hp.leaf_pdist.resize(size_t(off[T].lv));
+    parallel_for(T, [&](size_t t) {
         const std::vector<int32_t> &vs = trees[t];
         HostPlan &lp = local[t];
-        const int64_t bb0 = int64_t(hp.bb.size()), rec0 = int64_t(hp.recs.size()), lv0 = int64_t(hp.leaf_vtx.size());
-        const int32_t comp0 = int32_t(hp.comps.size()), call0 = int32_t(hp.calls.size());
-        for (Call c : lp.calls) {
+        const Off &o = off[t];
+        for (size_t i = 0; i < lp.calls.size(); ++i) {
+            Call c = lp.calls[i];
             c.minv = vs[size_t(c.minv)];
-            c.bb_begin += bb0;
-            c.bb_end += bb0;
-            c.rec_begin += rec0;
-            c.rec_end += rec0;
-            c.comp_begin += comp0;
-            c.comp_end += comp0;
-            hp.calls.push_back(c);
+            c.bb_begin += o.bb;
+            c.bb_end += o.bb;
+            c.rec_begin += o.rec;
+            c.rec_end += o.rec;
+            c.comp_begin += int32_t(o.comp);
+            c.comp_end += int32_t(o.comp);
+            hp.calls[size_t(o.call) + i] = c;
         }
-        for (int32_t v : lp.bb) hp.bb.push_back(vs[size_t(v)]);
-        for (Rec r : lp.recs) {
+        for (size_t i = 0; i < lp.bb.size(); ++i) hp.bb[size_t(o.bb) + i] = vs[size_t(lp.bb[i])];
+        for (size_t i = 0; i < lp.recs.size(); ++i) {
+            Rec r = lp.recs[i];
             r.v = vs[size_t(r.v)];
-            if (r.comp >= 0) r.comp += comp0;
-            hp.recs.push_back(r);
+            if (r.comp >= 0) r.comp += int32_t(o.comp);
+            hp.recs[size_t(o.rec) + i] = r;
         }
-        for (Comp cp : lp.comps) {
-            cp.call += call0;
+        for (size_t i = 0; i < lp.comps.size(); ++i) {
+            Comp cp = lp.comps[i];
+            cp.call += int32_t(o.call);
             cp.minv = vs[size_t(cp.minv)];
-            hp.comps.push_back(cp);
+            hp.comps[size_t(o.comp) + i] = cp;
         }
-        for (Leaf lf : lp.leaves) {
+        for (size_t i = 0; i < lp.leaves.size(); ++i) {
+            Leaf lf = lp.leaves[i];
             lf.minv = vs[size_t(lf.minv)];
-            lf.begin += lv0;
-            lf.end += lv0;
-            hp.leaves.push_back(lf);
+            lf.begin += o.lv;
+            lf.end += o.lv;
+            hp.leaves[size_t(o.leaf) + i] = lf;
         }
-        for (int32_t v : lp.leaf_vtx) hp.leaf_vtx.push_back(vs[size_t(v)]);
-        hp.leaf_dist.insert(hp.leaf_dist.end(), lp.leaf_dist.begin(), lp.leaf_dist.end());
-        hp.leaf_pdist.insert(hp.leaf_pdist.end(), lp.leaf_pdist.begin(), lp.leaf_pdist.end());
-        hp.n_levels = std::max(hp.n_levels, lp.n_levels);
-        HostPlan().calls.swap(lp.calls);
+        for (size_t i = 0; i < lp.leaf_vtx.size(); ++i) {
+            hp.leaf_vtx[size_t(o.lv) + i] = vs[size_t(lp.leaf_vtx[i])];
+            hp.leaf_dist[size_t(o.lv) + i] = lp.leaf_dist[i];
+            hp.leaf_pdist[size_t(o.lv) + i] = lp.leaf_pdist[i];
+        }
         lp = HostPlan();
-    }
+    });
     return TFI_OK;
 }
 
@@ -933,25 +985,23 @@ int build_plan(HostPlan &hp, int32_t n, int32_t m, const int32_t *u, const int32
         }
         q[size_t(i)] = std::max<int64_t>(1, int64_t(r));
     }
-    // acyclicity by union-find (a forest on n vertices)
-    {
-        std::vector<int32_t> par(static_cast<size_t>(n));
-        std::iota(par.begin(), par.end(), 0);
-        auto find = [&](int32_t a) {
-            while (par[size_t(a)] != a) {
-                par[size_t(a)] = par[size_t(par[size_t(a)])];
-                a = par[size_t(a)];
-            }
-            return a;
-        };
-        for (int32_t i = 0; i < m; ++i) {
-            const int32_t a = find(u[i]), b = find(v[i]);
-            if (a == b) {
-                err = "edge " + std::to_string(i) + " closes a cycle (or repeats an edge)";
-                return TFI_ERR_NOT_TREE;
-            }
-            par[size_t(a)] = b;
+    // acyclicity by union-find (a forest on n vertices); the sets are the trees
+    std::vector<int32_t> par(static_cast<size_t>(n));
+    std::iota(par.begin(), par.end(), 0);
+    auto find = [&](int32_t a) {
+        while (par[size_t(a)] != a) {
+            par[size_t(a)] = par[size_t(par[size_t(a)])];
+            a = par[size_t(a)];
         }
+        return a;
+    };
+    for (int32_t i = 0; i < m; ++i) {
+        const int32_t a = find(u[i]), b = find(v[i]);
+        if (a == b) {
+            err = "edge " + std::to_string(i) + " closes a cycle (or repeats an edge)";
+            return TFI_ERR_NOT_TREE;
+        }
+        par[size_t(a)] = b;
     }
     // CSR, neighbours ascending
     hp.ptr.assign(size_t(n) + 1, 0);
@@ -969,39 +1019,48 @@ int build_plan(HostPlan &hp, int32_t n, int32_t m, const int32_t *u, const int32
         }
         hp.adj.resize(tmp.size());
         hp.qlen.resize(tmp.size());
-        for (int32_t a = 0; a < n; ++a) {
-            std::sort(tmp.begin() + hp.ptr[size_t(a)], tmp.begin() + hp.ptr[size_t(a) + 1]);
-            for (int64_t e = hp.ptr[size_t(a)]; e < hp.ptr[size_t(a) + 1]; ++e) {
-                hp.adj[size_t(e)] = tmp[size_t(e)].first;
-                hp.qlen[size_t(e)] = tmp[size_t(e)].second;
-            }
-        }
-    }
-    // trees of the forest, each as an ascending vertex list (tree order = smallest vertex)
-    std::vector<int32_t> tree_of(size_t(n), -1);
-    std::vector<std::vector<int32_t>> trees;
-    for (int32_t s0 = 0; s0 < n; ++s0) {
-        if (tree_of[size_t(s0)] >= 0) continue;
-        const int32_t id = int32_t(trees.size());
-        trees.emplace_back();
-        std::vector<int32_t> &vs = trees.back();
-        vs.push_back(s0);
-        tree_of[size_t(s0)] = id;
-        for (size_t h = 0; h < vs.size(); ++h)
-            for (int64_t e = hp.ptr[size_t(vs[h])]; e < hp.ptr[size_t(vs[h]) + 1]; ++e)
-                if (tree_of[size_t(hp.adj[size_t(e)])] < 0) {
-                    tree_of[size_t(hp.adj[size_t(e)])] = id;
-                    vs.push_back(hp.adj[size_t(e)]);
+        // each vertex's list sorted by neighbour (distinct in a forest), in blocks of vertices
+        constexpr int32_t kBlock = 1 << 14;
+        parallel_for(size_t((n + kBlock - 1) / kBlock), [&](size_t blk) {
+            const int32_t a0 = int32_t(blk) * kBlock, a1 = std::min(n, a0 + kBlock);
+            for (int32_t a = a0; a < a1; ++a) {
+                std::sort(tmp.begin() + hp.ptr[size_t(a)], tmp.begin() + hp.ptr[size_t(a) + 1]);
+                for (int64_t e = hp.ptr[size_t(a)]; e < hp.ptr[size_t(a) + 1]; ++e) {
+                    hp.adj[size_t(e)] = tmp[size_t(e)].first;
+                    hp.qlen[size_t(e)] = tmp[size_t(e)].second;
                 }
-        std::sort(vs.begin(), vs.end());
+            }
+        });
     }
+    // trees of the forest, each as an ascending vertex list (tree order = smallest
+    // vertex): number each union-find set at its smallest vertex, then place the
+    // vertices by tree in ascending order (a counting sort)
+    std::vector<int32_t> tree_of(static_cast<size_t>(n));
+    std::vector<int32_t> root_tree(size_t(n), -1);
+    std::vector<int64_t> tsize;
+    for (int32_t x = 0; x < n; ++x) {
+        const int32_t r = find(x);
+        if (root_tree[size_t(r)] < 0) {
+            root_tree[size_t(r)] = int32_t(tsize.size());
+            tsize.push_back(0);
+        }
+        tree_of[size_t(x)] = root_tree[size_t(r)];
+        ++tsize[size_t(tree_of[size_t(x)])];
+    }
+    std::vector<std::vector<int32_t>> trees(tsize.size());
+    for (size_t t = 0; t < trees.size(); ++t) trees[t].reserve(size_t(tsize[t]));
+    for (int32_t x = 0; x < n; ++x) trees[size_t(tree_of[size_t(x)])].push_back(x);
+    std::vector<int32_t>().swap(par);
+    std::vector<int32_t>().swap(root_tree);
     if (trees.size() <= 1) {
         Builder b(hp, true);
         if (int rc = b.run(err)) return rc;
     } else if (int rc = plan_forest(hp, trees, err)) {
         return rc;
     }
-    if (int rc = flatten(hp, err)) return rc;
+    std::vector<int32_t> roots(trees.size());
+    for (size_t t = 0; t < trees.size(); ++t) roots[t] = trees[t][0];
+    if (int rc = flatten(hp, roots, err)) return rc;
     hp.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return TFI_OK;
 }
