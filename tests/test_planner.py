@@ -142,3 +142,21 @@ def test_sweep_auto_selection_host_only():
     assert auto["n_jobs_sweep"] + auto["n_jobs_fft"] + auto["n_jobs_direct"] == plain["n_jobs_fft"] + plain["n_jobs_direct"]
     other = mk(W.KernelSpec.rational(1.0), sweep="auto")
     assert other["n_jobs_sweep"] == 0
+
+
+@pytest.mark.parametrize("policy", ["adaptive", "diameter", "centroid"])
+def test_parallel_planning_is_deterministic(policy):
+    # the planner decomposes the calls of a level (and the trees of a forest) on all
+    # host threads; the plan must not depend on their interleaving
+    single = W.configs.sweep("rrt", n=1 << 15, d=16)
+    forest = W.configs.uneven_batch(count=50, lo=8, hi=4000, d=16)
+    for cfg, s0 in ((single, 64), (forest, 16)):
+        exports = []
+        for _ in range(3):
+            p = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=policy, leaf_max=s0,
+                                   host_only=True)
+            exports.append({k: p.export(k) for k in ("calls", "backbone", "records", "leaves", "leaf_packs",
+                                                      "gather_order")})
+        for e in exports[1:]:
+            for k in e:
+                assert np.array_equal(e[k], exports[0][k]), k
