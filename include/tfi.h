@@ -131,7 +131,10 @@ typedef struct {
  * host (Algorithms 1 and 6 per call, iteratively), flatten it, sample f,
  * compute the kernel spectra in FP64, and (unless TFI_PLAN_HOST_ONLY) upload
  * everything and allocate the workspace on the current device. On success
- * *out owns host and device memory until tfi_destroy. */
+ * *out owns host and device memory until tfi_destroy. The host work runs on
+ * all hardware threads (std::thread::hardware_concurrency; the calls of one
+ * recursion level, or the trees of a forest, in parallel) and returns the same
+ * plan whatever the thread count. */
 tfi_status tfi_plan(const tfi_tree *tree, const tfi_kernel *kernel, const tfi_options *opt, tfi_plan_t *out);
 
 /* out = K F (the operator above). F, out: device, n x d, dtype; out is
