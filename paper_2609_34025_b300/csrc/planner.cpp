@@ -967,23 +967,45 @@ int build_plan(HostPlan &hp, int32_t n, int32_t m, const int32_t *u, const int32
                std::string &err) {
     const auto t0 = std::chrono::steady_clock::now();
     hp.n = n;
-    // validate and quantise: q_e = max(1, round(w_e / delta)), ties to even
+    // validate and quantise: q_e = max(1, round(w_e / delta)), ties to even; in
+    // blocks of edges, reporting the first failing edge as a serial pass would
     std::vector<int64_t> q(static_cast<size_t>(m));
-    for (int32_t i = 0; i < m; ++i) {
-        if (u[i] < 0 || u[i] >= n || v[i] < 0 || v[i] >= n || u[i] == v[i]) {
-            err = "edge " + std::to_string(i) + " has an out-of-range endpoint or is a self loop";
-            return TFI_ERR_NOT_TREE;
+    {
+        constexpr int32_t kEdgeBlock = 1 << 16;
+        const size_t nb = size_t((int64_t(m) + kEdgeBlock - 1) / kEdgeBlock);
+        std::vector<int32_t> bad_edge(nb, -1), bad_code(nb, 0);
+        parallel_for(nb, [&](size_t b) {
+            const int32_t i0 = int32_t(b) * kEdgeBlock, i1 = std::min(m, i0 + kEdgeBlock);
+            for (int32_t i = i0; i < i1; ++i) {
+                int code = 0;
+                double r = 0.0;
+                if (u[i] < 0 || u[i] >= n || v[i] < 0 || v[i] >= n || u[i] == v[i]) {
+                    code = TFI_ERR_NOT_TREE;
+                } else if (!std::isfinite(w[i]) || !(w[i] > 0.0)) {
+                    code = TFI_ERR_WEIGHT;
+                } else {
+                    r = std::nearbyint(w[i] / hp.delta);
+                    if (!(r < double(kGridMax))) code = TFI_ERR_GRID_OVERFLOW;
+                }
+                if (code) {
+                    bad_edge[b] = i;
+                    bad_code[b] = code;
+                    return;
+                }
+                q[size_t(i)] = std::max<int64_t>(1, int64_t(r));
+            }
+        });
+        for (size_t b = 0; b < nb; ++b) {
+            if (bad_edge[b] < 0) continue;
+            const int32_t i = bad_edge[b];
+            if (bad_code[b] == TFI_ERR_NOT_TREE)
+                err = "edge " + std::to_string(i) + " has an out-of-range endpoint or is a self loop";
+            else if (bad_code[b] == TFI_ERR_WEIGHT)
+                err = "edge " + std::to_string(i) + " has a weight that is not finite and positive";
+            else
+                err = "edge length / delta exceeds 2^30";
+            return bad_code[b];
         }
-        if (!std::isfinite(w[i]) || !(w[i] > 0.0)) {
-            err = "edge " + std::to_string(i) + " has a weight that is not finite and positive";
-            return TFI_ERR_WEIGHT;
-        }
-        const double r = std::nearbyint(w[i] / hp.delta);
-        if (!(r < double(kGridMax))) {
-            err = "edge length / delta exceeds 2^30";
-            return TFI_ERR_GRID_OVERFLOW;
-        }
-        q[size_t(i)] = std::max<int64_t>(1, int64_t(r));
     }
     // acyclicity by union-find (a forest on n vertices); the sets are the trees
     std::vector<int32_t> par(static_cast<size_t>(n));
@@ -1004,19 +1026,36 @@ int build_plan(HostPlan &hp, int32_t n, int32_t m, const int32_t *u, const int32
         par[size_t(a)] = b;
     }
     // CSR, neighbours ascending
+    // (degrees and slots by atomic counters; each list is sorted below, so the
+    // order in which the slots are claimed does not matter)
     hp.ptr.assign(size_t(n) + 1, 0);
-    for (int32_t i = 0; i < m; ++i) {
-        hp.ptr[size_t(u[i]) + 1]++;
-        hp.ptr[size_t(v[i]) + 1]++;
+    constexpr int32_t kEdgeBlock = 1 << 16;
+    const size_t neb = size_t((int64_t(m) + kEdgeBlock - 1) / kEdgeBlock);
+    {
+        std::vector<std::atomic<int64_t>> cnt(static_cast<size_t>(n));
+        for (auto &c : cnt) c.store(0, std::memory_order_relaxed);
+        parallel_for(neb, [&](size_t b) {
+            const int32_t i1 = std::min(m, int32_t(b) * kEdgeBlock + kEdgeBlock);
+            for (int32_t i = int32_t(b) * kEdgeBlock; i < i1; ++i) {
+                cnt[size_t(u[i])].fetch_add(1, std::memory_order_relaxed);
+                cnt[size_t(v[i])].fetch_add(1, std::memory_order_relaxed);
+            }
+        });
+        for (int32_t i = 0; i < n; ++i) hp.ptr[size_t(i) + 1] = hp.ptr[size_t(i)] + cnt[size_t(i)].load(std::memory_order_relaxed);
     }
-    for (int32_t i = 0; i < n; ++i) hp.ptr[size_t(i) + 1] += hp.ptr[size_t(i)];
     {
         std::vector<std::pair<int32_t, int64_t>> tmp(size_t(2 * int64_t(m)));
-        std::vector<int64_t> fill(hp.ptr.begin(), hp.ptr.end() - 1);
-        for (int32_t i = 0; i < m; ++i) {
-            tmp[size_t(fill[size_t(u[i])]++)] = std::make_pair(int32_t(v[i]), q[size_t(i)]);
-            tmp[size_t(fill[size_t(v[i])]++)] = std::make_pair(int32_t(u[i]), q[size_t(i)]);
-        }
+        std::vector<std::atomic<int64_t>> fill(static_cast<size_t>(n));
+        for (int32_t i = 0; i < n; ++i) fill[size_t(i)].store(hp.ptr[size_t(i)], std::memory_order_relaxed);
+        parallel_for(neb, [&](size_t b) {
+            const int32_t i1 = std::min(m, int32_t(b) * kEdgeBlock + kEdgeBlock);
+            for (int32_t i = int32_t(b) * kEdgeBlock; i < i1; ++i) {
+                tmp[size_t(fill[size_t(u[i])].fetch_add(1, std::memory_order_relaxed))] =
+                    std::make_pair(int32_t(v[i]), q[size_t(i)]);
+                tmp[size_t(fill[size_t(v[i])].fetch_add(1, std::memory_order_relaxed))] =
+                    std::make_pair(int32_t(u[i]), q[size_t(i)]);
+            }
+        });
         hp.adj.resize(tmp.size());
         hp.qlen.resize(tmp.size());
         // each vertex's list sorted by neighbour (distinct in a forest), in blocks of vertices

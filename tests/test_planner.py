@@ -160,3 +160,30 @@ def test_parallel_planning_is_deterministic(policy):
         for e in exports[1:]:
             for k in e:
                 assert np.array_equal(e[k], exports[0][k]), k
+
+
+def test_first_invalid_edge_is_reported_across_blocks():
+    # edges are validated in parallel blocks; the error names the first invalid edge in
+    # input order, as a single pass would
+    n = 200_000
+    u = np.arange(1, n, dtype=np.int32)
+    v = (u - 1).astype(np.int32)
+    w = np.ones(n - 1)
+
+    def error(u, v, w):
+        with pytest.raises(tfi.TfiError) as e:
+            tfi.Plan(n, u, v, w, delta=1.0, kernel=("expsum", [1.0, 1.0]), leaf_max=8, host_only=True)
+        return e.value.name, str(e.value)
+
+    w1 = w.copy()
+    w1[150_000], w1[70_000] = np.nan, -1.0
+    assert error(u, v, w1) == ("WEIGHT", "tfi error WEIGHT: edge 70000 has a weight that is not finite and positive")
+    u2, w2 = u.copy(), w.copy()
+    u2[140_000], w2[90_000] = n + 5, 0.0
+    assert error(u2, v, w2)[1].endswith("edge 90000 has a weight that is not finite and positive")
+    u3 = u.copy()
+    u3[100] = v[100]
+    assert error(u3, v, w1)[0] == "NOT_TREE" and "edge 100 " in error(u3, v, w1)[1]
+    w4 = w.copy()
+    w4[123_456] = 1e12
+    assert error(u, v, w4)[0] == "GRID_OVERFLOW"
