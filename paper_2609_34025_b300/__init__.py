@@ -285,6 +285,12 @@ class Plan:
         return {k: (float(b[i]), float(f[i])) for i, k in enumerate(STAGES)}
 
     def export(self, what: str) -> np.ndarray:
+        """The plan's decomposition or launch layout as an int64 array (one row per item):
+        "calls" (level, min vertex, |V(S)|, kind, m, H, L), "backbone" (p_1..p_m of every call),
+        "records" (call, vertex, depth, coordinate, component), "leaves" (level, min vertex, size),
+        "device_keys" (call, vertex, device depth, device coordinate; device plans only),
+        "leaf_packs" (CTA, leaf begin, leaf end, CTA vertex capacity) and "gather_order"
+        (vertices in the gather's order)."""
         code, width = EXPORTS[what]
         ln = ctypes.c_int64()
         _check(lib().tfi_plan_export(self._h, code, None, 0, ctypes.byref(ln)))
