@@ -113,15 +113,28 @@ void parallel_for(size_t n, Fn fn) {
 // members (membership is set for the whole level before it starts), and the
 // traversal tokens are unique across threads.
 class Builder {
+    // vertex-indexed scratch of the traversals; calls of one level use them at
+    // their own members only, so one set serves all concurrent calls of a level
+    struct Scratch {
+        std::vector<int32_t> onp, seen, par;
+        std::vector<int64_t> dist, sz, maxchild;
+        void init(int32_t n) {
+            onp.assign(size_t(n), 0);
+            seen.assign(size_t(n), 0);
+            par.assign(size_t(n), -1);
+            dist.assign(size_t(n), 0);
+            sz.assign(size_t(n), 0);
+            maxchild.assign(size_t(n), 0);
+        }
+    };
+    static constexpr int64_t kSplitMin = int64_t(1) << 15;  // calls this large build both candidates at once
+
 public:
     Builder(HostPlan &hp, bool parallel) : hp_(hp), n_(hp.n), parallel_(parallel) {
         member_.assign(size_t(n_), 0);
-        onp_.assign(size_t(n_), 0);
-        seen_.assign(size_t(n_), 0);
-        dist_.assign(size_t(n_), 0);
-        par_.assign(size_t(n_), -1);
-        sz_.assign(size_t(n_), 0);
-        maxchild_.assign(size_t(n_), 0);
+        a_.init(n_);
+        // a second set for the centroid branch of large calls (concurrent with the diameter branch)
+        if (parallel_ && n_ >= kSplitMin) b_.init(n_);
     }
 
     int run(std::string &err) {
@@ -132,7 +145,7 @@ public:
         std::vector<int32_t> order;
         for (int32_t s = 0; s < n_; ++s) {
             if (done[size_t(s)]) continue;
-            traverse(s, 1, order);
+            traverse(a_, s, 1, order);
             for (int32_t v : order) done[size_t(v)] = 1;
             cur.push_back(Item{0, order, 0});
         }
@@ -201,18 +214,28 @@ private:
         std::vector<int32_t> order;
         if (nS <= hp_.leaf_max) {
             r.leaf = true;
-            r.rc = leaf(it.level, r.minv, mtok, r, order);
+            r.rc = leaf(a_, it.level, r.minv, mtok, r, order);
             return;
         }
         if (hp_.policy == TFI_POLICY_CENTROID) {
-            decompose(mtok, {centroid(r.minv, nS, mtok, order)}, r.D);
+            decompose(a_, mtok, {centroid(a_, r.minv, nS, mtok, order)}, r.D);
             r.kind = 1;
         } else if (hp_.policy == TFI_POLICY_DIAMETER) {
-            decompose(mtok, diameter(r.minv, mtok, order), r.D);
+            decompose(a_, mtok, diameter(a_, r.minv, mtok, order), r.D);
         } else {
             Decomp dc;
-            decompose(mtok, diameter(r.minv, mtok, order), r.D);
-            decompose(mtok, {centroid(r.minv, nS, mtok, order)}, dc);
+            if (!b_.seen.empty() && nS >= kSplitMin) {
+                // both candidates at once, each in its own scratch set
+                std::thread th([&]() {
+                    std::vector<int32_t> order2;
+                    decompose(b_, mtok, {centroid(b_, r.minv, nS, mtok, order2)}, dc);
+                });
+                decompose(a_, mtok, diameter(a_, r.minv, mtok, order), r.D);
+                th.join();
+            } else {
+                decompose(a_, mtok, diameter(a_, r.minv, mtok, order), r.D);
+                decompose(a_, mtok, {centroid(a_, r.minv, nS, mtok, order)}, dc);
+            }
             // the centroid wins only with a strictly smaller score (Algorithm 6)
             if (score(nS, dc) < score(nS, r.D)) {
                 r.D = std::move(dc);
@@ -226,62 +249,62 @@ private:
     }
 
     // Traverse the members of S (member == mtok) from s into order: dist_, par_.
-    void traverse(int32_t s, int32_t mtok, std::vector<int32_t> &order) {
+    void traverse(Scratch &sc, int32_t s, int32_t mtok, std::vector<int32_t> &order) {
         const int32_t tok = ++tok_seen_;
         order.clear();
         order.push_back(s);
-        seen_[size_t(s)] = tok;
-        dist_[size_t(s)] = 0;
-        par_[size_t(s)] = -1;
+        sc.seen[size_t(s)] = tok;
+        sc.dist[size_t(s)] = 0;
+        sc.par[size_t(s)] = -1;
         for (size_t h = 0; h < order.size(); ++h) {
             const int32_t a = order[h];
             for (int64_t e = hp_.ptr[size_t(a)]; e < hp_.ptr[size_t(a) + 1]; ++e) {
                 const int32_t b = hp_.adj[size_t(e)];
-                if (member_[size_t(b)] == mtok && seen_[size_t(b)] != tok) {
-                    seen_[size_t(b)] = tok;
-                    dist_[size_t(b)] = dist_[size_t(a)] + hp_.qlen[size_t(e)];
-                    par_[size_t(b)] = a;
+                if (member_[size_t(b)] == mtok && sc.seen[size_t(b)] != tok) {
+                    sc.seen[size_t(b)] = tok;
+                    sc.dist[size_t(b)] = sc.dist[size_t(a)] + hp_.qlen[size_t(e)];
+                    sc.par[size_t(b)] = a;
                     order.push_back(b);
                 }
             }
         }
     }
 
-    int32_t farthest(const std::vector<int32_t> &order) const {
+    static int32_t farthest(const Scratch &sc, const std::vector<int32_t> &order) {
         int32_t best = order[0];
         for (int32_t v : order) {
-            if (dist_[size_t(v)] > dist_[size_t(best)] || (dist_[size_t(v)] == dist_[size_t(best)] && v < best)) best = v;
+            if (sc.dist[size_t(v)] > sc.dist[size_t(best)] || (sc.dist[size_t(v)] == sc.dist[size_t(best)] && v < best)) best = v;
         }
         return best;
     }
 
     // Weighted diameter path by two traversals and parent pointers (Algorithm 6, first step).
-    std::vector<int32_t> diameter(int32_t minv, int32_t mtok, std::vector<int32_t> &order) {
-        traverse(minv, mtok, order);
-        const int32_t a = farthest(order);
-        traverse(a, mtok, order);
-        const int32_t b = farthest(order);
+    std::vector<int32_t> diameter(Scratch &sc, int32_t minv, int32_t mtok, std::vector<int32_t> &order) {
+        traverse(sc, minv, mtok, order);
+        const int32_t a = farthest(sc, order);
+        traverse(sc, a, mtok, order);
+        const int32_t b = farthest(sc, order);
         std::vector<int32_t> path;
-        for (int32_t v = b; v != -1; v = par_[size_t(v)]) path.push_back(v);
+        for (int32_t v = b; v != -1; v = sc.par[size_t(v)]) path.push_back(v);
         std::reverse(path.begin(), path.end());
         return path;
     }
 
     // Centroid by a rooted traversal and subtree sizes (Algorithm 6, second step).
-    int32_t centroid(int32_t minv, int64_t nS, int32_t mtok, std::vector<int32_t> &order) {
-        traverse(minv, mtok, order);
+    int32_t centroid(Scratch &sc, int32_t minv, int64_t nS, int32_t mtok, std::vector<int32_t> &order) {
+        traverse(sc, minv, mtok, order);
         for (int32_t v : order) {
-            sz_[size_t(v)] = 1;
-            maxchild_[size_t(v)] = 0;
+            sc.sz[size_t(v)] = 1;
+            sc.maxchild[size_t(v)] = 0;
         }
         for (size_t i = order.size(); i-- > 1;) {
-            const int32_t v = order[i], p = par_[size_t(v)];
-            sz_[size_t(p)] += sz_[size_t(v)];
-            maxchild_[size_t(p)] = std::max(maxchild_[size_t(p)], sz_[size_t(v)]);
+            const int32_t v = order[i], p = sc.par[size_t(v)];
+            sc.sz[size_t(p)] += sc.sz[size_t(v)];
+            sc.maxchild[size_t(p)] = std::max(sc.maxchild[size_t(p)], sc.sz[size_t(v)]);
         }
         int32_t best = -1;
         for (int32_t v : order) {
-            const int64_t big = std::max<int64_t>(nS - sz_[size_t(v)], maxchild_[size_t(v)]);
+            const int64_t big = std::max<int64_t>(nS - sc.sz[size_t(v)], sc.maxchild[size_t(v)]);
             if (2 * big <= nS && (best < 0 || v < best)) best = v;
         }
         return best;
@@ -294,11 +317,11 @@ private:
     }
 
     // Algorithm 1: components, anchors, projections and depths for backbone P.
-    void decompose(int32_t mtok, std::vector<int32_t> P, Decomp &D) {
+    void decompose(Scratch &sc, int32_t mtok, std::vector<int32_t> P, Decomp &D) {
         D.clear();
         D.P = std::move(P);
         const int32_t ptok = ++tok_onp_;
-        for (int32_t p : D.P) onp_[size_t(p)] = ptok;
+        for (int32_t p : D.P) sc.onp[size_t(p)] = ptok;
         D.X.push_back(0);
         for (size_t j = 1; j < D.P.size(); ++j) D.X.push_back(D.X.back() + edge_len(D.P[j - 1], D.P[j]));
         const int32_t tok = ++tok_seen_;
@@ -306,9 +329,9 @@ private:
             const int32_t p = D.P[j];
             for (int64_t e = hp_.ptr[size_t(p)]; e < hp_.ptr[size_t(p) + 1]; ++e) {
                 const int32_t r = hp_.adj[size_t(e)];
-                if (member_[size_t(r)] != mtok || onp_[size_t(r)] == ptok || seen_[size_t(r)] == tok) continue;
+                if (member_[size_t(r)] != mtok || sc.onp[size_t(r)] == ptok || sc.seen[size_t(r)] == tok) continue;
                 const size_t start = D.cv.size();
-                seen_[size_t(r)] = tok;
+                sc.seen[size_t(r)] = tok;
                 D.cv.push_back(r);
                 D.cd.push_back(hp_.qlen[size_t(e)]);  // the attaching edge p - r
                 int64_t h = 0;
@@ -318,8 +341,8 @@ private:
                     h = std::max(h, da);
                     for (int64_t f = hp_.ptr[size_t(a)]; f < hp_.ptr[size_t(a) + 1]; ++f) {
                         const int32_t b = hp_.adj[size_t(f)];
-                        if (member_[size_t(b)] == mtok && onp_[size_t(b)] != ptok && seen_[size_t(b)] != tok) {
-                            seen_[size_t(b)] = tok;
+                        if (member_[size_t(b)] == mtok && sc.onp[size_t(b)] != ptok && sc.seen[size_t(b)] != tok) {
+                            sc.seen[size_t(b)] = tok;
                             D.cv.push_back(b);
                             D.cd.push_back(da + hp_.qlen[size_t(f)]);
                         }
@@ -381,33 +404,33 @@ private:
     // Dense leaf: vertices in preorder from the smallest vertex, children ascending,
     // with grid distances from that root (subtrees are contiguous ranges), and the
     // leaf's diameter; begin / end are set when it is appended to the plan.
-    int leaf(int32_t level, int32_t minv, int32_t mtok, Result &r, std::vector<int32_t> &order) {
+    int leaf(Scratch &sc, int32_t level, int32_t minv, int32_t mtok, Result &r, std::vector<int32_t> &order) {
         r.lf.level = level;
         r.lf.minv = minv;
         const int32_t tok = ++tok_seen_;
         std::vector<int32_t> stack, kids;
         stack.push_back(minv);
-        seen_[size_t(minv)] = tok;
-        dist_[size_t(minv)] = 0;
-        par_[size_t(minv)] = -1;
+        sc.seen[size_t(minv)] = tok;
+        sc.dist[size_t(minv)] = 0;
+        sc.par[size_t(minv)] = -1;
         while (!stack.empty()) {
             const int32_t v = stack.back();
             stack.pop_back();
-            if (dist_[size_t(v)] >= kGridMax / 2) {
+            if (sc.dist[size_t(v)] >= kGridMax / 2) {
                 r.err = "grid distance beyond 2^29 inside a leaf (choose a larger delta)";
                 return TFI_ERR_GRID_OVERFLOW;
             }
             r.lvtx.push_back(v);
-            r.ldist.push_back(int32_t(dist_[size_t(v)]));
-            const int32_t p = par_[size_t(v)];
-            r.lpdist.push_back(p >= 0 ? int32_t(dist_[size_t(p)]) : 0);
+            r.ldist.push_back(int32_t(sc.dist[size_t(v)]));
+            const int32_t p = sc.par[size_t(v)];
+            r.lpdist.push_back(p >= 0 ? int32_t(sc.dist[size_t(p)]) : 0);
             kids.clear();
             for (int64_t e = hp_.ptr[size_t(v)]; e < hp_.ptr[size_t(v) + 1]; ++e) {
                 const int32_t b = hp_.adj[size_t(e)];
-                if (member_[size_t(b)] == mtok && seen_[size_t(b)] != tok) {
-                    seen_[size_t(b)] = tok;
-                    dist_[size_t(b)] = dist_[size_t(v)] + hp_.qlen[size_t(e)];
-                    par_[size_t(b)] = v;
+                if (member_[size_t(b)] == mtok && sc.seen[size_t(b)] != tok) {
+                    sc.seen[size_t(b)] = tok;
+                    sc.dist[size_t(b)] = sc.dist[size_t(v)] + hp_.qlen[size_t(e)];
+                    sc.par[size_t(b)] = v;
                     kids.push_back(b);
                 }
             }
@@ -423,17 +446,18 @@ private:
                 far = r.lvtx[i];
             }
         }
-        traverse(far, mtok, order);
+        traverse(sc, far, mtok, order);
         r.lf.diam = 0;
-        for (int32_t v : order) r.lf.diam = std::max(r.lf.diam, dist_[size_t(v)]);
+        for (int32_t v : order) r.lf.diam = std::max(r.lf.diam, sc.dist[size_t(v)]);
         return TFI_OK;
     }
+
 
     HostPlan &hp_;
     int32_t n_;
     bool parallel_;
-    std::vector<int32_t> member_, onp_, seen_, par_;
-    std::vector<int64_t> dist_, sz_, maxchild_;
+    std::vector<int32_t> member_;
+    Scratch a_, b_;
     std::atomic<int32_t> tok_onp_{0}, tok_seen_{0};
 };
 
