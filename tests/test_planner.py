@@ -187,3 +187,14 @@ def test_first_invalid_edge_is_reported_across_blocks():
     w4 = w.copy()
     w4[123_456] = 1e12
     assert error(u, v, w4)[0] == "GRID_OVERFLOW"
+
+
+@pytest.mark.parametrize("n,edges", [(1, []), (2, [(0, 1)]), (5, [(0, 1), (3, 4)]), (7, []), (3, [(2, 0)])])
+@pytest.mark.parametrize("policy", ["adaptive", "diameter", "centroid"])
+def test_degenerate_forests_plan_on_the_host(n, edges, policy):
+    u = np.array([e[0] for e in edges], dtype=np.int32)
+    v = np.array([e[1] for e in edges], dtype=np.int32)
+    p = tfi.Plan(n, u, v, np.ones(len(edges)), delta=1.0, kernel=("expsum", [1.0, 1.0]), leaf_max=1,
+                 policy=policy, host_only=True)
+    assert np.array_equal(np.sort(p.export("gather_order")), np.arange(n))
+    assert p.info()["n_calls"] == sum(1 for _ in edges)  # every 2-vertex tree is one call at s0 = 1
