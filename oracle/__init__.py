@@ -16,9 +16,13 @@ Contents
                   tree path; one traversal per target, FP64 accumulation.
                   Also the distance-binned correlation used for the gradient
                   with respect to kernel parameters.
-``stad_literal``  the paper's StAd-TFI as its algorithms state it
-                  (DecomposeOffPathComponents, ComputeGTerm / ComputeGTerm2DFFT,
-                  CrossSubRoutine, Solve, ChooseBackbone, CrossSubRoutineExp),
+``kernels``       also d f(k delta) / d theta for every analytic kind (pinned by
+                  central differences of ``brute``).
+``stad_literal``  the paper's StAd-TFI: the decomposition (DecomposeOffPathComponents,
+                  ChooseBackbone), the table evaluators (ComputeGTerm / ComputeGTerm2DFFT,
+                  the Hankel product), the cross term from Lemma "Cross-component
+                  correction", the recursion of Eq. "stad-split" and the exponential
+                  sweeps (CrossSubRoutineExp),
                   in FP64 with numpy FFTs, on grid units; it also reports the
                   decomposition arrays (projections, depths, anchors, backbone
                   coordinates) for bit-exact comparison with the planner.

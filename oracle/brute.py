@@ -129,7 +129,7 @@ def corr_hist(tree, delta: float, G: np.ndarray, F: np.ndarray, targets=None, th
 
 
 def kernel_param_grad(tree, delta: float, spec, G: np.ndarray, F: np.ndarray, threads: int = 0) -> np.ndarray:
-    """dL/dtheta for an expsum kernel, given G = dL/dout: sum_k df(k delta)/dtheta * hist[k]."""
+    """dL/dtheta for an analytic kernel, given G = dL/dout: sum_k df(k delta)/dtheta * hist[k]."""
     from .kernels import grid_param_derivs
 
     adj = Adjacency(tree, delta)

@@ -41,17 +41,40 @@ def grid_table(spec, delta: float, kmax: int) -> np.ndarray:
 
 
 def grid_param_derivs(spec, delta: float, kmax: int) -> np.ndarray:
-    """d f(k delta) / d theta for an expsum spec, shape (len(params), kmax+1),
-    rows ordered like spec.params = [a_1, b_1, a_2, b_2, ...]."""
-    assert spec.kind == "expsum"
+    """d f(k delta) / d theta, shape (len(params), kmax+1), rows in the order
+    of spec.params, for every analytic kind. Derivatives of the closed forms:
+      expsum   a_i e^{-b_i x}:   e^{-b_i x},  -a_i x e^{-b_i x}
+      gauss    a e^{-c x^2}:     e^{-c x^2},  -a x^2 e^{-c x^2}
+      rational a u^{-p}, u = 1 + c x^e:
+               u^{-p},  -a p x^e u^{-p-1},  -a p c x^e ln(x) u^{-p-1},  -a ln(u) u^{-p}
+      powexp   a x^p e^{-b x}:   x^p e^{-b x},  a x^p ln(x) e^{-b x},  -a x^{p+1} e^{-b x}
+    At x = 0 the terms x^s ln(x) (s > 0) are taken at their limit 0."""
     x = np.arange(kmax + 1, dtype=np.float64) * delta
     p = [float(t) for t in spec.params]
-    rows = []
-    for a, b in zip(p[0::2], p[1::2]):
+    pos = x > 0
+    logx = np.where(pos, np.log(np.where(pos, x, 1.0)), 0.0)
+    if spec.kind == "expsum":
+        rows = []
+        for a, b in zip(p[0::2], p[1::2]):
+            e = np.exp(-b * x)
+            rows += [e, -a * x * e]
+        return np.stack(rows)
+    if spec.kind == "gauss":
+        a, c = p
+        e = np.exp(-c * x * x)
+        return np.stack([e, -a * x * x * e])
+    if spec.kind == "rational":
+        a, c, ex, pw = p
+        xe = np.where(pos, np.power(np.where(pos, x, 1.0), ex), 0.0)
+        u = 1.0 + c * xe
+        t = np.power(u, -pw)
+        return np.stack([t, -a * pw * xe * t / u, -a * pw * c * xe * logx * t / u, -a * np.log(u) * t])
+    if spec.kind == "powexp":
+        a, pw, b = p
+        xp = np.where(pos, np.power(np.where(pos, x, 1.0), pw), 1.0 if pw == 0 else 0.0)
         e = np.exp(-b * x)
-        rows.append(e)              # d/da
-        rows.append(-a * x * e)     # d/db
-    return np.stack(rows)
+        return np.stack([xp * e, a * xp * logx * e, -a * x * xp * e])
+    raise ValueError(f"no parameter derivatives for kernel kind {spec.kind!r}")
 
 
 def quantise(w: np.ndarray, delta: float) -> np.ndarray:

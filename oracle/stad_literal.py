@@ -265,8 +265,8 @@ def compute_g_hankel(A: np.ndarray, fv: np.ndarray) -> np.ndarray:
 
 
 def compute_e_fft(b: np.ndarray, fv: np.ndarray) -> np.ndarray:
-    """E[q] = sum_{r>=1} f(q + r) b[r], q = 0..H_alpha, by a zero-padded 1D FFT
-    after reversing the profile (Algorithm 4, correction step). b[0] = 0."""
+    """E[q] = sum_{r>=1} f(q + r) b[r], q = 0..H_alpha (Eq. "stad-E"), by a
+    zero-padded 1D FFT after reversing the profile. b[0] = 0."""
     Ha = b.shape[0] - 1
     brev = b[::-1]
     fseq = fv[: 2 * Ha + 1]
@@ -276,43 +276,54 @@ def compute_e_fft(b: np.ndarray, fv: np.ndarray) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# Algorithm 4: CrossSubRoutine(S, P, x, f)
+# Cross-component term of Eq. "stad-split" (Lemma "Cross-component correction")
 # ---------------------------------------------------------------------------
 
+def _vertex_coords(dec):
+    """Per vertex of S: depth d(u), backbone column X(pi(u)) and component
+    index (-1 on the backbone), as three aligned arrays plus the vertex ids."""
+    col_of = {p: dec["X"][j] for j, p in enumerate(dec["P"])}
+    comp_of = {}
+    for ci, comp in enumerate(dec["comps"]):
+        for u in comp["verts"]:
+            comp_of[u] = ci
+    verts = np.array(sorted(dec["d"]), dtype=np.int64)
+    depth = np.array([dec["d"][u] for u in verts.tolist()], dtype=np.int64)
+    col = np.array([col_of[dec["pi"][u]] for u in verts.tolist()], dtype=np.int64)
+    cid = np.array([comp_of.get(u, -1) for u in verts.tolist()], dtype=np.int64)
+    return verts, depth, col, cid
+
+
 def cross_subroutine(dec, x: np.ndarray, fv: np.ndarray, evaluator: str = "fft2d"):
-    P, X, H = dec["P"], dec["X"], dec["H"]
-    W = X[-1] + 1
-    d = x.shape[1]
+    """Cross_P(u) for every u in S (Lemma "Cross-component correction").
+
+    By Lemma "Distances through the backbone", a source v outside u's
+    component is at distance d(u) + |X(pi u) - X(pi v)| + d(v), so summing
+    f over all of S with that surrogate distance is the table
+    G_q[s] = sum_{r,t} f(q + |s - t| + r) A_r[t] of Eq. "sumofFFTterms",
+    A being the field binned by (depth, backbone column). The surrogate is
+    wrong exactly for sources in u's own component, whose surrogate
+    distance is d(u) + d(v); their total is E_alpha[d(u)] of Eq. "stad-E"
+    (sources at depth >= 1 only, since every vertex of a component has
+    depth >= 1). So Cross(u) = G[d(u), X(pi u)] - E_alpha(u)[d(u)], with no
+    correction on the backbone.
+    """
+    H, W, d = dec["H"], dec["X"][-1] + 1, x.shape[1]
+    verts, depth, col, cid = _vertex_coords(dec)
     A = np.zeros((H + 1, W, d))
-    for t, p in enumerate(P):
-        A[0, X[t]] = x[p]                                  # A_0[t] = x_{p_t}
-    for comp in dec["comps"]:
-        col = X[comp["anchor"]]
-        for u in comp["verts"]:
-            A[dec["d"][u], col] += x[u]
-    if evaluator == "fft2d":
-        G = compute_g_2dfft(A, fv)
-    elif evaluator == "fft1d":
-        G = compute_g_1d(A, fv)
-    elif evaluator == "hankel":
-        G = compute_g_hankel(A, fv)
-    else:
-        G = compute_g_direct(A, fv)
-    cross = {}
-    for t, p in enumerate(P):
-        cross[p] = G[0, X[t]]
+    np.add.at(A, (depth, col), x[verts])
+    G = {"fft2d": compute_g_2dfft, "fft1d": compute_g_1d, "hankel": compute_g_hankel}.get(
+        evaluator, compute_g_direct)(A, fv)
+    out = G[depth, col].copy()
     Es = []
-    for comp in dec["comps"]:
+    for ci, comp in enumerate(dec["comps"]):
+        mine = cid == ci
         b = np.zeros((comp["H"] + 1, d))
-        for u in comp["verts"]:
-            b[dec["d"][u]] += x[u]
+        np.add.at(b, depth[mine], x[verts[mine]])
         E = compute_e_fft(b, fv)
         Es.append(E)
-        col = X[comp["anchor"]]
-        for u in comp["verts"]:
-            q = dec["d"][u]
-            cross[u] = G[q, col] - E[q]
-    return cross, dict(A=A, G=G, E=Es)
+        out[mine] -= E[depth[mine]]
+    return {int(u): out[i] for i, u in enumerate(verts.tolist())}, dict(A=A, G=G, E=Es)
 
 
 # ---------------------------------------------------------------------------

@@ -30,7 +30,7 @@ def _grad_case(t, delta, spec, d, leaf_max, policy="adaptive", dtype=torch.float
     assert len(c) >= len(ref)
     ref = np.concatenate([ref, np.zeros(len(c) - len(ref))])
     assert _nerr(c, ref) <= tol
-    if spec.kind == "expsum":
+    if spec.kind != "table":
         assert _nerr(dth, brute.kernel_param_grad(t, delta, spec, Gn, Fn)) <= tol
     return p
 
@@ -52,6 +52,20 @@ def test_grad_attention_heads_fp32_and_bf16():
 def test_grad_weighted_grid_forest():
     cfg = W.configs.uneven_batch(count=10, lo=20, hi=800, d=8)
     _grad_case(cfg["tree"], cfg["delta"], W.KernelSpec.rational(0.1, e=1.0, p=2.0), 8, 32)
+
+
+@pytest.mark.parametrize("spec", [
+    W.KernelSpec.gauss(0.02, a=1.2),
+    W.KernelSpec.rational(0.1, e=1.5, p=2.0, a=0.9),
+    W.KernelSpec.powexp(0.2, p=1.3, a=1.1),
+], ids=["gauss", "rational", "powexp"])
+@pytest.mark.parametrize("leaf_max", [1, 32])
+def test_grad_dtheta_every_analytic_kind(spec, leaf_max):
+    # dL/dtheta of the gauss, rational and powexp kinds (each parameter, including the exponents
+    # whose derivatives carry ln x) against the oracle's analytic derivatives, themselves pinned by
+    # finite differences of the brute force
+    cfg = W.configs.uneven_batch(count=6, lo=20, hi=600, d=8)
+    _grad_case(cfg["tree"], 1.0, spec, 8, leaf_max)
 
 
 def test_grad_rejects_tables_beyond_one_transform():

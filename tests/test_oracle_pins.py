@@ -246,6 +246,34 @@ def test_kernel_parameter_gradient_by_finite_differences():
         assert abs((lp - lm) / (2 * h) - grad[k]) < 1e-6 * max(1.0, abs(grad[k]))
 
 
+@pytest.mark.parametrize("spec", [
+    W.KernelSpec.gauss(0.3, a=1.2),
+    W.KernelSpec.rational(0.4, e=1.5, p=2.0, a=0.9),
+    W.KernelSpec.powexp(0.7, p=1.3, a=1.1),
+    W.KernelSpec.powexp(0.3, p=2.5, a=0.8),
+], ids=["gauss", "rational", "powexp", "powexp_p2.5"])
+def test_kernel_parameter_gradient_other_kinds_by_finite_differences(spec):
+    # the analytic derivatives of every parametrised kind against central differences of the
+    # brute-force apply, on a weighted tree whose grid distances are not integers in x (ln x terms);
+    # powexp needs p > 0 here: at p = 0 its value at x = 0 (the self pairs) jumps from a to 0
+    rng = np.random.default_rng(19)
+    t = W.grid_spanning_tree(5, 5, rng)
+    t = W.Tree(t.n, t.u, t.v, rng.uniform(0.5, 2.0, t.n - 1))
+    delta = 0.25
+    x, g = rng.standard_normal((2, t.n, 3))
+    grad = brute.kernel_param_grad(t, delta, spec, g, x)
+    theta = list(spec.params)
+    assert grad.shape == (len(theta),)
+    for k in range(len(theta)):
+        h = 1e-6 * max(1.0, abs(theta[k]))
+        tp, tm = list(theta), list(theta)
+        tp[k] += h
+        tm[k] -= h
+        lp = np.sum(g * brute.integrate(t, delta, W.KernelSpec(spec.kind, tp), x))
+        lm = np.sum(g * brute.integrate(t, delta, W.KernelSpec(spec.kind, tm), x))
+        assert abs((lp - lm) / (2 * h) - grad[k]) < 1e-6 * max(1.0, abs(grad[k])), (spec.kind, k)
+
+
 # --- the paper's logged decompositions --------------------------------------
 
 def _golden():
