@@ -175,17 +175,21 @@ tfi_status tfi_apply_host(tfi_plan_t plan, const void *F_host, void *out_host, i
  * Instead of the plan's workspace and per-d work lists, this call uses one
  * file-scope device array of TFI_STATIC_SCRATCH_BYTES (32 MiB) that every GPU
  * loading libtfi holds until the process exits. It calls no cudaMalloc,
- * cudaFree or other allocating routine; it only copies this d's work lists
- * from host memory into that array (cudaMemcpyAsync on `stream`).
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
+ * cudaFree or other allocating routine and copies nothing from host memory:
+ * the work lists it needs for this d are written into that array by a small
+ * kernel on `stream` from plan-owned lists built by tfi_plan.
+ *   - The first call on a device does one-time set-up with that device
+ *     current: it looks up the array's device address (cudaGetSymbolAddress)
+ *     and raises the kernels' shared-memory limits. Make that first call
  *     before any stream capture.
  *   - Plans whose workspace at this d (bin sums, table values, leaf terms and
- *     work lists) exceeds TFI_STATIC_SCRATCH_BYTES are rejected with
- *     TFI_ERR_ARG; use tfi_apply for them.
- *   - All calls share the one array and each call overwrites what it reads, so
- *     no state carries over; but calls that overlap on the GPU (other streams,
- *     other plans, other threads) race on it. Serialise them.
+ *     work items) exceeds TFI_STATIC_SCRATCH_BYTES are rejected with
+ *     TFI_ERR_ARG; use tfi_apply for them. Plans with exponential-sweep or
+ *     Hankel-evaluator tables are rejected with TFI_ERR_UNSUPPORTED.
+ *   - All calls share the one array, which keeps the last call's contents;
+ *     each call writes every value it reads before reading it, so nothing
+ *     needs clearing. Calls that overlap on the GPU (other streams, other
+ *     plans, other threads) race on the array: serialise them.
  * F, out, d, dtype and stream follow tfi_apply. */
 #define TFI_STATIC_SCRATCH_BYTES (32u << 20)
 tfi_status tfi_apply_static(tfi_plan_t plan, const void *F, void *out, int32_t d, int32_t dtype, tfi_stream_t stream);
@@ -243,6 +247,20 @@ tfi_status tfi_kernel_grad(tfi_plan_t plan, const void *grad_out, const void *F,
  * plan's device buffers (synchronous; no allocation). */
 tfi_status tfi_set_kernel(tfi_plan_t plan, const tfi_kernel *kernel);
 
+/* Failure-detection self-test of the bounded device wait (no counterpart in the
+ * paper). Every tensor-core kernel waits for its MMAs on an mbarrier with a poll
+ * limit and, when the limit runs out, records the failure in a plan-owned flag
+ * and returns instead of hanging (tfi_plan_info.device_errors counts such flags).
+ * This call launches one CTA that initialises an mbarrier for one arrival,
+ * arrives on it only if `arrive` is non-zero, and then waits on it through the
+ * same bounded wait with at most max_polls polls (1 .. 2^26; with a short sleep
+ * between polls, 10^4 polls take well under a millisecond). It issues no MMA
+ * and allocates no tensor memory, so a wait that runs out leaves nothing in
+ * flight. Returns TFI_OK when the wait completed and TFI_ERR_TIMEOUT when it
+ * gave up, in which case the plan's self-test flag stays set (counted by
+ * device_errors) until the next call. Synchronises `stream`. */
+tfi_status tfi_selftest_wait(tfi_plan_t plan, int32_t arrive, int32_t max_polls, tfi_stream_t stream);
+
 /* Release everything the plan owns. NULL is accepted and ignored. */
 tfi_status tfi_destroy(tfi_plan_t plan);
 
@@ -294,6 +312,12 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
  *                       counterpart: this is a launch layout (base case of Algorithm 5).
  *   TFI_EXPORT_GATHER_ORDER the n vertices in the order the output gather takes them: a
  *                       depth-first preorder of the forest, tree by tree. Launch layout only.
+ *   TFI_EXPORT_JOBS     7 per table job (a call's cross table or a component's correction), in plan
+ *                       order: evaluator (0 FFT, 1 direct, 2 exponential sweep, 3 Hankel product),
+ *                       log2 of the FFT points (-1 unless FFT), 1 for a correction, occupied bins,
+ *                       the first member vertex of its first bin and the last member of its last
+ *                       bin (-1 for a job without bins), and its largest depth (grid units).
+ *                       Vertices named here read this job's table in the gather.
  * If dst is NULL (or cap too small) only *len (number of int64 values) is set. */
 #define TFI_EXPORT_CALLS    0
 #define TFI_EXPORT_BACKBONE 1
@@ -302,6 +326,7 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
 #define TFI_EXPORT_DEVICE_KEYS 4
 #define TFI_EXPORT_LEAF_PACKS  5
 #define TFI_EXPORT_GATHER_ORDER 6
+#define TFI_EXPORT_JOBS         7
 tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t cap, int64_t *len);
 
 /* Stages of an apply, in launch order, for profiling and the roofline model:

@@ -26,7 +26,7 @@ KERNEL_KINDS = {"table": 0, "expsum": 1, "gauss": 2, "rational": 3, "powexp": 4}
 POLICIES = {"adaptive": 0, "diameter": 1, "centroid": 2}
 DTYPE_F32, DTYPE_BF16 = 0, 1
 EXPORTS = {"calls": (0, 7), "backbone": (1, 1), "records": (2, 5), "leaves": (3, 3), "device_keys": (4, 4),
-           "leaf_packs": (5, 4), "gather_order": (6, 1)}
+           "leaf_packs": (5, 4), "gather_order": (6, 1), "jobs": (7, 7)}
 
 
 class TfiError(RuntimeError):
@@ -62,7 +62,8 @@ class _Info(ctypes.Structure):
 EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_host", "tfi_destroy",
                     "tfi_plan_get_info", "tfi_plan_export", "tfi_profile_enable", "tfi_profile_read",
                     "tfi_stage_model", "tfi_apply_static", "tfi_dense_apply", "tfi_graph_create", "tfi_graph_launch",
-                    "tfi_graph_destroy", "tfi_sinkhorn", "tfi_kernel_grad", "tfi_set_kernel", "tfi_last_error")
+                    "tfi_graph_destroy", "tfi_sinkhorn", "tfi_kernel_grad", "tfi_set_kernel", "tfi_selftest_wait",
+                    "tfi_last_error")
 STAGES = ("leaf", "bucket", "fft", "direct", "gather", "sweep", "hankel")
 HANKEL_MODES = {None: 0, False: 0, "auto": 4, "all": 8}
 SWEEP_MODES = {None: 0, False: 0, True: 2, "all": 2, "auto": 32}
@@ -265,6 +266,15 @@ class Plan:
         _check(lib().tfi_plan_get_info(self._h, ctypes.byref(inf)))
         return {name: getattr(inf, name) for name, _ in _Info._fields_}
 
+    def selftest_wait(self, arrive: bool, max_polls: int = 10_000, stream=None) -> bool:
+        """Run the bounded-wait self-test (tfi_selftest_wait): True if the wait completed, False if
+        it ran out of polls (TFI_ERR_TIMEOUT; the plan's device_errors then counts it)."""
+        code = lib().tfi_selftest_wait(self._h, int(bool(arrive)), int(max_polls), _stream_handle(stream))
+        if code == 7:  # TFI_ERR_TIMEOUT
+            return False
+        _check(code)
+        return True
+
     def profile(self, enable: bool = True, serialize: bool = False):
         """Start (clearing totals) or stop per-stage CUDA-event timing; serialize runs every stage
         on the caller's stream, so each stage is timed alone."""
@@ -289,8 +299,9 @@ class Plan:
         "calls" (level, min vertex, |V(S)|, kind, m, H, L), "backbone" (p_1..p_m of every call),
         "records" (call, vertex, depth, coordinate, component), "leaves" (level, min vertex, size),
         "device_keys" (call, vertex, device depth, device coordinate; device plans only),
-        "leaf_packs" (CTA, leaf begin, leaf end, CTA vertex capacity) and "gather_order"
-        (vertices in the gather's order)."""
+        "leaf_packs" (CTA, leaf begin, leaf end, CTA vertex capacity), "gather_order"
+        (vertices in the gather's order) and "jobs" (evaluator, log2 FFT points, is correction,
+        bins, first member vertex, last member vertex, largest depth)."""
         code, width = EXPORTS[what]
         ln = ctypes.c_int64()
         _check(lib().tfi_plan_export(self._h, code, None, 0, ctypes.byref(ln)))

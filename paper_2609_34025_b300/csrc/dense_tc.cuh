@@ -71,10 +71,11 @@ __device__ __forceinline__ void bar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
 
-// Bounded wait on an mbarrier phase; returns false if it gave up.
-__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase: at most `limit` polls (backing off with a short
+// sleep after the first 64); returns false if it gave up.
+__device__ __forceinline__ bool bar_wait_n(uint64_t *bar, uint32_t parity, uint32_t limit) {
     const uint32_t a = smem_addr(bar);
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -86,6 +87,23 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
         if (it > 64) __nanosleep(64);
     }
     return false;
+}
+
+// The wait every tensor-core kernel uses on its MMA-completion mbarrier.
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) { return bar_wait_n(bar, parity, kSpinLimit); }
+
+// Failure-detection self-test: one thread initialises an mbarrier for one arrival,
+// optionally arrives on it, then waits for its first phase with at most `limit` polls
+// through the same bounded wait as the tensor-core kernels. With no arrival nothing can
+// complete the phase, so the wait runs out and the kernel records that in *err and
+// returns. No MMA is issued and no tensor memory is allocated.
+__global__ void bounded_wait_probe(int arrive, uint32_t limit, int32_t *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    bar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar)) : "memory");
+    if (!bar_wait_n(&bar, 0, limit)) *err = 1;
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *holder, uint32_t ncols) {

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -116,10 +117,19 @@ struct tfi_plan_s {
     std::vector<int32_t> dn_tree_ptr_h;
     double device_keys_ms = 0.0;
     int32_t n_hankel = 0;           // jobs evaluated by the Hankel-matrix product
-    int32_t *hk_err = nullptr;      // [0]: a Hankel CTA, [1]: a tensor-core leaf CTA whose bounded MMA wait gave up
+    int32_t *hk_err = nullptr;      // [0]: a Hankel CTA, [1]: a tensor-core leaf CTA whose bounded MMA wait gave up,
+                                    // [2]: the last tfi_selftest_wait gave up
     tfi::tc::LeafTile *leaf_tiles = nullptr;  // 128-row tiles of the leaf groups (tensor-core leaves)
     int32_t n_leaf_tiles = 0;
     std::map<int, WorkLists> work;  // per channel count d
+    // tfi_apply_static: its work lists without per-call host copies. Direct items do not depend
+    // on d; FFT jobs are kept by size class and expanded into (job, pair block) items on the
+    // device at each call, into the static workspace
+    tfi::dev::DirItem *st_dir = nullptr;
+    int32_t n_st_dir = 0;
+    int32_t *st_fft_job = nullptr;
+    std::vector<int> st_cls_lnp;
+    std::vector<int32_t> st_cls_joff, st_cls_njobs;
     // fork/join inside an apply: leaf terms and direct jobs run on their own
     // streams, concurrently with the bin sums and FFT jobs
     // aux[0]: leaves, aux[1]: direct / Hankel jobs, aux[2]: the critical path bin sums -> FFT jobs
@@ -257,9 +267,25 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
 
 constexpr int32_t kBucketSeg = 32;  // members per bin-sum segment
 
+constexpr int kMaxDevices = 256;
+std::atomic<int> g_sm_count[kMaxDevices] = {};
+
+// Streaming multiprocessors of the current device (read once per device).
+int device_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 148;
+    int v = g_sm_count[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        g_sm_count[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+// Grid of a grid-stride kernel: enough CTAs for the work, at most 32 per SM.
 int grid_for(int64_t work, int threads) {
     const int64_t b = (work + threads - 1) / threads;
-    return int(std::max<int64_t>(1, std::min<int64_t>(b, 148 * 32)));
+    return int(std::max<int64_t>(1, std::min<int64_t>(b, int64_t(device_sms()) * 32)));
 }
 
 constexpr int kLeafWarpThreads = 256;  // leaf_warp_kernel CTAs: 8 warps
@@ -415,10 +441,19 @@ void launch_direct(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
                                                                               p->key_x, d, p->kbuf, p->vbuf, p->ftab);
 }
 
-bool g_attr_done = false;
+std::mutex g_attr_mu;
+std::atomic<bool> g_attr_done[kMaxDevices] = {};
 
+// Raises the dynamic shared-memory limits of the kernels that need more than 48 KB,
+// once per device (the attribute is per device): under a mutex, so that concurrent
+// first calls on one device do not race, with a lock-free fast path afterwards.
 tfi_status set_attributes() {
-    if (g_attr_done) return TFI_OK;
+    int dev = -1;
+    TFI_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(TFI_ERR_ARG, "device ordinal out of range");
+    if (g_attr_done[dev].load(std::memory_order_acquire)) return TFI_OK;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (g_attr_done[dev].load(std::memory_order_relaxed)) return TFI_OK;
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_x2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
     TFI_CUDA(cudaFuncSetAttribute(tfi::tc::hankel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -445,7 +480,7 @@ tfi_status set_attributes() {
     LEAF_WARP_ATTR2(__nv_bfloat16, 4) LEAF_WARP_ATTR2(__nv_bfloat16, 8) LEAF_WARP_ATTR2(__nv_bfloat16, 16)
 #undef LEAF_WARP_ATTR2
 #undef LEAF_WARP_ATTR
-    g_attr_done = true;
+    g_attr_done[dev].store(true, std::memory_order_release);
     return TFI_OK;
 }
 
@@ -735,6 +770,29 @@ tfi_status upload_plan(tfi_plan_t p) {
         jd[j].pad = 0;
     }
     if (tfi_status rc = p->upload(&p->jobs, jd)) return rc;
+    {
+        std::vector<tfi::dev::DirItem> dir;
+        std::map<int, std::vector<int32_t>> by_class;
+        for (size_t j = 0; j < hp.jobs.size(); ++j) {
+            const tfi::Job &jb = hp.jobs[j];
+            if (jb.ke == jb.kb || jb.mode == 2 || jb.mode == 3) continue;
+            if (jb.mode == 0) {
+                by_class[jb.lp1 + jb.lp2].push_back(int32_t(j));
+            } else {
+                for (int64_t q = jb.kb; q < jb.ke; q += 64) dir.push_back(tfi::dev::DirItem{int32_t(j), int32_t(q)});
+            }
+        }
+        std::vector<int32_t> fj;
+        for (auto &kv : by_class) {
+            p->st_cls_lnp.push_back(kv.first);
+            p->st_cls_joff.push_back(int32_t(fj.size()));
+            p->st_cls_njobs.push_back(int32_t(kv.second.size()));
+            fj.insert(fj.end(), kv.second.begin(), kv.second.end());
+        }
+        if (tfi_status rc = p->upload(&p->st_dir, dir)) return rc;
+        if (tfi_status rc = p->upload(&p->st_fft_job, fj)) return rc;
+        p->n_st_dir = int32_t(dir.size());
+    }
     p->n_hankel = 0;
     for (const tfi::Job &jb : hp.jobs) p->n_hankel += jb.mode == 3;
     {
@@ -884,15 +942,14 @@ tfi_status check_apply_args(tfi_plan_t p, const void *a, const void *b, int32_t 
 constexpr size_t kStaticScratchBytes = size_t(TFI_STATIC_SCRATCH_BYTES);
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxStaticDevices = 256;
 std::mutex g_static_mu;
-void *g_static_addr[kMaxStaticDevices] = {};
+void *g_static_addr[kMaxDevices] = {};
 
 // Device address of g_static_scratch on device `dev` (which must be current).
 // In host code the symbol names a host-side stand-in, so the address is looked
 // up once per device with cudaGetSymbolAddress and cached.
 tfi_status static_scratch_address(int dev, unsigned char **out) {
-    if (dev < 0 || dev >= kMaxStaticDevices) return fail(TFI_ERR_ARG, "device ordinal out of range for the static workspace");
+    if (dev < 0 || dev >= kMaxDevices) return fail(TFI_ERR_ARG, "device ordinal out of range for the static workspace");
     std::lock_guard<std::mutex> lock(g_static_mu);
     if (!g_static_addr[dev]) {
         void *ptr = nullptr;
@@ -907,46 +964,43 @@ tfi_status static_scratch_address(int dev, unsigned char **out) {
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
+// FFT work items of one size class for tfi_apply_static: job list entry i / per, channel
+// pairs (i % per) * np ... of at most np pairs, for `pairs` channel pairs in all.
+__global__ void expand_fft_items(const int32_t *__restrict__ job, int n_jobs, int per, int np, int pairs,
+                                 tfi::dev::FftItem *__restrict__ items) {
+    const int64_t total = int64_t(n_jobs) * per;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int j = int(i / per), r = int(i - int64_t(j) * per);
+        items[i] = tfi::dev::FftItem{job[j], r * np, min(np, pairs - r * np)};
+    }
+}
+
 template <typename T>
 tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     if (p->n_sweeps > 0 || p->n_sw_ejobs > 0)
         return fail(TFI_ERR_UNSUPPORTED, "tfi_apply_static does not run exponential-sweep plans");
     if (p->n_hankel > 0) return fail(TFI_ERR_UNSUPPORTED, "tfi_apply_static does not run Hankel-evaluator plans");
     if (tfi_status rc = set_attributes()) return rc;
-    // work lists for d, built on the host (same grouping as the plan-owned path)
+    // FFT items for this d: per size class, one item per (job, block of np channel pairs),
+    // written into the static array by expand_fft_items (no host-sourced copy)
     const int pairs = (d + 1) / 2;
-    std::map<int, std::vector<tfi::dev::FftItem>> by_class;
-    std::vector<tfi::dev::DirItem> dir;
-    for (size_t j = 0; j < p->hp.jobs.size(); ++j) {
-        const tfi::Job &jb = p->hp.jobs[j];
-        if (jb.ke == jb.kb || jb.mode == 2) continue;
-        if (jb.mode == 0) {
-            const int lnp = jb.lp1 + jb.lp2;
-            const int np = fft_pairs_per_cta(lnp, pairs);
-            for (int p0 = 0; p0 < pairs; p0 += np)
-                by_class[lnp].push_back(tfi::dev::FftItem{int32_t(j), p0, std::min(np, pairs - p0)});
-        } else {
-            for (int64_t q = jb.kb; q < jb.ke; q += 64) dir.push_back(tfi::dev::DirItem{int32_t(j), int32_t(q)});
-        }
+    const size_t n_cls = p->st_cls_lnp.size();
+    std::vector<int> cls_np(n_cls), cls_per(n_cls);
+    std::vector<int64_t> cls_off(n_cls);
+    int64_t n_fft = 0;
+    for (size_t c = 0; c < n_cls; ++c) {
+        cls_np[c] = fft_pairs_per_cta(p->st_cls_lnp[c], pairs);
+        cls_per[c] = (pairs + cls_np[c] - 1) / cls_np[c];
+        cls_off[c] = n_fft;
+        n_fft += int64_t(p->st_cls_njobs[c]) * cls_per[c];
     }
-    std::vector<tfi::dev::FftItem> fft_all;
-    std::vector<int> cls_lnp, cls_count, cls_npair;
-    std::vector<size_t> cls_off;
-    for (auto &kv : by_class) {
-        cls_lnp.push_back(kv.first);
-        cls_count.push_back(int(kv.second.size()));
-        cls_npair.push_back(fft_pairs_per_cta(kv.first, pairs));
-        cls_off.push_back(fft_all.size());
-        fft_all.insert(fft_all.end(), kv.second.begin(), kv.second.end());
-    }
-    // carve the static array: bin sums, table values, leaf terms, work lists
+    // carve the static array: bin sums, table values, leaf terms, FFT items
     const size_t K = p->hp.key_r.size(), n = size_t(p->hp.n);
     const size_t o_k = 0;
     const size_t o_v = o_k + align256(K * size_t(d) * sizeof(float));
     const size_t o_l = o_v + align256(K * size_t(d) * sizeof(float));
     const size_t o_f = o_l + align256(n * size_t(d) * sizeof(float));
-    const size_t o_d = o_f + align256(fft_all.size() * sizeof(tfi::dev::FftItem));
-    const size_t total = o_d + align256(dir.size() * sizeof(tfi::dev::DirItem));
+    const size_t total = o_f + align256(size_t(n_fft) * sizeof(tfi::dev::FftItem));
     if (total > kStaticScratchBytes)
         return fail(TFI_ERR_ARG, "plan needs " + std::to_string(total) + " bytes of workspace at d=" + std::to_string(d) +
                                      ", more than the static workspace of " + std::to_string(kStaticScratchBytes) +
@@ -957,29 +1011,26 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
     float *vbuf = reinterpret_cast<float *>(base + o_v);
     float *lbuf = reinterpret_cast<float *>(base + o_l);
     auto *d_fft = reinterpret_cast<tfi::dev::FftItem *>(base + o_f);
-    auto *d_dir = reinterpret_cast<tfi::dev::DirItem *>(base + o_d);
-    // pageable sources: each copy returns once the host data has been staged
-    if (!fft_all.empty())
-        TFI_CUDA(cudaMemcpyAsync(d_fft, fft_all.data(), fft_all.size() * sizeof(fft_all[0]), cudaMemcpyHostToDevice, s));
-    if (!dir.empty())
-        TFI_CUDA(cudaMemcpyAsync(d_dir, dir.data(), dir.size() * sizeof(dir[0]), cudaMemcpyHostToDevice, s));
     // every workspace value an apply reads is written earlier in the same apply,
     // so nothing needs clearing between calls
     if (p->n_groups > 0) launch_leaf<16>(p, F, lbuf, d, s);
     if (K > 0) {
         tfi::dev::bucket_kernel<T, 1><<<grid_for(int64_t(K) * d, 256), 256, 0, s>>>(int64_t(K), p->key_ptr, p->key_vtx,
                                                                                    F, d, kbuf);
-        for (size_t c = 0; c < cls_lnp.size(); ++c) {
+        for (size_t c = 0; c < n_cls; ++c) {
+            const int64_t cnt = int64_t(p->st_cls_njobs[c]) * cls_per[c];
+            expand_fft_items<<<grid_for(cnt, 256), 256, 0, s>>>(p->st_fft_job + p->st_cls_joff[c], p->st_cls_njobs[c],
+                                                                cls_per[c], cls_np[c], pairs, d_fft + cls_off[c]);
             const size_t smem =
-                size_t(cls_npair[c]) * size_t(tfi::dev::padded_size(1 << cls_lnp[c])) * sizeof(float2);
-            tfi::dev::fft_kernel<<<cls_count[c], kFftThreads, smem, s>>>(d_fft + cls_off[c], p->jobs, p->key_r,
-                                                                        p->key_x, d, kbuf, vbuf, p->spectra,
-                                                                        p->twiddle);
+                size_t(cls_np[c]) * size_t(tfi::dev::padded_size(1 << p->st_cls_lnp[c])) * sizeof(float2);
+            tfi::dev::fft_kernel<<<unsigned(cnt), kFftThreads, smem, s>>>(d_fft + cls_off[c], p->jobs, p->key_r,
+                                                                          p->key_x, d, kbuf, vbuf, p->spectra,
+                                                                          p->twiddle);
         }
-        if (!dir.empty()) {
+        if (p->n_st_dir > 0) {
             constexpr int WARPS = 4;
-            dim3 grid((unsigned(dir.size()) + WARPS - 1) / WARPS, (d + 15) / 16);
-            tfi::dev::direct_kernel<16, WARPS, false><<<grid, 32 * WARPS, 0, s>>>(d_dir, int(dir.size()), p->jobs,
+            dim3 grid((unsigned(p->n_st_dir) + WARPS - 1) / WARPS, (d + 15) / 16);
+            tfi::dev::direct_kernel<16, WARPS, false><<<grid, 32 * WARPS, 0, s>>>(p->st_dir, p->n_st_dir, p->jobs,
                                                                                   p->key_r, p->key_x, d, kbuf, vbuf,
                                                                                   p->ftab);
         }
@@ -1553,6 +1604,23 @@ tfi_status tfi_set_kernel(tfi_plan_t plan, const tfi_kernel *kernel) {
     return TFI_OK;
 }
 
+tfi_status tfi_selftest_wait(tfi_plan_t plan, int32_t arrive, int32_t max_polls, tfi_stream_t stream) {
+    if (!plan) return fail(TFI_ERR_ARG, "null plan");
+    if (!plan->on_device) return fail(TFI_ERR_NO_DEVICE, "plan was built host-only");
+    if (max_polls < 1 || uint32_t(max_polls) > tfi::tc::kSpinLimit)
+        return fail(TFI_ERR_ARG, "max_polls must be in [1, 2^26]");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t *slot = plan->hk_err + 2;  // the self-test's own error slot, counted in device_errors
+    TFI_CUDA(cudaMemsetAsync(slot, 0, 4, s));
+    tfi::tc::bounded_wait_probe<<<1, 32, 0, s>>>(arrive != 0, uint32_t(max_polls), slot);
+    TFI_CUDA(cudaGetLastError());
+    int32_t gave_up = 0;
+    TFI_CUDA(cudaMemcpyAsync(&gave_up, slot, 4, cudaMemcpyDeviceToHost, s));
+    TFI_CUDA(cudaStreamSynchronize(s));
+    if (gave_up) return fail(TFI_ERR_TIMEOUT, "the bounded mbarrier wait gave up");
+    return TFI_OK;
+}
+
 tfi_status tfi_graph_launch(tfi_graph_t graph, tfi_stream_t stream) {
     if (!graph || !graph->exec) return fail(TFI_ERR_ARG, "null graph");
     TFI_CUDA(cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
@@ -1602,9 +1670,9 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info) {
     info->device_keys_ms = plan->device_keys_ms;
     info->hist_len = hp.hist_len;
     if (plan->hk_err) {
-        int32_t v[2] = {0, 0};
-        TFI_CUDA(cudaMemcpy(v, plan->hk_err, 8, cudaMemcpyDeviceToHost));
-        info->device_errors += (v[0] != 0) + (v[1] != 0);
+        int32_t v[3] = {0, 0, 0};
+        TFI_CUDA(cudaMemcpy(v, plan->hk_err, 12, cudaMemcpyDeviceToHost));
+        info->device_errors += (v[0] != 0) + (v[1] != 0) + (v[2] != 0);
     }
     if (plan->dn_err) {
         int32_t v = 0;
@@ -1744,6 +1812,15 @@ tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t 
                 }
             break;
         }
+        case TFI_EXPORT_JOBS:
+            for (const tfi::Job &j : hp.jobs) {
+                const bool any = j.ke > j.kb;
+                const int64_t row[7] = {j.mode, j.mode == 0 ? j.lp1 + j.lp2 : -1, j.is_comp, j.ke - j.kb,
+                                        any ? hp.key_vtx[size_t(hp.key_ptr[size_t(j.kb)])] : -1,
+                                        any ? hp.key_vtx[size_t(hp.key_ptr[size_t(j.ke)] - 1)] : -1, j.maxr};
+                v.insert(v.end(), row, row + 7);
+            }
+            break;
         case TFI_EXPORT_GATHER_ORDER: {
             const std::vector<int32_t> order = depth_first_order(hp);
             v.assign(order.begin(), order.end());

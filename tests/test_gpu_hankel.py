@@ -92,9 +92,10 @@ def test_auto_selection_and_determinism():
     x = torch.randn(h["tree"].n, 4096, device="cuda", dtype=torch.bfloat16)
     y1, y2 = p.apply(x), p.apply(x)
     assert torch.equal(y1, y2)
-    ref = q.apply(x).float()
-    for y in (y1.float(), auto.apply(x).float()):
-        assert ((y - ref).abs().max(0).values / ref.abs().max(0).values).max().item() <= 1e-2
+    # every evaluator choice against the FP64 oracle on the BF16-rounded input
+    ref = brute.integrate(h["tree"], 1.0, h["kernel"], x.double().cpu().numpy())
+    for y in (y1, auto.apply(x), q.apply(x)):
+        assert _err(y.double().cpu().numpy(), ref) <= TOL["bf16"]
 
 
 def test_adjoint_graph_and_kernel_grad():
@@ -114,4 +115,4 @@ def test_adjoint_graph_and_kernel_grad():
     assert torch.equal(out, p.apply(x)) and torch.equal(gF, p.apply(z))
     _, dth = p.kernel_grad(z, x)
     ref = brute.kernel_param_grad(t, 1.0, spec, z.cpu().double().numpy(), x.cpu().double().numpy())
-    assert np.abs(np.asarray(dth) - ref).max() <= 1e-3 * np.abs(ref).max()
+    assert np.abs(np.asarray(dth) - ref).max() <= 1e-4 * np.abs(ref).max()

@@ -114,8 +114,64 @@ def test_attention_grid_trees(dtype):
         assert _err(y, ref) <= TOL[dtype]
 
 
-def test_full_size_sampled_rrt_2p20():
-    # the benchmark workload at full size, checked on sampled outputs the oracle computes one by one
+def _stratified_targets(p, n, seed, per=96, n_random=128):
+    """Target vertices that reach every part of a plan: backbone vertices of the top two
+    recursion levels, the deepest records, the smallest vertex of the largest dense leaves,
+    member vertices of tables of every FFT size class and of direct tables, and uniform ones."""
+    rng = np.random.default_rng(seed)
+    calls, bb = p.export("calls"), p.export("backbone")
+    off = np.concatenate([[0], np.cumsum(calls[:, 4])])
+    top = np.concatenate([bb[off[i]:off[i + 1]] for i in np.nonzero(calls[:, 0] <= 1)[0]])
+    picks = [top[:per]]
+    recs = p.export("records")
+    picks.append(recs[np.argsort(-recs[:, 2], kind="stable")[:per], 1])
+    del recs
+    leaves = p.export("leaves")
+    picks.append(leaves[np.argsort(-leaves[:, 2], kind="stable")[:per], 1])
+    jobs = p.export("jobs")
+    classes = np.unique(jobs[jobs[:, 0] == 0, 1])
+    for lnp in classes:
+        sel = jobs[(jobs[:, 0] == 0) & (jobs[:, 1] == lnp)]
+        sel = sel[rng.permutation(len(sel))[:16]]
+        picks += [sel[:, 4], sel[:, 5]]
+    sel = jobs[jobs[:, 0] == 1]
+    sel = sel[rng.permutation(len(sel))[:32]]
+    picks += [sel[:, 4], sel[:, 5]]
+    picks.append(rng.choice(n, n_random, replace=False))
+    t = np.unique(np.concatenate(picks))
+    return t[t >= 0].astype(np.int32), len(classes)
+
+
+def _full_size_case(shape, n, leaf_max, per, n_random, min_targets):
+    # a full-size tree at the benchmark's leaf cutoff, checked on stratified outputs the oracle
+    # computes one by one
+    cfg = W.configs.sweep(shape=shape, n=n, d=16, kernel="exp")
+    t = cfg["tree"]
+    F = W.normal_field(t.n, 16, seed=123)
+    p = tfi.Plan.from_spec(t, cfg["delta"], cfg["kernel"], leaf_max=leaf_max, max_channels=16)
+    targets, n_classes = _stratified_targets(p, t.n, seed=1, per=per, n_random=n_random)
+    assert len(targets) >= min_targets
+    x = torch.from_numpy(F).cuda()
+    y = p.apply(x).cpu().numpy()[targets]
+    gF = p.apply_backward(x).cpu().numpy()[targets]
+    ref = brute.integrate(t, cfg["delta"], cfg["kernel"], F.astype(np.float64), targets=targets)
+    assert _err(y, ref) <= TOL["f32"]
+    assert _err(gF, ref) <= TOL["f32"]
+    return p, n_classes
+
+
+def test_full_size_stratified_rrt_2p20_bench_config():
+    # the benchmarked configuration itself: N = 2^20, s0 = 512 (packed big leaves, FFT classes)
+    p, n_classes = _full_size_case("rrt", 1 << 20, 512, per=128, n_random=256, min_targets=512)
+    assert n_classes >= 2 and p.info()["n_jobs_direct"] > 0
+
+
+@pytest.mark.parametrize("shape", ["binary", "caterpillar"])
+def test_full_size_stratified_other_shapes_2p18(shape):
+    _full_size_case(shape, 1 << 18, 512, per=48, n_random=96, min_targets=200)
+
+
+def test_full_size_sampled_rrt_2p20_small_leaves():
     cfg = W.configs.sweep(shape="rrt", n=1 << 20, d=16, kernel="exp")
     F = W.normal_field(cfg["tree"].n, 16, seed=123)
     rng = np.random.default_rng(0)
