@@ -111,6 +111,10 @@ typedef struct {
                                    when their cost, J (6 per bin + 4 per backbone run) per channel,
                                    is below that of the evaluator the cost model picked otherwise;
                                    ignored for other kernels */
+#define TFI_PLAN_FFT_BIG_ALL 64 /* every table beyond one CTA's shared memory (P1 P2 > 2^14 grid points;
+                                   up to 2^25 points with a backbone axis of at most 2^13) is evaluated
+                                   by the four-step FFT through global memory, whatever the cost model
+                                   prefers (by default it competes with direct summation) */
 #define TFI_PLAN_LEAF_ALU   16  /* dense leaves on the FP32 ALUs for every d (by default BF16 applies
                                    with d >= 64 sum leaves as f(D) x F products on the tensor cores:
                                    tcgen05 kind::tf32, f(D) split into hi + lo; FP32 applies always
@@ -287,6 +291,9 @@ typedef struct {
     int64_t n_jobs_hankel;  /* tables evaluated by the Hankel-matrix product (TFI_PLAN_HANKEL) */
     int64_t device_errors;  /* bounded device waits that gave up since the plan was built (0 when healthy;
                                reading it synchronises the device) */
+    int64_t n_jobs_fft_big; /* tables beyond one CTA's shared memory evaluated by the four-step FFT through
+                               global memory (P1 P2 > 2^14 points) */
+    int64_t sum_fft_big_points; /* sum over those tables of P1*P2 */
 } tfi_plan_info;
 tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
 
@@ -313,8 +320,9 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
  *   TFI_EXPORT_GATHER_ORDER the n vertices in the order the output gather takes them: a
  *                       depth-first preorder of the forest, tree by tree. Launch layout only.
  *   TFI_EXPORT_JOBS     7 per table job (a call's cross table or a component's correction), in plan
- *                       order: evaluator (0 FFT, 1 direct, 2 exponential sweep, 3 Hankel product),
- *                       log2 of the FFT points (-1 unless FFT), 1 for a correction, occupied bins,
+ *                       order: evaluator (0 FFT in shared memory, 1 direct, 2 exponential sweep,
+ *                       3 Hankel product, 4 four-step FFT through global memory), log2 of the
+ *                       FFT points (-1 unless an FFT), 1 for a correction, occupied bins,
  *                       the first member vertex of its first bin and the last member of its last
  *                       bin (-1 for a job without bins), and its largest depth (grid units).
  *                       Vertices named here read this job's table in the gather.

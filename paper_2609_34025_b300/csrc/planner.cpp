@@ -4,6 +4,7 @@
 #include "hankel_layout.hpp"
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -59,30 +60,20 @@ int ceil_log2(int64_t v) {
 }
 
 uint32_t bitrev(uint32_t k, int bits) {
-    uint32_t r = 0;
-    for (int i = 0; i < bits; ++i) r |= ((k >> i) & 1u) << (bits - 1 - i);
-    return r;
-}
-
-// Forward complex DFT in place (radix-2, natural order in and out), FP64.
-void fft64(std::complex<double> *a, int lg, int64_t stride) {
-    const int64_t n = int64_t(1) << lg;
-    for (int64_t i = 0; i < n; ++i) {
-        int64_t j = bitrev(uint32_t(i), lg);
-        if (i < j) std::swap(a[i * stride], a[j * stride]);
-    }
-    for (int64_t len = 2; len <= n; len <<= 1) {
-        const double ang = -2.0 * M_PI / double(len);
-        for (int64_t i = 0; i < n; i += len) {
-            for (int64_t k = 0; k < len / 2; ++k) {
-                std::complex<double> w(std::cos(ang * double(k)), std::sin(ang * double(k)));
-                std::complex<double> x = a[(i + k) * stride];
-                std::complex<double> y = a[(i + k + len / 2) * stride] * w;
-                a[(i + k) * stride] = x + y;
-                a[(i + k + len / 2) * stride] = x - y;
-            }
+    // byte-wise through a 256-entry table, then shifted down to `bits` bits
+    static const auto tab = [] {
+        std::array<uint8_t, 256> t{};
+        for (int b = 0; b < 256; ++b) {
+            uint8_t r = 0;
+            for (int i = 0; i < 8; ++i) r = uint8_t(r | (((b >> i) & 1) << (7 - i)));
+            t[size_t(b)] = r;
         }
-    }
+        return t;
+    }();
+    if (bits == 0) return 0;
+    const uint32_t r = (uint32_t(tab[k & 255]) << 24) | (uint32_t(tab[(k >> 8) & 255]) << 16) |
+                       (uint32_t(tab[(k >> 16) & 255]) << 8) | uint32_t(tab[(k >> 24) & 255]);
+    return r >> (32 - bits);
 }
 
 // Run fn(i) for i in [0, n) on all hardware threads (dynamic scheduling).
@@ -102,6 +93,80 @@ void parallel_for(size_t n, Fn fn) {
     for (size_t t = 1; t < nth; ++t) pool.emplace_back(worker);
     if (n) worker();
     for (std::thread &th : pool) th.join();
+}
+
+// Forward DFT in place of 2^lg contiguous points (natural order in and out), FP64,
+// radix-2 with a table of the 2^(lg-1) roots exp(-2 pi i k / 2^lg) (w).
+void fft64_tab(std::complex<double> *a, int lg, const std::complex<double> *w) {
+    const int64_t n = int64_t(1) << lg;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t j = bitrev(uint32_t(i), lg);
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (int ll = 1; ll <= lg; ++ll) {
+        const int64_t len = int64_t(1) << ll, half = len >> 1, step = n >> ll;
+        for (int64_t i = 0; i < n; i += len) {
+            for (int64_t k = 0; k < half; ++k) {
+                const std::complex<double> x = a[i + k], y = a[i + k + half] * w[k * step];
+                a[i + k] = x + y;
+                a[i + k + half] = x - y;
+            }
+        }
+    }
+}
+
+std::vector<std::complex<double>> roots64(int lg) {
+    const int64_t n = int64_t(1) << lg;
+    std::vector<std::complex<double>> w(size_t(std::max<int64_t>(1, n / 2)));
+    for (int64_t k = 0; k < n / 2; ++k) {
+        const double ang = -2.0 * M_PI * double(k) / double(n);
+        w[size_t(k)] = std::complex<double>(std::cos(ang), std::sin(ang));
+    }
+    return w;
+}
+
+// Forward DFT of 2^lg points spaced `stride` apart (natural order in and out), FP64.
+// Up to 2^14 points directly; longer ones by the four-step split n = n1 n2 (DFTs of
+// length n1 over strided columns, twiddles w_n^{j2 k1}, DFTs of length n2 over
+// rows, then X[k1 + n1 k2] from row k1), with the columns and rows on all host
+// threads when `par` is set.
+void fft64_any(std::complex<double> *a, int lg, int64_t stride, bool par) {
+    const int64_t n = int64_t(1) << lg;
+    std::vector<std::complex<double>> t(static_cast<size_t>(n));
+    for (int64_t i = 0; i < n; ++i) t[size_t(i)] = a[i * stride];
+    if (lg <= 14) {
+        const std::vector<std::complex<double>> w = roots64(lg);
+        fft64_tab(t.data(), lg, w.data());
+    } else {
+        const int l1 = lg / 2, l2 = lg - l1;
+        const int64_t n1 = int64_t(1) << l1, n2 = int64_t(1) << l2;
+        const std::vector<std::complex<double>> w1 = roots64(l1), w2 = roots64(l2);
+        // t[j1 n2 + j2]: columns j2 (length n1, stride n2)
+        auto cols = [&](size_t j2) {
+            std::vector<std::complex<double>> c(static_cast<size_t>(n1));
+            for (int64_t j1 = 0; j1 < n1; ++j1) c[size_t(j1)] = t[size_t(j1 * n2 + int64_t(j2))];
+            fft64_tab(c.data(), l1, w1.data());
+            for (int64_t k1 = 0; k1 < n1; ++k1) {
+                const double ang = -2.0 * M_PI * double(int64_t(j2) * k1) / double(n);  // w_n^{j2 k1}
+                t[size_t(k1 * n2 + int64_t(j2))] = c[size_t(k1)] * std::complex<double>(std::cos(ang), std::sin(ang));
+            }
+        };
+        auto rows = [&](size_t k1) { fft64_tab(t.data() + int64_t(k1) * n2, l2, w2.data()); };
+        if (par) {
+            parallel_for(size_t(n2), cols);
+            parallel_for(size_t(n1), rows);
+        } else {
+            for (int64_t j2 = 0; j2 < n2; ++j2) cols(size_t(j2));
+            for (int64_t k1 = 0; k1 < n1; ++k1) rows(size_t(k1));
+        }
+        auto put = [&](size_t k2) {
+            for (int64_t k1 = 0; k1 < n1; ++k1) a[(k1 + n1 * int64_t(k2)) * stride] = t[size_t(k1 * n2 + int64_t(k2))];
+        };
+        if (par) parallel_for(size_t(n2), put);
+        else for (int64_t k2 = 0; k2 < n2; ++k2) put(size_t(k2));
+        return;
+    }
+    for (int64_t i = 0; i < n; ++i) a[i * stride] = t[size_t(i)];
 }
 
 // The recursion of Algorithm 5, level by level: every call of a level is
@@ -467,6 +532,9 @@ private:
 // two channels per complex transform) plus the key scatter and read-back.
 constexpr double kFftCostPerPointLog = 3.0;
 constexpr double kFftCostPerKey = 4.0;
+// four-step FFT through global memory: about 22 bytes of DRAM traffic per point and
+// channel, against 2 flops per pair and channel for direct summation
+constexpr double kBigCostPerPoint = 50.0;
 // Hankel evaluator, per occupied backbone column and channel: the split-TF32
 // product (NP x KT per channel), the operand staging (KT loads) and two
 // prefix-sum updates per row; a CTA always covers 128 channels, so fewer
@@ -564,29 +632,66 @@ int sample_kernel(HostPlan &hp, std::string &err) {
     hp.ftab.resize(size_t(hp.ftab_len));
     for (int64_t k = 0; k < hp.ftab_len; ++k) hp.ftab[size_t(k)] = float(hp.f.grid(k, hp.delta));
     std::vector<std::complex<double>> buf;
-    for (int cls = 0; cls < 16 * 16; ++cls) {
-        const int32_t off = hp.spec_class_off[size_t(cls)];
+    for (int cls = 0; cls < kSpecClasses; ++cls) {
+        const int64_t off = hp.spec_class_off[size_t(cls)];
         if (off < 0) continue;
-        const int lp1 = cls / 16, lp2 = cls % 16;
+        const int lp1 = cls / 32, lp2 = cls % 32;
         const int64_t P1 = int64_t(1) << lp1, P2 = int64_t(1) << lp2, NP = P1 * P2;
+        const bool big = lp1 + lp2 > kFftMaxLog;
         buf.assign(size_t(NP), 0.0);
-        for (int64_t a = 0; a < P1; ++a) {
+        auto fill_row = [&](size_t a) {
             for (int64_t b = 0; b < P2; ++b) {
-                double fv = hp.f.grid(a + std::min(b, P2 - b), hp.delta);
+                double fv = hp.f.grid(int64_t(a) + std::min(b, P2 - b), hp.delta);
                 if (!std::isfinite(fv)) fv = 0.0;  // beyond a sampled table: never read for occupied bins
-                buf[size_t(a * P2 + b)] = fv;
+                buf[size_t(int64_t(a) * P2 + b)] = fv;
             }
+        };
+        auto fft_row = [&](size_t a) { fft64_any(buf.data() + int64_t(a) * P2, lp2, 1, false); };
+        auto fft_col = [&](size_t b) { fft64_any(buf.data() + int64_t(b), lp1, P2, big && P2 == 1); };
+        if (big) {
+            // rows in chunks of at least 2^12 points per task
+            const int64_t rows_per = std::max<int64_t>(1, (int64_t(1) << 12) / P2);
+            parallel_for(size_t((P1 + rows_per - 1) / rows_per), [&](size_t c) {
+                for (int64_t a = int64_t(c) * rows_per; a < std::min(P1, int64_t(c + 1) * rows_per); ++a) fill_row(size_t(a));
+            });
+            if (lp2 > 0) parallel_for(size_t(P1), fft_row);
+            if (P2 > 1) parallel_for(size_t(P2), fft_col);
+            else fft_col(0);
+        } else {
+            for (int64_t a = 0; a < P1; ++a) fill_row(size_t(a));
+            for (int64_t a = 0; a < P1; ++a) fft_row(size_t(a));
+            for (int64_t b = 0; b < P2; ++b) fft_col(size_t(b));
         }
-        for (int64_t a = 0; a < P1; ++a) fft64(buf.data() + a * P2, lp2, 1);
-        for (int64_t b = 0; b < P2; ++b) fft64(buf.data() + b, lp1, P2);
         const double scale = 1.0 / double(NP);
-        for (int64_t a = 0; a < P1; ++a) {
-            for (int64_t b = 0; b < P2; ++b) {
-                const std::complex<double> sv =
-                    buf[size_t(int64_t(bitrev(uint32_t(a), lp1)) * P2 + int64_t(bitrev(uint32_t(b), lp2)))] * scale;
-                hp.spectra[size_t(off) + size_t(2 * (a * P2 + b))] = float(sv.real());
-                hp.spectra[size_t(off) + size_t(2 * (a * P2 + b) + 1)] = float(sv.imag());
+        float *dst = hp.spectra.data() + off;
+        if (!big) {
+            // slot (a, b) holds frequency (brev a, brev b): the order the shared-memory FFT leaves
+            for (int64_t a = 0; a < P1; ++a) {
+                for (int64_t b = 0; b < P2; ++b) {
+                    const std::complex<double> sv =
+                        buf[size_t(int64_t(bitrev(uint32_t(a), lp1)) * P2 + int64_t(bitrev(uint32_t(b), lp2)))] * scale;
+                    dst[2 * (a * P2 + b)] = float(sv.real());
+                    dst[2 * (a * P2 + b) + 1] = float(sv.imag());
+                }
             }
+        } else {
+            // four-step order: slot s BLK + sb P2 + sc (column-FFT slot s, block slots sb, sc) holds
+            // outer frequency brev(s) + N1a brev(sb) and inner frequency brev(sc)
+            const BigSplit sp = big_split(lp1, lp2);
+            const int64_t NA = int64_t(1) << sp.lnA, NB = int64_t(1) << sp.lp1b, BLK = NB * P2;
+            parallel_for(size_t(NA), [&](size_t si) {
+                const int64_t s = int64_t(si);
+                const int64_t ka = bitrev(uint32_t(s), sp.lnA);
+                for (int64_t sb = 0; sb < NB; ++sb) {
+                    const int64_t k1 = ka + NA * int64_t(bitrev(uint32_t(sb), sp.lp1b));
+                    for (int64_t sc = 0; sc < P2; ++sc) {
+                        const std::complex<double> sv = buf[size_t(k1 * P2 + int64_t(bitrev(uint32_t(sc), lp2)))] * scale;
+                        const int64_t pos = s * BLK + sb * P2 + sc;
+                        dst[2 * pos] = float(sv.real());
+                        dst[2 * pos + 1] = float(sv.imag());
+                    }
+                }
+            });
         }
     }
     hp.sw_coef.clear();
@@ -663,6 +768,15 @@ int flatten(HostPlan &hp, const std::vector<int32_t> &roots, std::string &err) {
             const bool fft_ok = lg <= kFftMaxLog;
             jb.mode = (fft_ok && cost_fft < nk * nk) ? 0 : 1;
             double best = jb.mode == 0 ? cost_fft : nk * nk;
+            // tables beyond shared memory: the four-step FFT through global memory, which also
+            // pays for its passes over the whole padded table in DRAM
+            if (!fft_ok && lg <= kBigMaxLog && jb.lp2 <= kBigMaxInnerLog && jb.lp1 >= 1) {
+                const double cost_big = kFftCostPerPointLog * np * lg + kBigCostPerPoint * np + kFftCostPerKey * nk;
+                if (cost_big < best || (hp.flags & TFI_PLAN_FFT_BIG_ALL)) {
+                    jb.mode = 4;
+                    best = cost_big;
+                }
+            }
             // occupied backbone columns (runs of equal coordinate)
             int64_t ncols = 0;
             if ((hp.flags & (TFI_PLAN_HANKEL | TFI_PLAN_HANKEL_ALL | TFI_PLAN_SWEEP_AUTO))) {
@@ -834,14 +948,14 @@ int flatten(HostPlan &hp, const std::vector<int32_t> &roots, std::string &err) {
     hp.leaf_ftab_len = need_leaf + 1;
     hp.hist_len = std::max(need_any, need_leaf) + 1;
     // FFT size classes in first-use order; their spectra depend on f
-    hp.spec_class_off.assign(16 * 16, -1);
-    int32_t off = 0;
+    hp.spec_class_off.assign(kSpecClasses, -1);
+    int64_t off = 0;
     for (const Job &j : hp.jobs) {
-        if (j.mode != 0) continue;
-        const int cls = j.lp1 * 16 + j.lp2;
+        if (j.mode != 0 && j.mode != 4) continue;
+        const int cls = j.lp1 * 32 + j.lp2;
         if (hp.spec_class_off[size_t(cls)] >= 0) continue;
         hp.spec_class_off[size_t(cls)] = off;
-        off += int32_t(2) << (j.lp1 + j.lp2);
+        off += int64_t(2) << (j.lp1 + j.lp2);
     }
     hp.spectra.assign(size_t(off), 0.f);
     if (int rc = sample_kernel(hp, err)) return rc;

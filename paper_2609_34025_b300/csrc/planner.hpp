@@ -59,7 +59,8 @@ struct Job {
     int32_t maxr, maxx;   // largest depth / coordinate among the keys
     int32_t lp1, lp2;     // log2 FFT sizes (depth, backbone)
     int32_t mode;         // 0 = FFT, 1 = direct, 2 = exponential sweep (inside the call's sweep job),
-                          // 3 = Hankel-matrix product on tensor cores
+                          // 3 = Hankel-matrix product on tensor cores, 4 = four-step FFT through
+                          // global memory (tables beyond one CTA's shared memory)
     int32_t is_comp;      // 1 for a correction job
 };
 
@@ -110,7 +111,7 @@ struct HostPlan {
     int64_t hist_len = 0;                                  // 1 + largest grid distance any pair of a call can have
     std::vector<float> ftab;
     // FFT spectra per (lp1, lp2) class, bit-reversed order, scaled by 1/(P1 P2), interleaved re/im
-    std::vector<int32_t> spec_class_off;                   // [lp1 * 16 + lp2] -> offset in floats (complex = 2)
+    std::vector<int64_t> spec_class_off;                   // [lp1 * 32 + lp2] -> offset in floats (complex = 2)
     std::vector<float> spectra;
     std::vector<float> twiddle;                            // [h + o] = exp(-2 pi i o / (8 h)), h = 2^L < 2^kTwLog
     double plan_seconds = 0;
@@ -118,6 +119,26 @@ struct HostPlan {
 
 constexpr int kTwLog = 14;            // largest in-shared-memory FFT: 2^14 complex points
 constexpr int kFftMaxLog = 14;
+constexpr int kBigMaxLog = 25;        // largest four-step FFT table: 2^25 points
+constexpr int kBigMaxInnerLog = 13;   // its backbone axis stays within one block
+constexpr int kSpecClasses = 32 * 32; // spectrum classes, indexed lp1 * 32 + lp2
+
+// Split of a four-step FFT table of 2^lp1 x 2^lp2 points (depth outer, backbone
+// inner, lp1 >= 1, lp2 <= 13, lp1 + lp2 <= 25): columns of 2^lnA points (pass A / C)
+// and blocks of 2^(lp1b + lp2) contiguous points (pass B), lnA + lp1b = lp1. The
+// two are balanced (about half the bits each) within columns of at most 2^12 and
+// blocks of at most 2^13 points.
+struct BigSplit {
+    int lnA, lp1b;
+};
+inline BigSplit big_split(int lp1, int lp2) {
+    const int lg = lp1 + lp2;
+    int lnA = lg / 2;
+    if (lnA < lg - 13) lnA = lg - 13;
+    if (lnA > 12) lnA = 12;
+    if (lnA > lp1) lnA = lp1;
+    return BigSplit{lnA, lp1 - lnA};
+}
 constexpr int kLeafMax = 1024;        // largest dense leaf (shared-memory sparse table)
 constexpr int kLeafGroup = 256;       // small leaves are packed into groups of <= this many vertices
 constexpr int64_t kGridMax = int64_t(1) << 30;

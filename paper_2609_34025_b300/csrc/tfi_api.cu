@@ -22,6 +22,7 @@
 #include "leaf_tc.cuh"
 #include "kernels.cuh"
 #include "fft_x2.cuh"
+#include "fft_big.cuh"
 #include "planner.hpp"
 #include "tfi.h"
 
@@ -54,7 +55,18 @@ struct WorkLists {
     tfi::tc::HankelItem *d_hk = nullptr;
     int n_hk = 0;
     size_t hk_smem = 0;
+    // four-step FFT tables: one item per (table, channel pair); batches that fit the plan's
+    // buffer, each a run of size-class segments [i0, i1) of d_big
+    struct BigSeg {
+        tfi::dev::BigGeom g;
+        int64_t i0, i1, max_nk;
+    };
+    tfi::dev::BigItem *d_big = nullptr;
+    std::vector<std::vector<BigSeg>> big_batches;
+    int64_t big_elems = 0;  // buffer elements (complex) the largest batch needs
 };
+
+constexpr int64_t kBigBatchBytes = int64_t(4) << 30;  // four-step FFT buffer of a plan, at most
 
 }  // namespace
 
@@ -84,6 +96,11 @@ struct tfi_plan_s {
     float2 *spectra = nullptr, *twiddle = nullptr;
     float4 *twiddle_b = nullptr;  // the twiddles, each value as (re, re, im, im)
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
+    // four-step FFT tables: the buffer of one batch (grown on demand by build_work) and the two
+    // twiddle tables exp(-2 pi i j / 2^13), exp(-2 pi i j / 2^26), j < 2^13
+    float2 *big_buf = nullptr, *big_tw_hi = nullptr, *big_tw_lo = nullptr;
+    int64_t big_cap = 0;
+    int32_t n_big_jobs = 0;
     // bin sums by segments of at most kBucketSeg members (see bucket_seg_kernel)
     int32_t *seg_ptr = nullptr, *seg_dst = nullptr, *mb_key = nullptr, *mb_ptr = nullptr;
     int64_t n_segs = 0, n_multi = 0;
@@ -188,7 +205,9 @@ struct tfi_plan_s {
             cudaFree(kv.second.d_fft);
             cudaFree(kv.second.d_dir);
             cudaFree(kv.second.d_hk);
+            cudaFree(kv.second.d_big);
         }
+        cudaFree(big_buf);
         for (void *p : allocs) cudaFree(p);
     }
 };
@@ -218,7 +237,7 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
     const auto &jobs = p->hp.jobs;
     for (size_t j = 0; j < jobs.size(); ++j) {
         const tfi::Job &jb = jobs[j];
-        if (jb.ke == jb.kb || jb.mode == 2) continue;
+        if (jb.ke == jb.kb || jb.mode == 2 || jb.mode == 4) continue;
         if (jb.mode == 3) {
             const tfi::HankelLayout lay = tfi::hankel_layout(jb.maxr, jb.maxx);
             wl.hk_smem = std::max(wl.hk_smem, size_t(lay.bytes));
@@ -260,9 +279,108 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
         TFI_CUDA(cudaMalloc(&wl.d_hk, hk.size() * sizeof(hk[0])));
         TFI_CUDA(cudaMemcpy(wl.d_hk, hk.data(), hk.size() * sizeof(hk[0]), cudaMemcpyHostToDevice));
     }
+    {
+        // four-step FFT tables by size class, one item per channel pair, in batches whose arrays fit
+        // kBigBatchBytes (and 65535 items: the grid rows of the scatter / gather launches)
+        std::map<int, std::vector<int32_t>> big_cls;
+        for (size_t j = 0; j < jobs.size(); ++j)
+            if (jobs[j].mode == 4 && jobs[j].ke > jobs[j].kb) big_cls[jobs[j].lp1 * 32 + jobs[j].lp2].push_back(int32_t(j));
+        std::vector<tfi::dev::BigItem> items;
+        std::vector<WorkLists::BigSeg> cur;
+        int64_t used = 0, first = 0;
+        const int64_t cap = kBigBatchBytes / int64_t(sizeof(float2));
+        for (auto &kv : big_cls) {
+            const int lp1 = kv.first / 32, lp2 = kv.first % 32;
+            const tfi::BigSplit sp = tfi::big_split(lp1, lp2);
+            const tfi::dev::BigGeom g{lp1, lp2, sp.lnA, sp.lp1b};
+            const int64_t P = int64_t(1) << (lp1 + lp2);
+            const int64_t spec = p->hp.spec_class_off[size_t(kv.first)] / 2;
+            for (int32_t j : kv.second) {
+                const tfi::Job &jb = jobs[size_t(j)];
+                for (int pr = 0; pr < pairs; ++pr) {
+                    if (!cur.empty() && (used + P > cap || int64_t(items.size()) - first >= 65535)) {
+                        wl.big_batches.push_back(cur);
+                        cur.clear();
+                        used = 0;
+                    }
+                    if (cur.empty()) first = int64_t(items.size());
+                    if (cur.empty() || cur.back().g.lp1 != lp1 || cur.back().g.lp2 != lp2)
+                        cur.push_back(WorkLists::BigSeg{g, int64_t(items.size()), int64_t(items.size()), 0});
+                    items.push_back(tfi::dev::BigItem{used, spec, int32_t(jb.kb), int32_t(jb.ke), pr, jb.maxr});
+                    used += P;
+                    cur.back().i1 = int64_t(items.size());
+                    cur.back().max_nk = std::max<int64_t>(cur.back().max_nk, jb.ke - jb.kb);
+                    wl.big_elems = std::max(wl.big_elems, used);
+                }
+            }
+        }
+        if (!cur.empty()) wl.big_batches.push_back(cur);
+        if (!items.empty()) {
+            TFI_CUDA(cudaMalloc(&wl.d_big, items.size() * sizeof(items[0])));
+            TFI_CUDA(cudaMemcpy(wl.d_big, items.data(), items.size() * sizeof(items[0]), cudaMemcpyHostToDevice));
+        }
+        if (wl.big_elems > p->big_cap) {
+            // grow the plan's buffer (stream-ordered work on the old one has to finish first)
+            TFI_CUDA(cudaDeviceSynchronize());
+            cudaFree(p->big_buf);
+            p->dev_bytes -= p->big_cap * int64_t(sizeof(float2));
+            p->big_buf = nullptr;
+            p->big_cap = 0;
+            if (cudaMalloc(&p->big_buf, size_t(wl.big_elems) * sizeof(float2)) != cudaSuccess) {
+                cudaFree(wl.d_big);
+                return fail(TFI_ERR_OOM, "cudaMalloc failed for the four-step FFT buffer");
+            }
+            p->big_cap = wl.big_elems;
+            p->dev_bytes += p->big_cap * int64_t(sizeof(float2));
+        }
+    }
     auto res = p->work.emplace(d, wl);
     *out = &res.first->second;
     return TFI_OK;
+}
+
+// (a4, a5) tables beyond shared memory: per batch and size class, zero the rows pass A reads,
+// scatter the bin sums, the three passes of the four-step correlation, read the bins back
+void launch_big(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
+    for (const auto &batch : wl.big_batches) {
+        for (const WorkLists::BigSeg &sg : batch) {
+            const tfi::dev::BigGeom g = sg.g;
+            const unsigned n_it = unsigned(sg.i1 - sg.i0);
+            const tfi::dev::BigItem *it = wl.d_big + sg.i0;
+            const int64_t BLK = int64_t(1) << (g.lp1b + g.lp2), NA = int64_t(1) << g.lnA;
+            const int64_t P = BLK * NA;
+            const unsigned gz = unsigned(std::min<int64_t>(256, std::max<int64_t>(1, (P / 4 + BLK / 2 + 255) / 256)));
+            const unsigned gs = unsigned(std::min<int64_t>(64, std::max<int64_t>(1, (sg.max_nk + 255) / 256)));
+            tfi::dev::big_zero<<<dim3(gz, n_it), 256, 0, s>>>(it, g, p->big_buf);
+            tfi::dev::big_scatter<<<dim3(gs, n_it), 256, 0, s>>>(it, g, p->key_r, p->key_x, d, p->kbuf, p->big_buf);
+            if (g.lnA <= 11) {
+                constexpr int CG = 4;
+                const size_t smem = size_t(tfi::dev::padded_size(int(NA) * CG)) * sizeof(float2);
+                tfi::dev::big_columns<false, CG><<<unsigned(n_it * (BLK / CG)), 256, smem, s>>>(
+                    it, g, p->big_buf, p->twiddle, p->big_tw_hi, p->big_tw_lo);
+                tfi::dev::big_blocks<<<unsigned(n_it * NA), 256, size_t(tfi::dev::padded_size(int(BLK))) * sizeof(float2), s>>>(
+                    it, g, p->big_buf, p->spectra, p->twiddle, p->big_tw_hi, p->big_tw_lo);
+                tfi::dev::big_columns<true, CG><<<unsigned(n_it * (BLK / CG)), 256, smem, s>>>(
+                    it, g, p->big_buf, p->twiddle, p->big_tw_hi, p->big_tw_lo);
+            } else {
+                constexpr int CG = 2;
+                const size_t smem = size_t(tfi::dev::padded_size(int(NA) * CG)) * sizeof(float2);
+                tfi::dev::big_columns<false, CG><<<unsigned(n_it * (BLK / CG)), 256, smem, s>>>(
+                    it, g, p->big_buf, p->twiddle, p->big_tw_hi, p->big_tw_lo);
+                tfi::dev::big_blocks<<<unsigned(n_it * NA), 256, size_t(tfi::dev::padded_size(int(BLK))) * sizeof(float2), s>>>(
+                    it, g, p->big_buf, p->spectra, p->twiddle, p->big_tw_hi, p->big_tw_lo);
+                tfi::dev::big_columns<true, CG><<<unsigned(n_it * (BLK / CG)), 256, smem, s>>>(
+                    it, g, p->big_buf, p->twiddle, p->big_tw_hi, p->big_tw_lo);
+            }
+            tfi::dev::big_gather<<<dim3(gs, n_it), 256, 0, s>>>(it, g, p->key_r, p->key_x, d, p->big_buf, p->vbuf);
+        }
+    }
+}
+
+int big_launches(const WorkLists &wl) {
+    int n = 0;
+    for (const auto &b : wl.big_batches) n += 6 * int(b.size());
+    return n;
 }
 
 constexpr int32_t kBucketSeg = 32;  // members per bin-sum segment
@@ -457,6 +575,11 @@ tfi_status set_attributes() {
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_x2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
     TFI_CUDA(cudaFuncSetAttribute(tfi::tc::hankel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_columns<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_columns<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_columns<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_columns<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
 #define LEAF_TC_ATTR(T, NB)                                                                                 \
     TFI_CUDA(cudaFuncSetAttribute(tfi::tc::leaf_tc_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   227 * 1024));
@@ -596,7 +719,8 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
                     p->twiddle);
             }
         }
-        m_fft.done(int(wl->fft_lnp.size()));
+        launch_big(p, *wl, d, s_crit);
+        m_fft.done(int(wl->fft_lnp.size()) + big_launches(*wl));
         TFI_CUDA(cudaEventRecord(p->ev_crit, s_crit));
         TFI_CUDA(cudaStreamWaitEvent(s, p->ev_crit, 0));
         TFI_CUDA(cudaStreamWaitEvent(s, p->ev_dir, 0));
@@ -766,7 +890,7 @@ tfi_status upload_plan(tfi_plan_t p) {
         jd[j].ke = int32_t(jb.ke);
         jd[j].lp1 = jb.lp1;
         jd[j].lp2 = jb.lp2;
-        jd[j].spec_off = jb.mode == 0 ? hp.spec_class_off[size_t(jb.lp1 * 16 + jb.lp2)] / 2 : 0;
+        jd[j].spec_off = jb.mode == 0 ? int32_t(hp.spec_class_off[size_t(jb.lp1 * 32 + jb.lp2)] / 2) : 0;
         jd[j].pad = 0;
     }
     if (tfi_status rc = p->upload(&p->jobs, jd)) return rc;
@@ -775,7 +899,7 @@ tfi_status upload_plan(tfi_plan_t p) {
         std::map<int, std::vector<int32_t>> by_class;
         for (size_t j = 0; j < hp.jobs.size(); ++j) {
             const tfi::Job &jb = hp.jobs[j];
-            if (jb.ke == jb.kb || jb.mode == 2 || jb.mode == 3) continue;
+            if (jb.ke == jb.kb || jb.mode == 2 || jb.mode == 3 || jb.mode == 4) continue;
             if (jb.mode == 0) {
                 by_class[jb.lp1 + jb.lp2].push_back(int32_t(j));
             } else {
@@ -795,6 +919,18 @@ tfi_status upload_plan(tfi_plan_t p) {
     }
     p->n_hankel = 0;
     for (const tfi::Job &jb : hp.jobs) p->n_hankel += jb.mode == 3;
+    p->n_big_jobs = 0;
+    for (const tfi::Job &jb : hp.jobs) p->n_big_jobs += jb.mode == 4;
+    if (p->n_big_jobs > 0) {
+        std::vector<float2> hi(8192), lo(8192);
+        for (int j = 0; j < 8192; ++j) {
+            const double a = -2.0 * M_PI * double(j) / 8192.0, b = -2.0 * M_PI * double(j) / double(1 << 26);
+            hi[size_t(j)] = make_float2(float(std::cos(a)), float(std::sin(a)));
+            lo[size_t(j)] = make_float2(float(std::cos(b)), float(std::sin(b)));
+        }
+        if (tfi_status rc = p->upload(&p->big_tw_hi, hi)) return rc;
+        if (tfi_status rc = p->upload(&p->big_tw_lo, lo)) return rc;
+    }
     {
         void *q = nullptr;
         if (tfi_status rc = p->alloc(&q, 16)) return rc;
@@ -980,6 +1116,8 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
     if (p->n_sweeps > 0 || p->n_sw_ejobs > 0)
         return fail(TFI_ERR_UNSUPPORTED, "tfi_apply_static does not run exponential-sweep plans");
     if (p->n_hankel > 0) return fail(TFI_ERR_UNSUPPORTED, "tfi_apply_static does not run Hankel-evaluator plans");
+    if (p->n_big_jobs > 0)
+        return fail(TFI_ERR_UNSUPPORTED, "tfi_apply_static does not run plans with four-step FFT tables");
     if (tfi_status rc = set_attributes()) return rc;
     // FFT items for this d: per size class, one item per (job, block of np channel pairs),
     // written into the static array by expand_fft_items (no host-sourced copy)
@@ -1651,6 +1789,9 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info) {
         if (j.mode == 0) {
             info->n_jobs_fft++;
             info->sum_fft_points += int64_t(1) << (j.lp1 + j.lp2);
+        } else if (j.mode == 4) {
+            info->n_jobs_fft_big++;
+            info->sum_fft_big_points += int64_t(1) << (j.lp1 + j.lp2);
         } else if (j.mode == 1) {
             info->n_jobs_direct++;
         } else if (j.mode == 3) {
@@ -1731,12 +1872,15 @@ tfi_status tfi_stage_model(tfi_plan_t plan, int32_t d, int32_t dtype, double *by
             for (uint8_t b : seen) ncols += b;
             flops[TFI_STAGE_HANKEL] += 2.0 * double(j.maxr + j.maxx + 1) * double(j.maxr + 1) * ncols * D;
             bytes[TFI_STAGE_HANKEL] += nk * ((j.maxx > 0 ? 4 : 2) * D * 4 + 8);
-        } else if (j.mode == 0) {
+        } else if (j.mode == 0 || j.mode == 4) {
             const double np = std::ldexp(1.0, j.lp1 + j.lp2);
             const double lg = double(j.lp1 + j.lp2);
             kf += nk;
             // two complex transforms and one complex product per channel pair
             flops[TFI_STAGE_FFT] += std::ceil(D / 2) * (2 * 5 * np * lg + 6 * np);
+            // four-step tables also pass over their padded arrays in DRAM, per channel pair: the
+            // zeroed and read input half, two reads and writes of the whole, the stored output half
+            if (j.mode == 4) bytes[TFI_STAGE_FFT] += std::ceil(D / 2) * 5.5 * np * 8;
         } else if (j.mode == 2) {
             // per term: lambda^r weighting in and out, two recurrences per backbone vertex
             bytes[TFI_STAGE_SWEEP] += nk * (2 * D * 4 + 8);
@@ -1746,7 +1890,7 @@ tfi_status tfi_stage_model(tfi_plan_t plan, int32_t d, int32_t dtype, double *by
             flops[TFI_STAGE_DIRECT] += 2.0 * nk * nk * D;
         }
     }
-    bytes[TFI_STAGE_FFT] = kf * (2 * D * 4 + 8);
+    bytes[TFI_STAGE_FFT] += kf * (2 * D * 4 + 8);
     bytes[TFI_STAGE_DIRECT] = kd * (2 * D * 4 + 8);
     // per record two indices; per vertex its record range and leaf flag; every table row once (the
     // rows a vertex reads are shared with the other vertices of its bin); leaf rows; output rows
@@ -1815,7 +1959,7 @@ tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t 
         case TFI_EXPORT_JOBS:
             for (const tfi::Job &j : hp.jobs) {
                 const bool any = j.ke > j.kb;
-                const int64_t row[7] = {j.mode, j.mode == 0 ? j.lp1 + j.lp2 : -1, j.is_comp, j.ke - j.kb,
+                const int64_t row[7] = {j.mode, (j.mode == 0 || j.mode == 4) ? j.lp1 + j.lp2 : -1, j.is_comp, j.ke - j.kb,
                                         any ? hp.key_vtx[size_t(hp.key_ptr[size_t(j.kb)])] : -1,
                                         any ? hp.key_vtx[size_t(hp.key_ptr[size_t(j.ke)] - 1)] : -1, j.maxr};
                 v.insert(v.end(), row, row + 7);
