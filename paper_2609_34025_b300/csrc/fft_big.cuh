@@ -101,89 +101,109 @@ __global__ void big_gather(const BigItem *__restrict__ items, BigGeom g, const i
     }
 }
 
-// Pass A (INV = false) and pass C (INV = true): CG adjacent columns per CTA, the
-// length-N1a FFT over na in shared memory (element (na, c) at na CG + c).
-template <bool INV, int CG>
-__global__ void __launch_bounds__(256) big_columns(const BigItem *__restrict__ items, BigGeom g, float2 *__restrict__ buf,
-                                                   const float2 *__restrict__ tw, const float2 *__restrict__ tw_hi,
-                                                   const float2 *__restrict__ tw_lo) {
+// Pass A (INV = false) and pass C (INV = true): 2^lcg adjacent columns per CTA, the
+// length-N1a FFT over na in shared memory (element (na, c) at na 2^lcg + c). Columns
+// per CTA are chosen so that a CTA holds about 2^13 points.
+template <bool INV>
+__global__ void __launch_bounds__(256) big_columns(const BigItem *__restrict__ items, BigGeom g, int lcg,
+                                                   float2 *__restrict__ buf, const float2 *__restrict__ tw,
+                                                   const float2 *__restrict__ tw_hi, const float2 *__restrict__ tw_lo) {
     extern __shared__ float2 Z[];
-    constexpr int LCG = CG == 4 ? 2 : CG == 2 ? 1 : 0;
+    const int CG = 1 << lcg;
     const int NA = 1 << g.lnA;
     const int64_t BLK = int64_t(1) << (g.lp1b + g.lp2);
-    const int64_t per = BLK / CG;
+    const int64_t per = BLK >> lcg;
     const BigItem it = items[blockIdx.x / per];
-    const int64_t col0 = (blockIdx.x % per) * CG;
+    const int64_t col0 = (blockIdx.x % per) << lcg;
     float2 *a = buf + it.off;
     const int64_t P1 = int64_t(1) << g.lp1;
-    const int padnp = padded_size(NA * CG);
+    const int padnp = padded_size(NA << lcg);
     if (!INV) {
         // rows that can hold a bin: na = 0 and na >= na_lo; the rest are zero
         const int na_lo = int((P1 - it.maxr) >> g.lp1b);
-        for (int e = threadIdx.x; e < NA * CG; e += blockDim.x) {
-            const int na = e >> LCG, c = e & (CG - 1);
+        for (int e = threadIdx.x; e < (NA << lcg); e += blockDim.x) {
+            const int na = e >> lcg, c = e & (CG - 1);
             Z[padded(e)] = (na == 0 || na >= na_lo) ? a[int64_t(na) * BLK + col0 + c] : make_float2(0.f, 0.f);
         }
     } else {
-        for (int e = threadIdx.x; e < NA * CG; e += blockDim.x) {
-            const int na = e >> LCG, c = e & (CG - 1);
+        for (int e = threadIdx.x; e < (NA << lcg); e += blockDim.x) {
+            const int na = e >> lcg, c = e & (CG - 1);
             Z[padded(e)] = a[int64_t(na) * BLK + col0 + c];
         }
     }
     __syncthreads();
     if (!INV) {
-        fft_axis<false>(Z, padnp, 1, g.lnA, CG, LCG, 1, true, tw, false);
+        fft_axis<false>(Z, padnp, 1, g.lnA, CG, lcg, 1, true, tw, false);
         // slot s holds frequency ka = brev(s); column (nb, x) takes w_{P1}^{nb ka}
-        for (int e = threadIdx.x; e < NA * CG; e += blockDim.x) {
-            const int s = e >> LCG, c = e & (CG - 1);
+        for (int e = threadIdx.x; e < (NA << lcg); e += blockDim.x) {
+            const int s = e >> lcg, c = e & (CG - 1);
             const int64_t nb = (col0 + c) >> g.lp2;
             const int64_t m = (nb * brev_bits(s, g.lnA)) & (P1 - 1);
             a[int64_t(s) * BLK + col0 + c] = m ? cmul(Z[padded(e)], big_twiddle(m, g.lp1, tw_hi, tw_lo)) : Z[padded(e)];
         }
     } else {
-        fft_axis<true>(Z, padnp, 1, g.lnA, CG, LCG, 1, true, tw, false);
+        fft_axis<true>(Z, padnp, 1, g.lnA, CG, lcg, 1, true, tw, false);
         // only depths q <= maxr are read back
         const int na_hi = it.maxr >> g.lp1b;
-        for (int e = threadIdx.x; e < NA * CG; e += blockDim.x) {
-            const int na = e >> LCG, c = e & (CG - 1);
+        for (int e = threadIdx.x; e < (NA << lcg); e += blockDim.x) {
+            const int na = e >> lcg, c = e & (CG - 1);
             if (na <= na_hi) a[int64_t(na) * BLK + col0 + c] = Z[padded(e)];
         }
     }
 }
 
-// Pass B: one block (one ka) per CTA: the N1b x P2 forward FFT, the product with the
+// Pass B: 2^lnb consecutive blocks (consecutive ka slots) per CTA, each in its own
+// padded shared-memory array: the N1b x P2 forward FFT, the product with that block's
 // spectrum, the inverse FFT and the factor w_{P1}^{-nb ka}.
-__global__ void __launch_bounds__(256) big_blocks(const BigItem *__restrict__ items, BigGeom g, float2 *__restrict__ buf,
-                                                  const float2 *__restrict__ spectra, const float2 *__restrict__ tw,
-                                                  const float2 *__restrict__ tw_hi, const float2 *__restrict__ tw_lo) {
+__global__ void __launch_bounds__(256) big_blocks(const BigItem *__restrict__ items, BigGeom g, int lnb,
+                                                  float2 *__restrict__ buf, const float2 *__restrict__ spectra,
+                                                  const float2 *__restrict__ tw, const float2 *__restrict__ tw_hi,
+                                                  const float2 *__restrict__ tw_lo) {
     extern __shared__ float2 Z[];
     const int lb = g.lp1b + g.lp2;
-    const int BLK = 1 << lb, P2 = 1 << g.lp2;
-    const BigItem it = items[blockIdx.x >> g.lnA];
-    const int s = int(blockIdx.x & ((1u << g.lnA) - 1));
-    float2 *a = buf + it.off + int64_t(s) * BLK;
+    const int BLK = 1 << lb, P2 = 1 << g.lp2, NBK = 1 << lnb;
+    const int per = 1 << (g.lnA - lnb);
+    const BigItem it = items[blockIdx.x / per];
+    const int s0 = int(blockIdx.x % per) << lnb;
+    float2 *a = buf + it.off + int64_t(s0) * BLK;
     const int padnp = padded_size(BLK);
-    for (int e = threadIdx.x; e < BLK; e += blockDim.x) Z[padded(e)] = a[e];
+    for (int e = threadIdx.x; e < (BLK << lnb); e += blockDim.x) Z[(e >> lb) * padnp + padded(e & (BLK - 1))] = a[e];
     __syncthreads();
-    const float2 *S = spectra + it.spec_off + int64_t(s) * BLK;
+    const float2 *S = spectra + it.spec_off + int64_t(s0) * BLK;
     if (g.lp1b > 0) {
-        fft_axis<false>(Z, padnp, 1, g.lp2, 1, g.lp1b, P2, false, tw, false);
-        fft_axis<false>(Z, padnp, 1, g.lp1b, P2, g.lp2, 1, true, tw, true);
-        fused_bottom(Z, padnp, 1, g.lp1b, P2, g.lp2, 1, true, S);
-        fft_axis<true>(Z, padnp, 1, g.lp1b, P2, g.lp2, 1, true, tw, true);
-        fft_axis<true>(Z, padnp, 1, g.lp2, 1, g.lp1b, P2, false, tw, false);
+        fft_axis<false>(Z, padnp, NBK, g.lp2, 1, g.lp1b, P2, false, tw, false);
+        fft_axis<false>(Z, padnp, NBK, g.lp1b, P2, g.lp2, 1, true, tw, true);
+        fused_bottom(Z, padnp, NBK, g.lp1b, P2, g.lp2, 1, true, S, BLK);
+        fft_axis<true>(Z, padnp, NBK, g.lp1b, P2, g.lp2, 1, true, tw, true);
+        fft_axis<true>(Z, padnp, NBK, g.lp2, 1, g.lp1b, P2, false, tw, false);
     } else {
-        fft_axis<false>(Z, padnp, 1, g.lp2, 1, 0, P2, false, tw, true);
-        fused_bottom(Z, padnp, 1, g.lp2, 1, 0, P2, false, S);
-        fft_axis<true>(Z, padnp, 1, g.lp2, 1, 0, P2, false, tw, true);
+        fft_axis<false>(Z, padnp, NBK, g.lp2, 1, 0, P2, false, tw, true);
+        fused_bottom(Z, padnp, NBK, g.lp2, 1, 0, P2, false, S, BLK);
+        fft_axis<true>(Z, padnp, NBK, g.lp2, 1, 0, P2, false, tw, true);
     }
     const int64_t P1 = int64_t(1) << g.lp1;
-    const int64_t ka = brev_bits(s, g.lnA);
-    for (int e = threadIdx.x; e < BLK; e += blockDim.x) {
-        const int64_t m = ((int64_t(e >> g.lp2)) * ka) & (P1 - 1);
-        const float2 v = Z[padded(e)];
+    for (int e = threadIdx.x; e < (BLK << lnb); e += blockDim.x) {
+        const int q = e >> lb, el = e & (BLK - 1);
+        const int64_t ka = brev_bits(s0 + q, g.lnA);
+        const int64_t m = ((int64_t(el >> g.lp2)) * ka) & (P1 - 1);
+        const float2 v = Z[q * padnp + padded(el)];
         a[e] = m ? cmulc(v, big_twiddle(m, g.lp1, tw_hi, tw_lo)) : v;
     }
+}
+
+// Columns per CTA (log2) for passes A and C, and blocks per CTA (log2) for pass B: about
+// 2^13 points per CTA.
+__host__ __device__ inline int big_lcg(BigGeom g) {
+    int l = 13 - g.lnA;
+    if (l < 1) l = 1;
+    if (l > g.lp1b + g.lp2) l = g.lp1b + g.lp2;
+    return l;
+}
+__host__ __device__ inline int big_lnb(BigGeom g) {
+    int l = 13 - (g.lp1b + g.lp2);
+    if (l < 0) l = 0;
+    if (l > g.lnA) l = g.lnA;
+    return l;
 }
 
 }  // namespace dev

@@ -387,7 +387,7 @@ __device__ __forceinline__ void fft_axis(float2 *Z, int padnp, int npair, int ln
 // by the kernel spectrum in between, all in registers (no twiddles at span 1).
 template <int RL>
 __device__ __forceinline__ void fused_bottom_pass(float2 *Z, int padnp, int npair, int ln, int es, int llog, int ls,
-                                                  bool line_fast, const float2 *__restrict__ S) {
+                                                  bool line_fast, const float2 *__restrict__ S, int s_pair) {
     constexpr int R = 1 << RL;
     const int glog = ln - RL;
     const int total = npair << (llog + glog);
@@ -414,8 +414,9 @@ __device__ __forceinline__ void fused_bottom_pass(float2 *Z, int padnp, int npai
             for (int t = 0; t < R; ++t) adr[t] = padded(e0 + t * es);
         }
         float2 sp[R], v[R];
+        const float2 *Sp = S + p * s_pair;
 #pragma unroll
-        for (int q = 0; q < R; ++q) sp[q] = __ldg(S + e0 + q * es);
+        for (int q = 0; q < R; ++q) sp[q] = __ldg(Sp + e0 + q * es);
 #pragma unroll
         for (int t = 0; t < R; ++t) v[t] = Zp[adr[t]];
         dft_dif<RL>(v);
@@ -428,13 +429,14 @@ __device__ __forceinline__ void fused_bottom_pass(float2 *Z, int padnp, int npai
     __syncthreads();
 }
 
+// s_pair: offset between the spectra of consecutive arrays (0: one spectrum for all)
 __device__ __forceinline__ void fused_bottom(float2 *Z, int padnp, int npair, int ln, int es, int llog, int ls,
-                                             bool line_fast, const float2 *__restrict__ S) {
+                                             bool line_fast, const float2 *__restrict__ S, int s_pair = 0) {
     const int full = ln / 3, rem = ln - 3 * full;
     const int rl = full > 0 ? 3 : rem;
-    if (rl == 3) fused_bottom_pass<3>(Z, padnp, npair, ln, es, llog, ls, line_fast, S);
-    else if (rl == 2) fused_bottom_pass<2>(Z, padnp, npair, ln, es, llog, ls, line_fast, S);
-    else fused_bottom_pass<1>(Z, padnp, npair, ln, es, llog, ls, line_fast, S);
+    if (rl == 3) fused_bottom_pass<3>(Z, padnp, npair, ln, es, llog, ls, line_fast, S, s_pair);
+    else if (rl == 2) fused_bottom_pass<2>(Z, padnp, npair, ln, es, llog, ls, line_fast, S, s_pair);
+    else fused_bottom_pass<1>(Z, padnp, npair, ln, es, llog, ls, line_fast, S, s_pair);
 }
 
 __global__ void fft_kernel(const FftItem *__restrict__ items, const JobDev *__restrict__ jobs,

@@ -353,25 +353,16 @@ void launch_big(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
             const unsigned gs = unsigned(std::min<int64_t>(64, std::max<int64_t>(1, (sg.max_nk + 255) / 256)));
             tfi::dev::big_zero<<<dim3(gz, n_it), 256, 0, s>>>(it, g, p->big_buf);
             tfi::dev::big_scatter<<<dim3(gs, n_it), 256, 0, s>>>(it, g, p->key_r, p->key_x, d, p->kbuf, p->big_buf);
-            if (g.lnA <= 11) {
-                constexpr int CG = 4;
-                const size_t smem = size_t(tfi::dev::padded_size(int(NA) * CG)) * sizeof(float2);
-                tfi::dev::big_columns<false, CG><<<unsigned(n_it * (BLK / CG)), 256, smem, s>>>(
-                    it, g, p->big_buf, p->twiddle, p->big_tw_hi, p->big_tw_lo);
-                tfi::dev::big_blocks<<<unsigned(n_it * NA), 256, size_t(tfi::dev::padded_size(int(BLK))) * sizeof(float2), s>>>(
-                    it, g, p->big_buf, p->spectra, p->twiddle, p->big_tw_hi, p->big_tw_lo);
-                tfi::dev::big_columns<true, CG><<<unsigned(n_it * (BLK / CG)), 256, smem, s>>>(
-                    it, g, p->big_buf, p->twiddle, p->big_tw_hi, p->big_tw_lo);
-            } else {
-                constexpr int CG = 2;
-                const size_t smem = size_t(tfi::dev::padded_size(int(NA) * CG)) * sizeof(float2);
-                tfi::dev::big_columns<false, CG><<<unsigned(n_it * (BLK / CG)), 256, smem, s>>>(
-                    it, g, p->big_buf, p->twiddle, p->big_tw_hi, p->big_tw_lo);
-                tfi::dev::big_blocks<<<unsigned(n_it * NA), 256, size_t(tfi::dev::padded_size(int(BLK))) * sizeof(float2), s>>>(
-                    it, g, p->big_buf, p->spectra, p->twiddle, p->big_tw_hi, p->big_tw_lo);
-                tfi::dev::big_columns<true, CG><<<unsigned(n_it * (BLK / CG)), 256, smem, s>>>(
-                    it, g, p->big_buf, p->twiddle, p->big_tw_hi, p->big_tw_lo);
-            }
+            const int lcg = tfi::dev::big_lcg(g), lnb = tfi::dev::big_lnb(g);
+            const size_t smem_c = size_t(tfi::dev::padded_size(int(NA) << lcg)) * sizeof(float2);
+            const size_t smem_b = (size_t(tfi::dev::padded_size(int(BLK))) << lnb) * sizeof(float2);
+            const unsigned grid_c = unsigned(n_it * (BLK >> lcg)), grid_b = unsigned(n_it * (NA >> lnb));
+            tfi::dev::big_columns<false><<<grid_c, 256, smem_c, s>>>(it, g, lcg, p->big_buf, p->twiddle, p->big_tw_hi,
+                                                                    p->big_tw_lo);
+            tfi::dev::big_blocks<<<grid_b, 256, smem_b, s>>>(it, g, lnb, p->big_buf, p->spectra, p->twiddle,
+                                                             p->big_tw_hi, p->big_tw_lo);
+            tfi::dev::big_columns<true><<<grid_c, 256, smem_c, s>>>(it, g, lcg, p->big_buf, p->twiddle, p->big_tw_hi,
+                                                                   p->big_tw_lo);
             tfi::dev::big_gather<<<dim3(gs, n_it), 256, 0, s>>>(it, g, p->key_r, p->key_x, d, p->big_buf, p->vbuf);
         }
     }
@@ -576,10 +567,8 @@ tfi_status set_attributes() {
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::fft_x2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
     TFI_CUDA(cudaFuncSetAttribute(tfi::tc::hankel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
-    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_columns<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
-    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_columns<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
-    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_columns<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
-    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_columns<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_columns<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
+    TFI_CUDA(cudaFuncSetAttribute(tfi::dev::big_columns<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024));
 #define LEAF_TC_ATTR(T, NB)                                                                                 \
     TFI_CUDA(cudaFuncSetAttribute(tfi::tc::leaf_tc_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   227 * 1024));
