@@ -239,8 +239,10 @@ tfi_status tfi_sinkhorn(tfi_plan_t plan, const float *a, const float *b, float *
  *   entries, or NULL (a TFI_F_TABLE kernel has no parameters). In device memory
  *   it is written on `stream` (no synchronisation); in host memory the call
  *   synchronises `stream` to copy it back. The first call allocates the
- *   gradient workspace. Needs every table of the plan to fit one shared-memory
- *   transform (P1 P2 <= 2^13), else TFI_ERR_UNSUPPORTED. */
+ *   gradient workspace. A table of more than 2^13 grid points is correlated
+ *   directly (pair dot products binned by distance), which takes tables of up to
+ *   8160 occupied bins; a plan with a larger table of that kind returns
+ *   TFI_ERR_UNSUPPORTED. */
 tfi_status tfi_kernel_grad(tfi_plan_t plan, const void *grad_out, const void *F, int32_t d, int32_t dtype, double *C,
                            int64_t C_len, double *dtheta, tfi_stream_t stream);
 

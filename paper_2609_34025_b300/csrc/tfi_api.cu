@@ -1331,16 +1331,19 @@ tfi_status build_grad(tfi_plan_t p) {
     std::vector<int32_t> djobs;   // and the direct jobs' indices
     for (const tfi::Job &j : hp.jobs) {
         if (j.ke == j.kb) continue;
-        if (j.lp1 + j.lp2 > 13)
-            return fail(TFI_ERR_UNSUPPORTED, "kernel gradient needs every table to fit one shared-memory transform (P1 P2 <= 2^13)");
         const int32_t len = 2 * j.maxr + j.maxx + 1;
         // direct evaluation (pair dot products over the channels, then binning) when it is cheaper
-        // than one FFT correlation per channel at max_channels
+        // than one FFT correlation per channel at max_channels; a table beyond one shared-memory
+        // transform (P1 P2 > 2^13) takes the direct evaluation whatever its size class
         const double nk = double(j.ke - j.kb), D = double(hp.max_channels);
         const double np = std::ldexp(1.0, j.lp1 + j.lp2);
         const double cost_direct = 2 * nk * nk * D + double(len) * nk * nk;
         const double cost_fft = D * (5 * np * std::max(1, j.lp1 + j.lp2) + 10 * np);
-        const int32_t mode = (nk <= 32 * 255 && cost_direct < cost_fft) ? 1 : 0;
+        const bool fft_ok = j.lp1 + j.lp2 <= 13, direct_ok = nk <= 32 * 255;
+        if (!fft_ok && !direct_ok)
+            return fail(TFI_ERR_UNSUPPORTED, "kernel gradient: a table has more than 2^13 points and more than 8160 "
+                                             "occupied bins (neither evaluator of the correlation takes it)");
+        const int32_t mode = (direct_ok && (!fft_ok || cost_direct < cost_fft)) ? 1 : 0;
         gj.push_back(tfi::grad::GradJob{int32_t(j.kb), int32_t(j.ke), j.lp1, j.lp2, j.maxr, j.maxx, hoff, mode, 0,
                                         mode ? moff : 0});
         if (mode) {
@@ -1354,7 +1357,7 @@ tfi_status build_grad(tfi_plan_t p) {
         seg_len.push_back(len);
         seg_sign.push_back(j.is_comp ? -1.f : 1.f);
         hoff += int64_t(len) * nblk;  // one histogram per channel block; the job's sum lands in the first
-        max_lnp = std::max(max_lnp, j.lp1 + j.lp2);
+        if (mode == 0) max_lnp = std::max(max_lnp, j.lp1 + j.lp2);  // sizes grad_fft_kernel's shared memory
     }
     std::vector<int32_t> leaf_ptr(1, 0), hist_len;
     std::vector<int64_t> pair_off, hist_off;

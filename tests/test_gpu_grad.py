@@ -68,13 +68,22 @@ def test_grad_dtheta_every_analytic_kind(spec, leaf_max):
     _grad_case(cfg["tree"], 1.0, spec, 8, leaf_max)
 
 
-def test_grad_rejects_tables_beyond_one_transform():
+@pytest.mark.parametrize("leaf_max", [1, 16])
+def test_grad_diameter_policy_tables_beyond_one_transform(leaf_max):
+    # C1 under the diameter policy: its top diameter call has a table of 2^15 grid points, beyond one
+    # shared-memory transform, whose pair histogram is taken by the direct correlation
     cfg = W.configs.rrt_n2000()
-    p = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy="diameter", leaf_max=1, max_channels=4)
+    _grad_case(cfg["tree"], cfg["delta"], W.KernelSpec.expsum([0.7, -0.3], [0.4, 0.1]), 8, leaf_max,
+               policy="diameter")
+
+
+def test_grad_rejects_huge_tables_with_many_bins():
+    # the 2^14-vertex caterpillar at grid 1/64: tables of up to 2^19 points with tens of thousands of bins
+    cfg = W.configs.sweep(shape="caterpillar", n=1 << 14, d=4, kernel="exp")
+    p = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], leaf_max=64, max_channels=4)
     x = torch.zeros(cfg["tree"].n, 4, device="cuda")
-    z = torch.zeros_like(x)
     with pytest.raises(tfi.TfiError) as e:
-        p.kernel_grad(x, z)
+        p.kernel_grad(x, torch.zeros_like(x))
     assert e.value.name == "UNSUPPORTED"
 
 
