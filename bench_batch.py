@@ -2,7 +2,8 @@
 [64, 65536] (integer edge lengths 1..8, grid step 1), d = 16 FP32 N(0,1),
 f(x) = 1/(1 + 0.1 x)^2; forward + backward per step.
 
-The forest is planned once (leaf cutoff s0 autotuned on a subset of the trees)
+The forest is planned once (leaf cutoff s0 and the shared-memory FFT tile chosen by
+the library autotuner, tfi_autotune, on a subset of the trees)
 and a whole step is captured in one CUDA graph: every tree's calls share the
 same launches. It is compared with a per-tree launch loop (one plan and two
 applies per tree) on the same GPU, and spot-checked against the FP64 oracle.
@@ -57,21 +58,13 @@ def main():
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k
 
-    # autotune the leaf cutoff on the first 256 trees (a representative size mix)
-    sub_t = min(256, a.count)
-    sub, _ = T.forest([T.Tree(int(sizes[i]), forest.u[offs[i] - i:offs[i + 1] - i - 1] - offs[i],
-                              forest.v[offs[i] - i:offs[i + 1] - i - 1] - offs[i],
-                              forest.w[offs[i] - i:offs[i + 1] - i - 1]) for i in range(sub_t)])
-    xs = torch.from_numpy(W.normal_field(sub.n, d, seed=5)).cuda()
-    tune = {}
-    for s0 in (64, 128, 256, 512):
-        ps = tfi.Plan.from_spec(sub, delta, spec, leaf_max=s0, max_channels=d)
-        tune[s0] = timed(lambda: ps.apply(xs), 5)
-        ps.close()
-    best = min(tune, key=tune.get)
+    # the library autotuner: leaf cutoff and shared-memory FFT tile timed on the first 256 trees
+    # (a representative size mix), then the whole forest planned once with the winner
     t0 = time.perf_counter()
-    plan = tfi.Plan.from_spec(forest, delta, spec, leaf_max=best, max_channels=d)
+    plan, tuned = tfi.Plan.autotune(forest, delta, spec, d, leaf_candidates=[64, 128, 256, 512],
+                                    sample_trees=min(256, a.count), reps=5)
     plan_s = time.perf_counter() - t0
+    best = tuned["leaf_max"]
     F = torch.from_numpy(W.normal_field(n, d, seed=123)).cuda()
     G = torch.from_numpy(W.normal_field(n, d, seed=124)).cuda()
     out, gF = torch.empty_like(F), torch.empty_like(F)
@@ -111,9 +104,8 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"uneven_batch_{a.count}_trees", "trees": a.count, "n_total": int(n),
                    "sizes": "log-uniform [64, 65536]", "weights": "integers 1..8", "delta": 1.0, "d": d,
-                   "kernel": "1/(1+0.1x)^2", "leaf_max_autotuned": best,
-                   "autotune_ms_per_apply_256_trees": {str(k): round(v, 4) for k, v in tune.items()},
-                   "plan_seconds": round(plan_s, 2), "launch": "one CUDA graph per fwd+bwd step"},
+                   "kernel": "1/(1+0.1x)^2", "autotuned": tuned, "autotune_trees": min(256, a.count),
+                   "autotune_and_plan_seconds": round(plan_s, 2), "launch": "one CUDA graph per fwd+bwd step"},
         "per_tree_loop": {"trees": nloop, "n": loop_n, "ms_per_step": loop_ms,
                           "value": loop_n * d / (loop_ms / 1e3), "plan_seconds": round(loop_plan_s, 2)},
         "speedup_vs_loop": (loop_n * d / (loop_ms / 1e3)) and (n * d / (step_ms / 1e3)) / (loop_n * d / (loop_ms / 1e3)),

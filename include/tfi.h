@@ -126,6 +126,9 @@ typedef struct {
     int32_t leaf_max;       /* s0 >= 1: a call with <= s0 vertices is summed densely (s0 = 1: base case f(0) x_u) */
     int32_t max_channels;   /* largest d any apply will use (sizes the workspace) */
     int32_t flags;          /* TFI_PLAN_* */
+    int32_t fft_cta_points; /* shared-memory FFT tile: points x channel pairs one CTA transforms for tables
+                               below 2^13 points (4096, 8192 or 16384, i.e. 32, 64 or 128 KB of shared
+                               memory; 0 = 8192). A launch-shape knob, chosen by tfi_autotune */
 } tfi_options;
 
 #define TFI_DTYPE_F32  0
@@ -140,6 +143,24 @@ typedef struct {
  * recursion level, or the trees of a forest, in parallel) and returns the same
  * plan whatever the thread count. */
 tfi_status tfi_plan(const tfi_tree *tree, const tfi_kernel *kernel, const tfi_options *opt, tfi_plan_t *out);
+
+/* Autotuner (launch-shape and leaf-cutoff choice for a given tree and width; the
+ * paper has no counterpart: its cost model picks backbones, not launch shapes).
+ * For each leaf cutoff in leaf_candidates (n_leaf of them; NULL / 0 = {64, 128,
+ * 256, 512, 1024}) it plans the forest with *opt and that leaf_max, and for each
+ * shared-memory FFT tile (fft_cta_points 4096, 8192, 16384) times `reps` applies
+ * of d channels of dtype with CUDA events on a private stream after two warm-up
+ * applies; the fastest configuration is written to *tuned (a copy of *opt with
+ * leaf_max and fft_cta_points set) and its time per apply to *best_ms (nullable).
+ * With sample_trees > 0 and a forest of more trees, the tuning runs on its first
+ * sample_trees trees (by smallest vertex) and the whole forest is planned once
+ * with the winner. When plan_out is non-NULL it receives that plan (owned by the
+ * caller); otherwise nothing stays allocated. Host work as in tfi_plan; device
+ * fields of n x d are allocated for the timing and freed. Synchronises the device
+ * work it launches. */
+tfi_status tfi_autotune(const tfi_tree *tree, const tfi_kernel *kernel, const tfi_options *opt, int32_t d,
+                        int32_t dtype, const int32_t *leaf_candidates, int32_t n_leaf, int32_t sample_trees,
+                        int32_t reps, tfi_options *tuned, double *best_ms, tfi_plan_t *plan_out);
 
 /* out = K F (the operator above). F, out: device, n x d, dtype; out is
  * overwritten and must not alias F. 1 <= d <= max_channels. */

@@ -48,7 +48,7 @@ class _Kernel(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("policy", ctypes.c_int32), ("leaf_max", ctypes.c_int32),
-                ("max_channels", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("max_channels", ctypes.c_int32), ("flags", ctypes.c_int32), ("fft_cta_points", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -64,7 +64,7 @@ EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_ho
                     "tfi_plan_get_info", "tfi_plan_export", "tfi_profile_enable", "tfi_profile_read",
                     "tfi_stage_model", "tfi_apply_static", "tfi_dense_apply", "tfi_graph_create", "tfi_graph_launch",
                     "tfi_graph_destroy", "tfi_sinkhorn", "tfi_kernel_grad", "tfi_set_kernel", "tfi_selftest_wait",
-                    "tfi_last_error")
+                    "tfi_autotune", "tfi_last_error")
 STAGES = ("leaf", "bucket", "fft", "direct", "gather", "sweep", "hankel")
 HANKEL_MODES = {None: 0, False: 0, "auto": 4, "all": 8}
 SWEEP_MODES = {None: 0, False: 0, True: 2, "all": 2, "auto": 32}
@@ -133,7 +133,7 @@ class Plan:
 
     def __init__(self, n, u, v, w, delta=1.0, kernel=("expsum", [1.0, 1.0]), table=None, policy="adaptive",
                  leaf_max=64, max_channels=16, host_only=False, sweep=False, hankel=None, leaf_alu=False,
-                 fft_big_all=False):
+                 fft_big_all=False, fft_cta_points=0):
         u = np.ascontiguousarray(u, dtype=np.int32)
         v = np.ascontiguousarray(v, dtype=np.int32)
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -145,7 +145,7 @@ class Plan:
                       0 if tab is None else int(tab.shape[0]), None if tab is None else tab.ctypes.data)
         opt = _Options(float(delta), POLICIES[policy], int(leaf_max), int(max_channels),
                        (1 if host_only else 0) | SWEEP_MODES[sweep] | HANKEL_MODES[hankel] | (16 if leaf_alu else 0)
-                       | (64 if fft_big_all else 0))
+                       | (64 if fft_big_all else 0), int(fft_cta_points))
         h = ctypes.c_void_p()
         _check(lib().tfi_plan(ctypes.byref(tree), ctypes.byref(ker), ctypes.byref(opt), ctypes.byref(h)))
         self._h = h
@@ -154,6 +154,41 @@ class Plan:
         self.host_only = host_only
         self.kernel_kind = KERNEL_KINDS[kind]
         self.n_params = 0 if kind == "table" else int(params.shape[0])
+
+    @classmethod
+    def autotune(cls, tree, delta, spec, d, dtype="f32", leaf_candidates=None, sample_trees=0, reps=5,
+                 policy="adaptive", max_channels=None, **flags):
+        """Plan with the leaf cutoff and FFT tile that measure fastest for d channels (tfi_autotune).
+        Returns (plan, {"leaf_max", "fft_cta_points", "ms_per_apply"})."""
+        u = np.ascontiguousarray(tree.u, dtype=np.int32)
+        v = np.ascontiguousarray(tree.v, dtype=np.int32)
+        w = np.ascontiguousarray(tree.w, dtype=np.float64)
+        params = np.ascontiguousarray(list(spec.params), dtype=np.float64)
+        tab = None if getattr(spec, "table", None) is None else np.ascontiguousarray(spec.table, dtype=np.float64)
+        tr = _Tree(int(tree.n), int(u.shape[0]), u.ctypes.data, v.ctypes.data, w.ctypes.data)
+        ker = _Kernel(KERNEL_KINDS[spec.kind], int(params.shape[0]), params.ctypes.data if params.size else None,
+                      0 if tab is None else int(tab.shape[0]), None if tab is None else tab.ctypes.data)
+        mc = int(max_channels or d)
+        fl = SWEEP_MODES[flags.get("sweep", False)] | HANKEL_MODES[flags.get("hankel", None)] | \
+            (16 if flags.get("leaf_alu") else 0) | (64 if flags.get("fft_big_all") else 0)
+        opt = _Options(float(delta), POLICIES[policy], 64, mc, fl, 0)
+        cand = None if leaf_candidates is None else np.ascontiguousarray(leaf_candidates, dtype=np.int32)
+        tuned = _Options()
+        ms = ctypes.c_double()
+        h = ctypes.c_void_p()
+        dt = DTYPE_F32 if dtype in ("f32", DTYPE_F32) else DTYPE_BF16
+        _check(lib().tfi_autotune(ctypes.byref(tr), ctypes.byref(ker), ctypes.byref(opt), int(d), dt,
+                                  None if cand is None else cand.ctypes.data, 0 if cand is None else int(cand.shape[0]),
+                                  int(sample_trees), int(reps), ctypes.byref(tuned), ctypes.byref(ms), ctypes.byref(h)))
+        plan = cls.__new__(cls)
+        plan._h = h
+        plan.n = int(tree.n)
+        plan.max_channels = mc
+        plan.host_only = False
+        plan.kernel_kind = KERNEL_KINDS[spec.kind]
+        plan.n_params = 0 if spec.kind == "table" else int(params.shape[0])
+        return plan, {"leaf_max": int(tuned.leaf_max), "fft_cta_points": int(tuned.fft_cta_points),
+                      "ms_per_apply": float(ms.value)}
 
     @classmethod
     def from_spec(cls, tree, delta, spec, **kw):

@@ -139,6 +139,7 @@ struct tfi_plan_s {
     tfi::tc::LeafTile *leaf_tiles = nullptr;  // 128-row tiles of the leaf groups (tensor-core leaves)
     int32_t n_leaf_tiles = 0;
     std::map<int, WorkLists> work;  // per channel count d
+    int32_t fft_cta_points = 1 << 13;  // tfi_options.fft_cta_points (0 there: this default)
     // tfi_apply_static: its work lists without per-call host copies. Direct items do not depend
     // on d; FFT jobs are kept by size class and expanded into (job, pair block) items on the
     // device at each call, into the static workspace
@@ -215,10 +216,12 @@ struct tfi_plan_s {
 namespace {
 
 constexpr int kFftThreads = 256;
-constexpr int kFftSmemPairPoints = 1 << 13;  // points x pairs per CTA (64 KB) for classes below 2^14
+constexpr int kFftSmemPairPoints = 1 << 13;  // default points x pairs per CTA (64 KB) for classes below 2^13
 
-int fft_pairs_per_cta(int lnp, int pairs) {
-    const int cap = lnp >= 13 ? 1 : (kFftSmemPairPoints >> lnp);
+// Channel pairs per CTA of the shared-memory FFT for a class of 2^lnp points: up to
+// cta_points / 2^lnp (tfi_options.fft_cta_points; one pair from 2^13 points on).
+int fft_pairs_per_cta(int lnp, int pairs, int cta_points) {
+    const int cap = lnp >= 13 ? 1 : std::max(1, cta_points >> lnp);
     return std::max(1, std::min(pairs, cap));
 }
 
@@ -246,7 +249,7 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
                 hk.push_back(tfi::tc::HankelItem{int32_t(jb.kb), int32_t(jb.ke), c0, jb.maxr, jb.maxx, {0, 0, 0}});
         } else if (jb.mode == 0) {
             const int lnp = jb.lp1 + jb.lp2;
-            const int np = fft_pairs_per_cta(lnp, pairs);
+            const int np = fft_pairs_per_cta(lnp, pairs, p->fft_cta_points);
             for (int p0 = 0; p0 < pairs; p0 += np)
                 by_class[lnp].push_back(tfi::dev::FftItem{int32_t(j), p0, std::min(np, pairs - p0)});
         } else {
@@ -257,7 +260,7 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
     for (auto &kv : by_class) {
         wl.fft_lnp.push_back(kv.first);
         wl.fft_count.push_back(int(kv.second.size()));
-        wl.fft_npair.push_back(fft_pairs_per_cta(kv.first, pairs));
+        wl.fft_npair.push_back(fft_pairs_per_cta(kv.first, pairs, p->fft_cta_points));
         wl.fft_off.push_back(int64_t(all.size()));
         all.insert(all.end(), kv.second.begin(), kv.second.end());
     }
@@ -1116,7 +1119,7 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
     std::vector<int64_t> cls_off(n_cls);
     int64_t n_fft = 0;
     for (size_t c = 0; c < n_cls; ++c) {
-        cls_np[c] = fft_pairs_per_cta(p->st_cls_lnp[c], pairs);
+        cls_np[c] = fft_pairs_per_cta(p->st_cls_lnp[c], pairs, kFftSmemPairPoints);
         cls_per[c] = (pairs + cls_np[c] - 1) / cls_np[c];
         cls_off[c] = n_fft;
         n_fft += int64_t(p->st_cls_njobs[c]) * cls_per[c];
@@ -1486,6 +1489,9 @@ tfi_status tfi_plan(const tfi_tree *tree, const tfi_kernel *kernel, const tfi_op
     if (opt->leaf_max < 1 || opt->leaf_max > tfi::kLeafMax)
         return fail(TFI_ERR_ARG, "leaf_max must be in [1, " + std::to_string(tfi::kLeafMax) + "]");
     if (opt->max_channels < 1) return fail(TFI_ERR_ARG, "max_channels must be >= 1");
+    if (opt->fft_cta_points != 0 && opt->fft_cta_points != 4096 && opt->fft_cta_points != 8192 &&
+        opt->fft_cta_points != 16384)
+        return fail(TFI_ERR_ARG, "fft_cta_points must be 0, 4096, 8192 or 16384");
     if (kernel->kind < 0 || kernel->kind > 4) return fail(TFI_ERR_ARG, "unknown kernel kind");
     if (kernel->n_params < 0 || (kernel->n_params > 0 && !kernel->params)) return fail(TFI_ERR_ARG, "bad kernel params");
     const int need[5] = {0, 2, 2, 4, 3};
@@ -1502,6 +1508,7 @@ tfi_status tfi_plan(const tfi_tree *tree, const tfi_kernel *kernel, const tfi_op
     hp.leaf_max = opt->leaf_max;
     hp.max_channels = opt->max_channels;
     hp.flags = opt->flags;
+    p->fft_cta_points = opt->fft_cta_points ? opt->fft_cta_points : kFftSmemPairPoints;
     if ((opt->flags & TFI_PLAN_SWEEP) && kernel->kind != TFI_F_EXPSUM)
         return fail(TFI_ERR_ARG, "TFI_PLAN_SWEEP needs an exponential-sum kernel (TFI_F_EXPSUM)");
     hp.f.kind = kernel->kind;
@@ -1523,6 +1530,172 @@ tfi_status tfi_plan(const tfi_tree *tree, const tfi_kernel *kernel, const tfi_op
     }
     *out = p.release();
     return TFI_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Drop the per-d work lists (they depend on fft_cta_points); rebuilt on the next apply.
+void clear_work(tfi_plan_t p) {
+    for (auto &kv : p->work) {
+        cudaFree(kv.second.d_fft);
+        cudaFree(kv.second.d_dir);
+        cudaFree(kv.second.d_hk);
+        cudaFree(kv.second.d_big);
+    }
+    p->work.clear();
+}
+
+__global__ void fill_ones_bf16(int64_t n, __nv_bfloat16 *x) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        x[i] = __float2bfloat16_rn(1.f);
+}
+
+// The first `count` trees of a forest (ordered by their smallest vertex), relabelled in
+// ascending vertex order; every tree when count <= 0 or the forest has fewer trees.
+struct SubForest {
+    std::vector<int32_t> u, v;
+    std::vector<double> w;
+    int32_t n = 0;
+    bool whole = true;
+};
+SubForest first_trees(const tfi_tree *t, int32_t count) {
+    SubForest sf;
+    std::vector<int32_t> par(size_t(t->n));
+    std::iota(par.begin(), par.end(), 0);
+    auto find = [&](int32_t a) {
+        while (par[size_t(a)] != a) a = par[size_t(a)] = par[size_t(par[size_t(a)])];
+        return a;
+    };
+    for (int32_t e = 0; e < t->n_edges; ++e) {
+        const int32_t a = find(t->u[e]), b = find(t->v[e]);
+        if (a != b) par[size_t(std::max(a, b))] = std::min(a, b);  // root = smallest vertex of the tree
+    }
+    std::vector<int32_t> label(size_t(t->n), -1);
+    int32_t trees = 0;
+    for (int32_t x = 0; x < t->n; ++x) {
+        const int32_t r = find(x);
+        if (r == x) ++trees;
+        if (count <= 0 || trees <= count) label[size_t(x)] = sf.n++;
+    }
+    sf.whole = count <= 0 || trees <= count;
+    for (int32_t e = 0; e < t->n_edges; ++e) {
+        if (label[size_t(t->u[e])] < 0) continue;
+        sf.u.push_back(label[size_t(t->u[e])]);
+        sf.v.push_back(label[size_t(t->v[e])]);
+        sf.w.push_back(t->w[e]);
+    }
+    return sf;
+}
+
+}  // namespace
+
+extern "C" {
+
+tfi_status tfi_autotune(const tfi_tree *tree, const tfi_kernel *kernel, const tfi_options *opt, int32_t d,
+                        int32_t dtype, const int32_t *leaf_candidates, int32_t n_leaf, int32_t sample_trees,
+                        int32_t reps, tfi_options *tuned, double *best_ms, tfi_plan_t *plan_out) {
+    if (!tree || !kernel || !opt || !tuned) return fail(TFI_ERR_ARG, "null argument");
+    if (plan_out) *plan_out = nullptr;
+    if (opt->flags & TFI_PLAN_HOST_ONLY) return fail(TFI_ERR_ARG, "autotuning measures on the device (no HOST_ONLY)");
+    if (d < 1 || d > opt->max_channels) return fail(TFI_ERR_ARG, "d must be in [1, max_channels]");
+    if (dtype != TFI_DTYPE_F32 && dtype != TFI_DTYPE_BF16) return fail(TFI_ERR_ARG, "unknown dtype");
+    if (n_leaf < 0 || (n_leaf > 0 && !leaf_candidates)) return fail(TFI_ERR_ARG, "bad leaf candidates");
+    if (reps < 1) return fail(TFI_ERR_ARG, "reps must be >= 1");
+    if (tree->n < 1 || tree->n_edges < 0 || tree->n_edges > tree->n - 1 ||
+        (tree->n_edges > 0 && (!tree->u || !tree->v || !tree->w)))
+        return fail(TFI_ERR_ARG, "bad tree");
+    for (int32_t e = 0; e < tree->n_edges; ++e)
+        if (tree->u[e] < 0 || tree->u[e] >= tree->n || tree->v[e] < 0 || tree->v[e] >= tree->n)
+            return fail(TFI_ERR_NOT_TREE, "edge endpoint out of range");
+    std::vector<int32_t> cand;
+    if (n_leaf > 0) cand.assign(leaf_candidates, leaf_candidates + n_leaf);
+    else cand = {64, 128, 256, 512, 1024};
+    const int32_t ctas[3] = {4096, 8192, 16384};
+    const SubForest sf = first_trees(tree, sample_trees);
+    const tfi_tree sub{sf.n, int32_t(sf.u.size()), sf.u.data(), sf.v.data(), sf.w.data()};
+    const tfi_tree *tune_tree = sf.whole ? tree : &sub;
+    const size_t esz = dtype == TFI_DTYPE_BF16 ? 2 : 4;
+    const int64_t nd = int64_t(tune_tree->n) * d;
+    struct Buffers {
+        void *F = nullptr, *out = nullptr;
+        cudaStream_t s = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Buffers() {
+            cudaFree(F);
+            cudaFree(out);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            if (s) cudaStreamDestroy(s);
+        }
+    } b;
+    if (cudaMalloc(&b.F, size_t(nd) * esz) != cudaSuccess || cudaMalloc(&b.out, size_t(nd) * esz) != cudaSuccess)
+        return fail(TFI_ERR_OOM, "cudaMalloc failed for the autotuning fields");
+    TFI_CUDA(cudaStreamCreateWithFlags(&b.s, cudaStreamNonBlocking));
+    TFI_CUDA(cudaEventCreate(&b.e0));
+    TFI_CUDA(cudaEventCreate(&b.e1));
+    if (dtype == TFI_DTYPE_F32)
+        tfi::dev::fill_value<<<grid_for(nd, 256), 256, 0, b.s>>>(nd, 1.f, static_cast<float *>(b.F));
+    else
+        fill_ones_bf16<<<grid_for(nd, 256), 256, 0, b.s>>>(nd, static_cast<__nv_bfloat16 *>(b.F));
+    TFI_CUDA(cudaGetLastError());
+    double best = INFINITY;
+    tfi_options best_opt = *opt;
+    tfi_plan_t keep = nullptr;
+    for (int32_t s0 : cand) {
+        tfi_options o = *opt;
+        o.leaf_max = std::max(1, std::min(s0, tfi::kLeafMax));
+        o.fft_cta_points = 0;
+        tfi_plan_t pl = nullptr;
+        if (tfi_status rc = tfi_plan(tune_tree, kernel, &o, &pl)) {
+            tfi_destroy(keep);
+            return rc;
+        }
+        bool kept = false;
+        for (int32_t cta : ctas) {
+            clear_work(pl);
+            pl->fft_cta_points = cta;
+            tfi_status rc = TFI_OK;
+            for (int w = 0; w < 2 && rc == TFI_OK; ++w) rc = tfi_apply(pl, b.F, b.out, d, dtype, b.s);
+            if (rc == TFI_OK) rc = cudaEventRecord(b.e0, b.s) == cudaSuccess ? TFI_OK : TFI_ERR_CUDA;
+            for (int r = 0; r < reps && rc == TFI_OK; ++r) rc = tfi_apply(pl, b.F, b.out, d, dtype, b.s);
+            float ms = 0.f;
+            if (rc == TFI_OK && (cudaEventRecord(b.e1, b.s) != cudaSuccess || cudaEventSynchronize(b.e1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&ms, b.e0, b.e1) != cudaSuccess))
+                rc = fail(TFI_ERR_CUDA, "autotuning timing failed");
+            if (rc != TFI_OK) {
+                tfi_destroy(pl);
+                if (keep != pl) tfi_destroy(keep);
+                return rc;
+            }
+            const double per = double(ms) / reps;
+            if (per < best) {
+                best = per;
+                best_opt = o;
+                best_opt.fft_cta_points = cta;
+                if (keep && keep != pl) tfi_destroy(keep);
+                keep = pl;
+                kept = true;
+            }
+        }
+        if (!kept) tfi_destroy(pl);
+    }
+    *tuned = best_opt;
+    if (best_ms) *best_ms = best;
+    if (!plan_out) {
+        tfi_destroy(keep);
+        return TFI_OK;
+    }
+    if (sf.whole) {
+        // the winner's plan, with its work lists rebuilt for the chosen tile on the next apply
+        clear_work(keep);
+        keep->fft_cta_points = best_opt.fft_cta_points;
+        *plan_out = keep;
+        return TFI_OK;
+    }
+    tfi_destroy(keep);
+    return tfi_plan(tree, kernel, &best_opt, plan_out);
 }
 
 tfi_status tfi_apply(tfi_plan_t plan, const void *F, void *out, int32_t d, int32_t dtype, tfi_stream_t stream) {

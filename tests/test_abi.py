@@ -94,3 +94,10 @@ def test_quantisation_matches_oracle_rounding():
     p = _plan(8, list(range(7)), list(range(1, 8)), w, delta=1.0, policy="diameter", leaf_max=1)
     calls = p.export("calls")
     assert calls[0, 6] == quantise(w, 1.0).sum()
+
+
+def test_rejects_bad_fft_tile():
+    t = W.path(10)
+    with pytest.raises(tfi.TfiError) as e:
+        tfi.Plan.from_spec(t, 1.0, W.KernelSpec.exp(0.1), host_only=True, fft_cta_points=1000)
+    assert e.value.name == "ARG"
