@@ -554,6 +554,31 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_profile_helper(a):
+    """ncu helper: plan the workload and run `--profile-applies` forward applies (or dense
+    applies with --profile-dense) with no timing and no JSON line, so that a capture covers
+    exactly those launches after the plan-time ones."""
+    import torch
+
+    import paper_2609_34025_b300 as tfi
+    from paper_2609_34025_b300 import build as tbuild
+    import workloads as W
+
+    tbuild.build()
+    cfg = W.configs.sweep(**workload_args(a))
+    plan = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=a.policy, leaf_max=a.leaf_max,
+                              max_channels=a.d)
+    x = torch.from_numpy(W.normal_field(cfg["tree"].n, a.d, seed=123)).cuda()
+    out = torch.empty_like(x)
+    for _ in range(a.profile_applies):
+        (plan.dense_apply if a.profile_dense else plan.apply)(x, out)
+    torch.cuda.synchronize()
+    info = plan.info()
+    print(f"profile helper: {workload_name(a)}, {a.profile_applies} {'dense ' if a.profile_dense else ''}applies, "
+          f"{info['n_jobs_fft']} FFT / {info['n_jobs_fft_big']} four-step / {info['n_jobs_direct']} direct tables",
+          file=sys.stderr)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -571,10 +596,16 @@ def main():
     ap.add_argument("--dense-n", dest="dense_n", type=int, default=1 << 16, help="tree size of the dense baseline")
     ap.add_argument("--no-c2-sweep", dest="c2", action="store_false",
                     help="skip the other C2 shapes, widths and kernels at the same N")
+    ap.add_argument("--profile-applies", dest="profile_applies", type=int, default=0,
+                    help="ncu helper: plan, run this many forward applies, no timing, no JSON line")
+    ap.add_argument("--profile-dense", dest="profile_dense", action="store_true",
+                    help="with --profile-applies: the dense tensor-core path instead")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
-    if a.impl == "reference":
+    if a.profile_applies > 0:
+        run_profile_helper(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)
