@@ -356,3 +356,27 @@ def test_sinkhorn_oracle_marginals_and_cost_identity():
     K2 = S.dense_matrix(t, delta, W.KernelSpec.powexp(1.0 / eps))
     direct = np.einsum("ic,ij,ij,jc->c", u, K, D, v)
     np.testing.assert_allclose(S.transport_cost(K2, u, v), direct, rtol=1e-12)
+
+
+def test_sinkhorn_at_eps_005_is_fp32_representable_with_a_dense_kernel():
+    # The torus-MST recipe at eps = 0.05 (Delta = 1/256): two thirds of the kernel matrix underflow
+    # to zero in FP32, yet the plain dense iteration run entirely in FP32 reaches the FP64 transport
+    # cost to 1e-6. So FP32 arithmetic as such does not prevent this regime; what it needs is an
+    # elementwise-accurate K v for entries far below max(K v), which the dense product has.
+    from oracle import sinkhorn as S
+    cfg = W.configs.torus_sinkhorn(n=1500, pairs=4)
+    t, delta = cfg["tree"], cfg["delta"]
+    spec = W.KernelSpec.exp(1.0 / 0.05)
+    a, b = W.dirichlet_pairs(t.n, 4, seed=1)
+    K = S.dense_matrix(t, delta, spec)
+    K2 = S.dense_matrix(t, delta, W.KernelSpec.powexp(1.0 / 0.05))
+    u64, v64 = S.sinkhorn(K, a.astype(np.float64), b.astype(np.float64), 200)
+    K32, a32, b32 = K.astype(np.float32), a.astype(np.float32), b.astype(np.float32)
+    assert np.mean(K32 == 0) > 0.5
+    u, v = np.ones_like(a32), np.ones_like(b32)
+    for _ in range(200):
+        u = a32 / (K32 @ v + np.float32(1e-30))
+        v = b32 / (K32.T @ u + np.float32(1e-30))
+    c64 = S.transport_cost(K2, u64, v64)
+    c32 = S.transport_cost(K2, u.astype(np.float64), v.astype(np.float64))
+    np.testing.assert_allclose(c32, c64, rtol=1e-5)
