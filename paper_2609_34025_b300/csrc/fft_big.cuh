@@ -155,16 +155,17 @@ __global__ void __launch_bounds__(256) big_columns(const BigItem *__restrict__ i
 // Pass B: 2^lnb consecutive blocks (consecutive ka slots) per CTA, each in its own
 // padded shared-memory array: the N1b x P2 forward FFT, the product with that block's
 // spectrum, the inverse FFT and the factor w_{P1}^{-nb ka}.
-__global__ void __launch_bounds__(256) big_blocks(const BigItem *__restrict__ items, BigGeom g, int lnb,
+// CTAs run block-major (every item's blocks s0 .. s0 + 2^lnb - 1 next to each other): the
+// items of a launch share their size class's spectrum, whose blocks then come from L2.
+__global__ void __launch_bounds__(256) big_blocks(const BigItem *__restrict__ items, int n_items, BigGeom g, int lnb,
                                                   float2 *__restrict__ buf, const float2 *__restrict__ spectra,
                                                   const float2 *__restrict__ tw, const float2 *__restrict__ tw_hi,
                                                   const float2 *__restrict__ tw_lo) {
     extern __shared__ float2 Z[];
     const int lb = g.lp1b + g.lp2;
     const int BLK = 1 << lb, P2 = 1 << g.lp2, NBK = 1 << lnb;
-    const int per = 1 << (g.lnA - lnb);
-    const BigItem it = items[blockIdx.x / per];
-    const int s0 = int(blockIdx.x % per) << lnb;
+    const BigItem it = items[blockIdx.x % n_items];
+    const int s0 = int(blockIdx.x / n_items) << lnb;
     float2 *a = buf + it.off + int64_t(s0) * BLK;
     const int padnp = padded_size(BLK);
     for (int e = threadIdx.x; e < (BLK << lnb); e += blockDim.x) Z[(e >> lb) * padnp + padded(e & (BLK - 1))] = a[e];

@@ -362,7 +362,7 @@ void launch_big(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
             const unsigned grid_c = unsigned(n_it * (BLK >> lcg)), grid_b = unsigned(n_it * (NA >> lnb));
             tfi::dev::big_columns<false><<<grid_c, 256, smem_c, s>>>(it, g, lcg, p->big_buf, p->twiddle, p->big_tw_hi,
                                                                     p->big_tw_lo);
-            tfi::dev::big_blocks<<<grid_b, 256, smem_b, s>>>(it, g, lnb, p->big_buf, p->spectra, p->twiddle,
+            tfi::dev::big_blocks<<<grid_b, 256, smem_b, s>>>(it, int(n_it), g, lnb, p->big_buf, p->spectra, p->twiddle,
                                                              p->big_tw_hi, p->big_tw_lo);
             tfi::dev::big_columns<true><<<grid_c, 256, smem_c, s>>>(it, g, lcg, p->big_buf, p->twiddle, p->big_tw_hi,
                                                                    p->big_tw_lo);
