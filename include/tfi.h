@@ -190,6 +190,17 @@ tfi_status tfi_dense_apply(tfi_plan_t plan, const void *F, void *out, int32_t d,
 tfi_status tfi_apply_host(tfi_plan_t plan, const void *F_host, void *out_host, int32_t d, int32_t dtype,
                           tfi_stream_t stream);
 
+/* out_host[i] = K F_host[i] for n_fields independent fields in HOST memory,
+ * pipelined: field i + 1 is copied in and field i - 1 copied out while field i
+ * is applied (two plan-owned staging slots, a copy-in and a copy-out stream
+ * owned by the plan, the apply on `stream`). Overlap needs pinned host memory;
+ * pageable buffers give the same results without it. Each array is n x d of
+ * dtype; inputs are read and outputs written during the call only, and the
+ * call returns when every output is in host memory. The first call allocates
+ * four n x max_channels FP32 staging buffers and the two copy streams. */
+tfi_status tfi_apply_host_many(tfi_plan_t plan, int32_t n_fields, const void *const *F_host, void *const *out_host,
+                               int32_t d, int32_t dtype, tfi_stream_t stream);
+
 /* Allocation-free apply: the same result as tfi_apply, for callers that must not
  * allocate device memory while they run. That includes hosts that own all
  * device memory through their own allocator or a fixed budget and forbid

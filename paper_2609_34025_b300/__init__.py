@@ -64,7 +64,7 @@ EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_ho
                     "tfi_plan_get_info", "tfi_plan_export", "tfi_profile_enable", "tfi_profile_read",
                     "tfi_stage_model", "tfi_apply_static", "tfi_dense_apply", "tfi_graph_create", "tfi_graph_launch",
                     "tfi_graph_destroy", "tfi_sinkhorn", "tfi_kernel_grad", "tfi_set_kernel", "tfi_selftest_wait",
-                    "tfi_autotune", "tfi_last_error")
+                    "tfi_autotune", "tfi_apply_host_many", "tfi_last_error")
 STAGES = ("leaf", "bucket", "fft", "direct", "gather", "sweep", "hankel")
 HANKEL_MODES = {None: 0, False: 0, "auto": 4, "all": 8}
 SWEEP_MODES = {None: 0, False: 0, True: 2, "all": 2, "auto": 32}
@@ -298,6 +298,15 @@ class Plan:
         """Host pointers (e.g. pinned torch tensors) in and out, synchronised."""
         _check(lib().tfi_apply_host(self._h, ctypes.c_void_p(f_ptr), ctypes.c_void_p(out_ptr), int(d), int(dtype),
                                     _stream_handle(stream)))
+
+    def apply_host_many(self, f_ptrs, out_ptrs, d: int, dtype: int = DTYPE_F32, stream=None):
+        """Host fields in and out (e.g. pinned torch tensors), pipelined copies and applies, synchronised."""
+        n = len(f_ptrs)
+        if len(out_ptrs) != n:
+            raise ValueError("need one output per input")
+        fa = (ctypes.c_void_p * max(1, n))(*[ctypes.c_void_p(p) for p in f_ptrs])
+        oa = (ctypes.c_void_p * max(1, n))(*[ctypes.c_void_p(p) for p in out_ptrs])
+        _check(lib().tfi_apply_host_many(self._h, n, fa, oa, int(d), int(dtype), _stream_handle(stream)))
 
     def info(self) -> dict:
         inf = _Info()

@@ -123,6 +123,12 @@ struct tfi_plan_s {
     float *sw_beta = nullptr, *sw_coef = nullptr, *sw_scratch = nullptr;
     int32_t n_sweeps = 0, n_sw_ejobs = 0, sw_terms = 0;
     void *stage_in = nullptr, *stage_out = nullptr;
+    // tfi_apply_host_many: two staging slots (in, out), copy-in and copy-out streams, and per slot
+    // the events that order copy-in -> apply -> copy-out and the reuse of a slot two fields later
+    void *pipe_in[2] = {nullptr, nullptr}, *pipe_out[2] = {nullptr, nullptr};
+    cudaStream_t pipe_cin = nullptr, pipe_cout = nullptr;
+    cudaEvent_t ev_in_ready[2] = {nullptr, nullptr}, ev_in_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_out_ready[2] = {nullptr, nullptr}, ev_out_free[2] = {nullptr, nullptr};
     int32_t *dev_rec_r = nullptr, *dev_rec_x = nullptr;  // record keys computed on the device at plan time
     // dense tensor-core evaluation (built on first use): per-tree preorder, root
     // distances, sparse table of parent distances, f samples up to the largest diameter
@@ -197,8 +203,12 @@ struct tfi_plan_s {
         return TFI_OK;
     }
     ~tfi_plan_s() {
-        for (cudaEvent_t e : {ev_fork, ev_leaf, ev_bucket, ev_dir, ev_crit})
+        for (cudaEvent_t e : {ev_fork, ev_leaf, ev_bucket, ev_dir, ev_crit, ev_in_ready[0], ev_in_ready[1],
+                              ev_in_free[0], ev_in_free[1], ev_out_ready[0], ev_out_ready[1], ev_out_free[0],
+                              ev_out_free[1]})
             if (e) cudaEventDestroy(e);
+        for (cudaStream_t st : {pipe_cin, pipe_cout})
+            if (st) cudaStreamDestroy(st);
         for (cudaStream_t st : aux)
             if (st) cudaStreamDestroy(st);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
@@ -1749,6 +1759,57 @@ tfi_status tfi_apply_host(tfi_plan_t plan, const void *F_host, void *out_host, i
     TFI_CUDA(cudaMemcpyAsync(plan->stage_in, F_host, bytes, cudaMemcpyHostToDevice, s));
     if (tfi_status rc = tfi_apply(plan, plan->stage_in, plan->stage_out, d, dtype, stream)) return rc;
     TFI_CUDA(cudaMemcpyAsync(out_host, plan->stage_out, bytes, cudaMemcpyDeviceToHost, s));
+    TFI_CUDA(cudaStreamSynchronize(s));
+    return TFI_OK;
+}
+
+tfi_status tfi_apply_host_many(tfi_plan_t plan, int32_t n_fields, const void *const *F_host, void *const *out_host,
+                               int32_t d, int32_t dtype, tfi_stream_t stream) {
+    if (!plan || n_fields < 0 || (n_fields > 0 && (!F_host || !out_host))) return fail(TFI_ERR_ARG, "null argument");
+    if (!plan->on_device) return fail(TFI_ERR_NO_DEVICE, "plan was built host-only");
+    for (int32_t i = 0; i < n_fields; ++i)
+        if (!F_host[i] || !out_host[i]) return fail(TFI_ERR_ARG, "null field pointer");
+    if (n_fields == 0) return TFI_OK;
+    if (!plan->pipe_in[0]) {
+        const size_t cap = size_t(plan->hp.n) * size_t(plan->hp.max_channels) * 4;
+        for (int k = 0; k < 2; ++k) {
+            if (tfi_status rc = plan->alloc(&plan->pipe_in[k], cap)) return rc;
+            if (tfi_status rc = plan->alloc(&plan->pipe_out[k], cap)) return rc;
+        }
+        TFI_CUDA(cudaStreamCreateWithFlags(&plan->pipe_cin, cudaStreamNonBlocking));
+        TFI_CUDA(cudaStreamCreateWithFlags(&plan->pipe_cout, cudaStreamNonBlocking));
+        for (cudaEvent_t *e : {&plan->ev_in_ready[0], &plan->ev_in_ready[1], &plan->ev_in_free[0], &plan->ev_in_free[1],
+                               &plan->ev_out_ready[0], &plan->ev_out_ready[1], &plan->ev_out_free[0],
+                               &plan->ev_out_free[1]})
+            TFI_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    if (tfi_status rc = check_apply_args(plan, plan->pipe_in[0], plan->pipe_out[0], d, dtype)) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = size_t(plan->hp.n) * size_t(d) * (dtype == TFI_DTYPE_BF16 ? 2 : 4);
+    // the copy streams start after the work already queued on the caller's stream
+    TFI_CUDA(cudaEventRecord(plan->ev_fork, s));
+    TFI_CUDA(cudaStreamWaitEvent(plan->pipe_cin, plan->ev_fork, 0));
+    TFI_CUDA(cudaStreamWaitEvent(plan->pipe_cout, plan->ev_fork, 0));
+    for (int32_t i = 0; i < n_fields; ++i) {
+        const int k = i & 1;
+        // copy-in: slot k's input is free once the apply of field i - 2 has read it
+        if (i >= 2) TFI_CUDA(cudaStreamWaitEvent(plan->pipe_cin, plan->ev_in_free[k], 0));
+        TFI_CUDA(cudaMemcpyAsync(plan->pipe_in[k], F_host[i], bytes, cudaMemcpyHostToDevice, plan->pipe_cin));
+        TFI_CUDA(cudaEventRecord(plan->ev_in_ready[k], plan->pipe_cin));
+        // apply on the caller's stream once the input has arrived and slot k's output of field i - 2
+        // has been copied out
+        TFI_CUDA(cudaStreamWaitEvent(s, plan->ev_in_ready[k], 0));
+        if (i >= 2) TFI_CUDA(cudaStreamWaitEvent(s, plan->ev_out_free[k], 0));
+        if (tfi_status rc = tfi_apply(plan, plan->pipe_in[k], plan->pipe_out[k], d, dtype, stream)) return rc;
+        TFI_CUDA(cudaEventRecord(plan->ev_in_free[k], s));
+        TFI_CUDA(cudaEventRecord(plan->ev_out_ready[k], s));
+        // copy-out
+        TFI_CUDA(cudaStreamWaitEvent(plan->pipe_cout, plan->ev_out_ready[k], 0));
+        TFI_CUDA(cudaMemcpyAsync(out_host[i], plan->pipe_out[k], bytes, cudaMemcpyDeviceToHost, plan->pipe_cout));
+        TFI_CUDA(cudaEventRecord(plan->ev_out_free[k], plan->pipe_cout));
+    }
+    TFI_CUDA(cudaStreamSynchronize(plan->pipe_cout));
+    TFI_CUDA(cudaStreamSynchronize(plan->pipe_cin));
     TFI_CUDA(cudaStreamSynchronize(s));
     return TFI_OK;
 }

@@ -208,6 +208,28 @@ def test_autograd_function():
     assert _err(x.grad.cpu().numpy(), ref) <= TOL["f32"]
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_apply_host_many_pipelined(pinned, dtype):
+    # five independent host fields (the two staging slots are each reused), pinned and pageable,
+    # against the oracle on the same (dtype-rounded) inputs
+    t = _rrt(3000, 8)
+    spec = W.KernelSpec.rational(0.05, e=1.0, p=2.0)
+    d = 8
+    p = tfi.Plan.from_spec(t, 1.0, spec, leaf_max=64, max_channels=d)
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    code = tfi.DTYPE_F32 if dtype == "f32" else tfi.DTYPE_BF16
+    ins = [torch.from_numpy(W.normal_field(t.n, d, seed=40 + i)).to(tdt) for i in range(5)]
+    outs = [torch.full_like(x, float("nan")) for x in ins]
+    if pinned:
+        ins = [x.pin_memory() for x in ins]
+        outs = [y.pin_memory() for y in outs]
+    p.apply_host_many([x.data_ptr() for x in ins], [y.data_ptr() for y in outs], d, code)
+    for x, y in zip(ins, outs):
+        ref = brute.integrate(t, 1.0, spec, x.double().numpy())
+        assert _err(y.double().numpy(), ref) <= TOL[dtype]
+
+
 def test_apply_host_matches_device():
     t = _rrt(2500, 8)
     p = tfi.Plan.from_spec(t, 1.0, W.KernelSpec.exp(0.2), leaf_max=64, max_channels=16)
