@@ -115,6 +115,12 @@ typedef struct {
                                    up to 2^25 points with a backbone axis of at most 2^13) is evaluated
                                    by the four-step FFT through global memory, whatever the cost model
                                    prefers (by default it competes with direct summation) */
+#define TFI_PLAN_NO_TRUNCATE 128 /* keep every table whole. By default, when every FP32 sample f(k delta) from
+                                   some distance T up to the largest one a table can pair is zero, bins at
+                                   depth >= T (which then neither contribute nor receive anything) are left
+                                   out of their tables and their table values set to zero: exact for the
+                                   sampled kernel, and the tables shrink to depths below T. Not applied
+                                   with TFI_PLAN_SWEEP / TFI_PLAN_SWEEP_AUTO */
 #define TFI_PLAN_LEAF_ALU   16  /* dense leaves on the FP32 ALUs for every d (by default BF16 applies
                                    with d >= 64 sum leaves as f(D) x F products on the tensor cores:
                                    tcgen05 kind::tf32, f(D) split into hi + lo; FP32 applies always
@@ -282,7 +288,10 @@ tfi_status tfi_kernel_grad(tfi_plan_t plan, const void *grad_out, const void *F,
  * learnable parameters): same kind and number of parameters (or, for
  * TFI_F_TABLE, a table at least as long as the plan needs). Recomputes the
  * FP32 samples and the FP64 spectra on the host and copies them into the
- * plan's device buffers (synchronous; no allocation). */
+ * plan's device buffers (synchronous; no allocation). A plan whose tables were
+ * truncated (tfi_plan_info.trunc_len >= 0) takes only kernels whose FP32 samples
+ * are zero from trunc_len on; others return TFI_ERR_UNSUPPORTED (plan again, or
+ * plan with TFI_PLAN_NO_TRUNCATE). */
 tfi_status tfi_set_kernel(tfi_plan_t plan, const tfi_kernel *kernel);
 
 /* Failure-detection self-test of the bounded device wait (no counterpart in the
@@ -328,6 +337,8 @@ typedef struct {
     int64_t n_jobs_fft_big; /* tables beyond one CTA's shared memory evaluated by the four-step FFT through
                                global memory (P1 P2 > 2^14 points) */
     int64_t sum_fft_big_points; /* sum over those tables of P1*P2 */
+    int64_t trunc_len;      /* T of TFI_PLAN_NO_TRUNCATE's truncation (grid units), or -1 when no table was cut */
+    int64_t n_zero_bins;    /* bins left out of their tables by that truncation (their values are zero) */
 } tfi_plan_info;
 tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
 

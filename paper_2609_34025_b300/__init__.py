@@ -57,7 +57,8 @@ class _Info(ctypes.Structure):
         "n_centroid", "sum_table", "sum_fft_points", "sum_leaf_pairs", "ftab_len", "device_bytes")] + [
         ("plan_seconds", ctypes.c_double), ("device_keys_ms", ctypes.c_double), ("n_jobs_sweep", ctypes.c_int64),
         ("hist_len", ctypes.c_int64), ("n_jobs_hankel", ctypes.c_int64), ("device_errors", ctypes.c_int64),
-        ("n_jobs_fft_big", ctypes.c_int64), ("sum_fft_big_points", ctypes.c_int64)]
+        ("n_jobs_fft_big", ctypes.c_int64), ("sum_fft_big_points", ctypes.c_int64), ("trunc_len", ctypes.c_int64),
+        ("n_zero_bins", ctypes.c_int64)]
 
 
 EXPORTED_SYMBOLS = ("tfi_plan", "tfi_apply", "tfi_apply_backward", "tfi_apply_host", "tfi_destroy",
@@ -133,7 +134,7 @@ class Plan:
 
     def __init__(self, n, u, v, w, delta=1.0, kernel=("expsum", [1.0, 1.0]), table=None, policy="adaptive",
                  leaf_max=64, max_channels=16, host_only=False, sweep=False, hankel=None, leaf_alu=False,
-                 fft_big_all=False, fft_cta_points=0):
+                 fft_big_all=False, fft_cta_points=0, truncate=True):
         u = np.ascontiguousarray(u, dtype=np.int32)
         v = np.ascontiguousarray(v, dtype=np.int32)
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -145,7 +146,7 @@ class Plan:
                       0 if tab is None else int(tab.shape[0]), None if tab is None else tab.ctypes.data)
         opt = _Options(float(delta), POLICIES[policy], int(leaf_max), int(max_channels),
                        (1 if host_only else 0) | SWEEP_MODES[sweep] | HANKEL_MODES[hankel] | (16 if leaf_alu else 0)
-                       | (64 if fft_big_all else 0), int(fft_cta_points))
+                       | (64 if fft_big_all else 0) | (0 if truncate else 128), int(fft_cta_points))
         h = ctypes.c_void_p()
         _check(lib().tfi_plan(ctypes.byref(tree), ctypes.byref(ker), ctypes.byref(opt), ctypes.byref(h)))
         self._h = h

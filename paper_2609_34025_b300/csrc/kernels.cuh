@@ -1186,6 +1186,16 @@ __global__ void sinkhorn_scale(int64_t n, const float *__restrict__ marg, const 
         out[i] = marg[i] / (Kx[i] + delta);
 }
 
+// Table values of the bins a support truncation left out of their tables: zero rows
+// [ranges[2i], ranges[2i + 1]) of vbuf, one CTA row per range.
+__global__ void zero_rows(const int32_t *__restrict__ ranges, int n_ranges, int d, float *__restrict__ vbuf) {
+    for (int r = blockIdx.y; r < n_ranges; r += gridDim.y) {
+        const int64_t b = int64_t(ranges[2 * r]) * d, e = int64_t(ranges[2 * r + 1]) * d;
+        for (int64_t i = b + blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < e; i += int64_t(gridDim.x) * blockDim.x)
+            vbuf[i] = 0.f;
+    }
+}
+
 __global__ void fill_value(int64_t n, float v, float *__restrict__ out) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
         out[i] = v;

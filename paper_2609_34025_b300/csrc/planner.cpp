@@ -557,6 +557,25 @@ double hankel_cost(int32_t H, int32_t L, double ncols, double nk, int d) {
 }
 
 
+// 1 + the largest k < len whose FP32 sample float(f(k delta)) is not zero (0 if none): every
+// sample from there to len - 1 is zero. Scanned downwards in chunks on all host threads.
+int64_t fp32_support(const KernelFn &f, double delta, int64_t len) {
+    constexpr int64_t kChunk = int64_t(1) << 16;
+    const size_t nch = size_t((len + kChunk - 1) / kChunk);
+    std::vector<int64_t> last(nch, -1);
+    parallel_for(nch, [&](size_t c) {
+        const int64_t lo = int64_t(c) * kChunk, hi = std::min(len, lo + kChunk);
+        for (int64_t k = hi - 1; k >= lo; --k)
+            if (float(f.grid(k, delta)) != 0.f) {
+                last[c] = k;
+                return;
+            }
+    });
+    for (size_t c = nch; c-- > 0;)
+        if (last[c] >= 0) return last[c] + 1;
+    return 0;
+}
+
 // Bins of one call: its A-bins (distinct (depth, coordinate)) and each
 // component's b-bins (distinct depth), members ascending by vertex id.
 struct CallBins {
@@ -628,6 +647,10 @@ int sample_kernel(HostPlan &hp, std::string &err) {
     if (hp.f.kind == TFI_F_TABLE && hp.hist_len > int64_t(hp.f.table.size())) {
         err = "sampled kernel table shorter than the largest grid distance the plan needs";
         return TFI_ERR_GRID_OVERFLOW;
+    }
+    if (hp.trunc >= 0 && fp32_support(hp.f, hp.delta, hp.trunc_check) > hp.trunc) {
+        err = "the kernel's FP32 samples reach beyond the distance at which the plan truncated its tables; plan again";
+        return TFI_ERR_UNSUPPORTED;
     }
     hp.ftab.resize(size_t(hp.ftab_len));
     for (int64_t k = 0; k < hp.ftab_len; ++k) hp.ftab[size_t(k)] = float(hp.f.grid(k, hp.delta));
@@ -725,6 +748,21 @@ int flatten(HostPlan &hp, const std::vector<int32_t> &roots, std::string &err) {
         err = "plan too large for 32-bit bin indices";
         return TFI_ERR_UNSUPPORTED;
     }
+    // support truncation (not with the exponential sweeps, whose jobs span whole calls)
+    hp.trunc = -1;
+    hp.zero_ranges.clear();
+    hp.jobs_full.clear();
+    {
+        int64_t need_calls = 0;
+        for (const Call &c : hp.calls) need_calls = std::max<int64_t>(need_calls, 2 * c.H + c.L);
+        hp.trunc_check = need_calls + 1;
+        if (!(hp.flags & (TFI_PLAN_SWEEP | TFI_PLAN_SWEEP_AUTO | TFI_PLAN_NO_TRUNCATE)) && !hp.calls.empty()) {
+            const int64_t T = fp32_support(hp.f, hp.delta, hp.trunc_check);
+            if (T < hp.trunc_check) hp.trunc = T;
+        }
+    }
+    std::vector<std::vector<int32_t>> call_zero(hp.trunc >= 0 ? C : 0);
+    if (hp.trunc >= 0) hp.jobs_full.resize(size_t(joff[C]));
     hp.key_r.resize(size_t(koff[C]));
     hp.key_x.resize(size_t(koff[C]));
     hp.key_ptr.resize(size_t(koff[C]) + 1);
@@ -752,6 +790,22 @@ int flatten(HostPlan &hp, const std::vector<int32_t> &roots, std::string &err) {
             jb.kb = koff[c] + cb.jobs[j].first;
             jb.ke = koff[c] + cb.jobs[j].second;
             jb.is_comp = j > 0 ? 1 : 0;
+            if (hp.trunc >= 0) {
+                // the untruncated job (for the kernel gradient), then the cut: bins ascend in depth,
+                // and those at depth >= trunc only read zero samples
+                Job full = jb;
+                for (int64_t k = full.kb; k < full.ke; ++k) {
+                    full.maxr = std::max(full.maxr, hp.key_r[size_t(k)]);
+                    full.maxx = std::max(full.maxx, hp.key_x[size_t(k)]);
+                }
+                full.lp1 = ceil_log2(2 * int64_t(full.maxr) + 1);
+                full.lp2 = full.maxx > 0 ? ceil_log2(2 * int64_t(full.maxx)) : 0;
+                hp.jobs_full[size_t(joff[c]) + j] = full;
+                int64_t cut = jb.kb;
+                while (cut < jb.ke && hp.key_r[size_t(cut)] < hp.trunc) ++cut;
+                if (cut < jb.ke) call_zero[c].insert(call_zero[c].end(), {int32_t(cut), int32_t(jb.ke)});
+                jb.ke = cut;
+            }
             int32_t maxr = 0, maxx = 0;
             for (int64_t k = jb.kb; k < jb.ke; ++k) {
                 maxr = std::max(maxr, hp.key_r[size_t(k)]);
@@ -801,6 +855,12 @@ int flatten(HostPlan &hp, const std::vector<int32_t> &roots, std::string &err) {
         CallBins().kr.swap(cb.kr);
         cb = CallBins();
     });
+    for (const std::vector<int32_t> &z : call_zero) hp.zero_ranges.insert(hp.zero_ranges.end(), z.begin(), z.end());
+    if (hp.zero_ranges.empty()) {
+        // no bin lies beyond the support: the tables are whole, and any kernel may replace f later
+        hp.trunc = -1;
+        hp.jobs_full.clear();
+    }
     if (hp.flags & TFI_PLAN_SWEEP) {
         // Algorithm 7 for every table
         for (Job &j : hp.jobs) j.mode = 2;
@@ -944,6 +1004,7 @@ int flatten(HostPlan &hp, const std::vector<int32_t> &roots, std::string &err) {
         need_any = std::max(need_any, top);
         if (j.mode == 1 || j.mode == 3) need = std::max(need, top);
     }
+    for (const Job &j : hp.jobs_full) need_any = std::max<int64_t>(need_any, 2 * int64_t(j.maxr) + j.maxx);
     hp.ftab_len = need + 1;
     hp.leaf_ftab_len = need_leaf + 1;
     hp.hist_len = std::max(need_any, need_leaf) + 1;

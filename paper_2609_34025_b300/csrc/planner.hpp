@@ -109,6 +109,13 @@ struct HostPlan {
     int64_t ftab_len = 0;
     int64_t leaf_ftab_len = 1;                             // samples a dense leaf reads: its largest diameter + 1
     int64_t hist_len = 0;                                  // 1 + largest grid distance any pair of a call can have
+    // support truncation: every FP32 sample f(k delta) with trunc <= k < trunc_check is zero, so bins at
+    // depth >= trunc neither contribute nor receive anything; their table values are zeroed (zero_ranges:
+    // [begin, end) key ranges) and the jobs end before them. trunc = -1: no truncation. jobs_full keeps
+    // the untruncated jobs (the kernel gradient counts pairs at every distance).
+    int64_t trunc = -1, trunc_check = 0;
+    std::vector<int32_t> zero_ranges;
+    std::vector<Job> jobs_full;
     std::vector<float> ftab;
     // FFT spectra per (lp1, lp2) class, bit-reversed order, scaled by 1/(P1 P2), interleaved re/im
     std::vector<int64_t> spec_class_off;                   // [lp1 * 32 + lp2] -> offset in floats (complex = 2)

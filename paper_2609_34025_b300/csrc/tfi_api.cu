@@ -152,6 +152,9 @@ struct tfi_plan_s {
     tfi::dev::DirItem *st_dir = nullptr;
     int32_t n_st_dir = 0;
     int32_t *st_fft_job = nullptr;
+    // support truncation: key ranges whose table values are zero
+    int32_t *zero_ranges = nullptr;
+    int32_t n_zero_ranges = 0;
     std::vector<int> st_cls_lnp;
     std::vector<int32_t> st_cls_joff, st_cls_njobs;
     // fork/join inside an apply: leaf terms and direct jobs run on their own
@@ -642,6 +645,11 @@ struct StageMark {
     }
 };
 
+void launch_zero_rows(tfi_plan_t p, float *vbuf, int d, cudaStream_t s) {
+    const unsigned gy = unsigned(std::min<int32_t>(p->n_zero_ranges, 65535));
+    tfi::dev::zero_rows<<<dim3(4, gy), 256, 0, s>>>(p->zero_ranges, p->n_zero_ranges, d, vbuf);
+}
+
 template <typename T>
 tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     struct ApplyRange {  // the whole apply as one NVTX range
@@ -666,6 +674,8 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
         m_bucket.done(p->n_multi > 0 ? 2 : 1);
         TFI_CUDA(cudaEventRecord(p->ev_bucket, s_crit));
     }
+    // bins cut from their tables by the support truncation: zero values (no inputs needed)
+    if (p->n_zero_ranges > 0) launch_zero_rows(p, p->vbuf, d, s_leaf);
     // (a7) dense leaves -> lbuf, on the low-priority leaf stream
     StageMark m_leaf(p, s_leaf, TFI_STAGE_LEAF);
     launch_leaves(p, F, d, s_leaf);
@@ -923,6 +933,8 @@ tfi_status upload_plan(tfi_plan_t p) {
     for (const tfi::Job &jb : hp.jobs) p->n_hankel += jb.mode == 3;
     p->n_big_jobs = 0;
     for (const tfi::Job &jb : hp.jobs) p->n_big_jobs += jb.mode == 4;
+    if (tfi_status rc = p->upload(&p->zero_ranges, hp.zero_ranges)) return rc;
+    p->n_zero_ranges = int32_t(hp.zero_ranges.size() / 2);
     if (p->n_big_jobs > 0) {
         std::vector<float2> hi(8192), lo(8192);
         for (int j = 0; j < 8192; ++j) {
@@ -1153,6 +1165,7 @@ tfi_status apply_static_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream
     auto *d_fft = reinterpret_cast<tfi::dev::FftItem *>(base + o_f);
     // every workspace value an apply reads is written earlier in the same apply,
     // so nothing needs clearing between calls
+    if (p->n_zero_ranges > 0) launch_zero_rows(p, vbuf, d, s);
     if (p->n_groups > 0) launch_leaf<16>(p, F, lbuf, d, s);
     if (K > 0) {
         tfi::dev::bucket_kernel<T, 1><<<grid_for(int64_t(K) * d, 256), 256, 0, s>>>(int64_t(K), p->key_ptr, p->key_vtx,
@@ -1332,6 +1345,8 @@ tfi_status dense_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
 tfi_status build_grad(tfi_plan_t p) {
     if (p->grad_ready) return TFI_OK;
     const tfi::HostPlan &hp = p->hp;
+    // the gradient counts pairs at every distance: the jobs before any support truncation
+    const std::vector<tfi::Job> &gjobs = hp.jobs_full.empty() ? hp.jobs : hp.jobs_full;
     std::vector<tfi::grad::GradJob> gj;
     std::vector<int64_t> seg_off;
     std::vector<int32_t> seg_len;
@@ -1342,7 +1357,7 @@ tfi_status build_grad(tfi_plan_t p) {
     const int64_t ncb_max = (hp.max_channels + tfi::grad::kGradDotCB - 1) / tfi::grad::kGradDotCB;
     std::vector<int64_t> ditems;  // direct jobs: (job << 16 | row tile << 8 | column tile) items
     std::vector<int32_t> djobs;   // and the direct jobs' indices
-    for (const tfi::Job &j : hp.jobs) {
+    for (const tfi::Job &j : gjobs) {
         if (j.ke == j.kb) continue;
         const int32_t len = 2 * j.maxr + j.maxx + 1;
         // direct evaluation (pair dot products over the channels, then binning) when it is cheaper
@@ -2036,6 +2051,8 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info) {
     info->plan_seconds = hp.plan_seconds;
     info->device_keys_ms = plan->device_keys_ms;
     info->hist_len = hp.hist_len;
+    info->trunc_len = hp.trunc;
+    for (size_t r = 0; r + 1 < hp.zero_ranges.size(); r += 2) info->n_zero_bins += hp.zero_ranges[r + 1] - hp.zero_ranges[r];
     if (plan->hk_err) {
         int32_t v[3] = {0, 0, 0};
         TFI_CUDA(cudaMemcpy(v, plan->hk_err, 12, cudaMemcpyDeviceToHost));

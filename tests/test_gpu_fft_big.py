@@ -35,9 +35,10 @@ def _apply(p, F):
 @pytest.mark.parametrize("kernel", ["cauchy", "exp", "gauss"])
 @pytest.mark.parametrize("d", [1, 3, 16])
 def test_caterpillar_2p14_all_outputs(kernel, d):
+    # whole tables (no support truncation, which would shrink the exp and gauss tables below 2^14)
     cfg = W.configs.sweep(shape="caterpillar", n=1 << 14, d=d, kernel=kernel)
     t = cfg["tree"]
-    p = tfi.Plan.from_spec(t, cfg["delta"], cfg["kernel"], leaf_max=64, max_channels=d)
+    p = tfi.Plan.from_spec(t, cfg["delta"], cfg["kernel"], leaf_max=64, max_channels=d, truncate=False)
     assert p.info()["n_jobs_fft_big"] > 0
     F = W.normal_field(t.n, d, seed=123)
     y = _apply(p, F)
@@ -89,7 +90,8 @@ def test_caterpillar_2p19_stratified_batches_and_adjoint():
 def test_graph_replay_with_big_tables():
     cfg = W.configs.sweep(shape="caterpillar", n=1 << 14, d=8, kernel="exp")
     t = cfg["tree"]
-    p = tfi.Plan.from_spec(t, cfg["delta"], cfg["kernel"], leaf_max=64, max_channels=8)
+    p = tfi.Plan.from_spec(t, cfg["delta"], cfg["kernel"], leaf_max=64, max_channels=8, truncate=False)
+    assert p.info()["n_jobs_fft_big"] > 0
     x = torch.from_numpy(W.normal_field(t.n, 8, seed=3)).cuda()
     z = torch.from_numpy(W.normal_field(t.n, 8, seed=4)).cuda()
     out, gF = torch.empty_like(x), torch.empty_like(x)
