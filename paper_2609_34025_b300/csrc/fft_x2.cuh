@@ -274,9 +274,11 @@ __device__ __forceinline__ void fft_axis_x2(ulonglong2 *Z, int NP, int nplane, i
 
 // Span-1 pass of the innermost axis, forward and inverse, with the product by
 // the kernel spectrum (one spectrum value per point, shared by both pairs).
+// s_plane: offset between the spectra of consecutive planes (0: one spectrum for all)
 template <int RL>
 __device__ __forceinline__ void fused_bottom_pass_x2(ulonglong2 *Z, int NP, int nplane, int ln, int es, int llog,
-                                                     int ls, bool line_fast, const float2 *__restrict__ S) {
+                                                     int ls, bool line_fast, const float2 *__restrict__ S,
+                                                     int s_plane) {
     constexpr int R = 1 << RL;
     const int glog = ln - RL;
     const int total = nplane << (llog + glog);
@@ -302,8 +304,9 @@ __device__ __forceinline__ void fused_bottom_pass_x2(ulonglong2 *Z, int NP, int 
             v[t] = Cx2{q.x, q.y};
         }
         dft_dif_x2<RL>(v);
+        const float2 *Sp = S + p * s_plane;
 #pragma unroll
-        for (int q = 0; q < R; ++q) v[q] = cx_mul(v[q], cx_bcast(__ldg(S + e0 + q * es)));
+        for (int q = 0; q < R; ++q) v[q] = cx_mul(v[q], cx_bcast(__ldg(Sp + e0 + q * es)));
         idft_dit_x2<RL>(v);
 #pragma unroll
         for (int t = 0; t < R; ++t) Zp[adr[t]] = make_ulonglong2(v[t].re, v[t].im);
@@ -312,12 +315,12 @@ __device__ __forceinline__ void fused_bottom_pass_x2(ulonglong2 *Z, int NP, int 
 }
 
 __device__ __forceinline__ void fused_bottom_x2(ulonglong2 *Z, int NP, int nplane, int ln, int es, int llog, int ls,
-                                                bool line_fast, const float2 *__restrict__ S) {
+                                                bool line_fast, const float2 *__restrict__ S, int s_plane = 0) {
     const int full = ln / 3, rem = ln - 3 * full;
     const int rl = full > 0 ? 3 : rem;
-    if (rl == 3) fused_bottom_pass_x2<3>(Z, NP, nplane, ln, es, llog, ls, line_fast, S);
-    else if (rl == 2) fused_bottom_pass_x2<2>(Z, NP, nplane, ln, es, llog, ls, line_fast, S);
-    else fused_bottom_pass_x2<1>(Z, NP, nplane, ln, es, llog, ls, line_fast, S);
+    if (rl == 3) fused_bottom_pass_x2<3>(Z, NP, nplane, ln, es, llog, ls, line_fast, S, s_plane);
+    else if (rl == 2) fused_bottom_pass_x2<2>(Z, NP, nplane, ln, es, llog, ls, line_fast, S, s_plane);
+    else fused_bottom_pass_x2<1>(Z, NP, nplane, ln, es, llog, ls, line_fast, S, s_plane);
 }
 
 // ---------------------------------------------------------------------------
@@ -406,7 +409,7 @@ __device__ __forceinline__ void pass_1d_dispatch(ulonglong2 *Z, int NP, int npla
 // span-1 pass with the spectrum product
 template <int RL>
 __device__ __forceinline__ void bottom_1d_x2(ulonglong2 *Z, int NP, int nplane, int ln,
-                                             const float2 *__restrict__ S) {
+                                             const float2 *__restrict__ S, int s_plane) {
     constexpr int R = 1 << RL;
     const int glog = ln - RL;
     const int total = nplane << glog;
@@ -424,8 +427,9 @@ __device__ __forceinline__ void bottom_1d_x2(ulonglong2 *Z, int NP, int nplane, 
             v[t] = Cx2{q.x, q.y};
         }
         dft_dif_x2<RL>(v);
+        const float2 *Sp = S + p * s_plane;
 #pragma unroll
-        for (int q = 0; q < R; ++q) v[q] = cx_mul(v[q], cx_bcast(__ldg(S + e0 + q)));
+        for (int q = 0; q < R; ++q) v[q] = cx_mul(v[q], cx_bcast(__ldg(Sp + e0 + q)));
         idft_dit_x2<RL>(v);
 #pragma unroll
         for (int t = 0; t < R; ++t) Zp[adr[t]] = make_ulonglong2(v[t].re, v[t].im);
@@ -433,22 +437,24 @@ __device__ __forceinline__ void bottom_1d_x2(ulonglong2 *Z, int NP, int nplane, 
     __syncthreads();
 }
 
-// forward transform, spectrum product and inverse of a 2^ln-point table (ln >= 1)
+// forward transform, spectrum product and inverse of a 2^ln-point table (ln >= 1); s_plane as in
+// fused_bottom_pass_x2
 __device__ __forceinline__ void fft_1d_x2(ulonglong2 *Z, int NP, int nplane, int ln, const float2 *__restrict__ tw,
-                                          const ulonglong2 *__restrict__ twb, const float2 *__restrict__ S) {
+                                          const ulonglong2 *__restrict__ twb, const float2 *__restrict__ S,
+                                          int s_plane = 0) {
     const int full = ln / 3, rem = ln - 3 * full;
     if (full > 0) {
         if (rem == 2) pass_1d_dispatch<false, 2>(Z, NP, nplane, ln, ln - 2, tw, twb);
         else if (rem == 1) pass_1d_dispatch<false, 1>(Z, NP, nplane, ln, ln - 1, tw, twb);
         for (int k = 0; k < full - 1; ++k) pass_1d_dispatch<false, 3>(Z, NP, nplane, ln, ln - rem - 3 * (k + 1), tw, twb);
-        bottom_1d_x2<3>(Z, NP, nplane, ln, S);
+        bottom_1d_x2<3>(Z, NP, nplane, ln, S, s_plane);
         for (int k = full - 2; k >= 0; --k) pass_1d_dispatch<true, 3>(Z, NP, nplane, ln, ln - rem - 3 * (k + 1), tw, twb);
         if (rem == 2) pass_1d_dispatch<true, 2>(Z, NP, nplane, ln, ln - 2, tw, twb);
         else if (rem == 1) pass_1d_dispatch<true, 1>(Z, NP, nplane, ln, ln - 1, tw, twb);
     } else if (rem == 2) {
-        bottom_1d_x2<2>(Z, NP, nplane, ln, S);
+        bottom_1d_x2<2>(Z, NP, nplane, ln, S, s_plane);
     } else {
-        bottom_1d_x2<1>(Z, NP, nplane, ln, S);
+        bottom_1d_x2<1>(Z, NP, nplane, ln, S, s_plane);
     }
 }
 

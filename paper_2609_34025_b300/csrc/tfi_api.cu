@@ -63,7 +63,7 @@ struct WorkLists {
     };
     tfi::dev::BigItem *d_big = nullptr;
     std::vector<std::vector<BigSeg>> big_batches;
-    int64_t big_elems = 0;  // buffer elements (complex) the largest batch needs
+    int64_t big_elems = 0;  // buffer elements (16 bytes: two channel pairs) the largest batch needs
 };
 
 constexpr int64_t kBigBatchBytes = int64_t(4) << 30;  // four-step FFT buffer of a plan, at most
@@ -98,7 +98,8 @@ struct tfi_plan_s {
     float *kbuf = nullptr, *vbuf = nullptr, *lbuf = nullptr;
     // four-step FFT tables: the buffer of one batch (grown on demand by build_work) and the two
     // twiddle tables exp(-2 pi i j / 2^13), exp(-2 pi i j / 2^26), j < 2^13
-    float2 *big_buf = nullptr, *big_tw_hi = nullptr, *big_tw_lo = nullptr;
+    ulonglong2 *big_buf = nullptr;  // 16-byte elements: one point of two channel pairs
+    float2 *big_tw_hi = nullptr, *big_tw_lo = nullptr;
     int64_t big_cap = 0;
     int32_t n_big_jobs = 0;
     // bin sums by segments of at most kBucketSeg members (see bucket_seg_kernel)
@@ -296,15 +297,16 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
         TFI_CUDA(cudaMemcpy(wl.d_hk, hk.data(), hk.size() * sizeof(hk[0]), cudaMemcpyHostToDevice));
     }
     {
-        // four-step FFT tables by size class, one item per channel pair, in batches whose arrays fit
-        // kBigBatchBytes (and 65535 items: the grid rows of the scatter / gather launches)
+        // four-step FFT tables by size class, one item per plane of four channels, in batches whose
+        // arrays fit kBigBatchBytes (and 65535 items: the grid rows of the scatter / gather launches)
         std::map<int, std::vector<int32_t>> big_cls;
         for (size_t j = 0; j < jobs.size(); ++j)
             if (jobs[j].mode == 4 && jobs[j].ke > jobs[j].kb) big_cls[jobs[j].lp1 * 32 + jobs[j].lp2].push_back(int32_t(j));
         std::vector<tfi::dev::BigItem> items;
         std::vector<WorkLists::BigSeg> cur;
         int64_t used = 0, first = 0;
-        const int64_t cap = kBigBatchBytes / int64_t(sizeof(float2));
+        const int64_t cap = kBigBatchBytes / int64_t(sizeof(ulonglong2));
+        const int planes = (d + 3) / 4;
         for (auto &kv : big_cls) {
             const int lp1 = kv.first / 32, lp2 = kv.first % 32;
             const tfi::BigSplit sp = tfi::big_split(lp1, lp2);
@@ -313,7 +315,7 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
             const int64_t spec = p->hp.spec_class_off[size_t(kv.first)] / 2;
             for (int32_t j : kv.second) {
                 const tfi::Job &jb = jobs[size_t(j)];
-                for (int pr = 0; pr < pairs; ++pr) {
+                for (int pr = 0; pr < planes; ++pr) {
                     if (!cur.empty() && (used + P > cap || int64_t(items.size()) - first >= 65535)) {
                         wl.big_batches.push_back(cur);
                         cur.clear();
@@ -339,15 +341,15 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
             // grow the plan's buffer (stream-ordered work on the old one has to finish first)
             TFI_CUDA(cudaDeviceSynchronize());
             cudaFree(p->big_buf);
-            p->dev_bytes -= p->big_cap * int64_t(sizeof(float2));
+            p->dev_bytes -= p->big_cap * int64_t(sizeof(ulonglong2));
             p->big_buf = nullptr;
             p->big_cap = 0;
-            if (cudaMalloc(&p->big_buf, size_t(wl.big_elems) * sizeof(float2)) != cudaSuccess) {
+            if (cudaMalloc(&p->big_buf, size_t(wl.big_elems) * sizeof(ulonglong2)) != cudaSuccess) {
                 cudaFree(wl.d_big);
                 return fail(TFI_ERR_OOM, "cudaMalloc failed for the four-step FFT buffer");
             }
             p->big_cap = wl.big_elems;
-            p->dev_bytes += p->big_cap * int64_t(sizeof(float2));
+            p->dev_bytes += p->big_cap * int64_t(sizeof(ulonglong2));
         }
     }
     auto res = p->work.emplace(d, wl);
@@ -365,17 +367,18 @@ void launch_big(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
             const tfi::dev::BigItem *it = wl.d_big + sg.i0;
             const int64_t BLK = int64_t(1) << (g.lp1b + g.lp2), NA = int64_t(1) << g.lnA;
             const int64_t P = BLK * NA;
-            const unsigned gz = unsigned(std::min<int64_t>(256, std::max<int64_t>(1, (P / 4 + BLK / 2 + 255) / 256)));
+            const unsigned gz = unsigned(std::min<int64_t>(256, std::max<int64_t>(1, (P / 2 + BLK + 255) / 256)));
             const unsigned gs = unsigned(std::min<int64_t>(64, std::max<int64_t>(1, (sg.max_nk + 255) / 256)));
             tfi::dev::big_zero<<<dim3(gz, n_it), 256, 0, s>>>(it, g, p->big_buf);
             tfi::dev::big_scatter<<<dim3(gs, n_it), 256, 0, s>>>(it, g, p->key_r, p->key_x, d, p->kbuf, p->big_buf);
             const int lcg = tfi::dev::big_lcg(g), lnb = tfi::dev::big_lnb(g);
-            const size_t smem_c = size_t(tfi::dev::padded_size(int(NA) << lcg)) * sizeof(float2);
-            const size_t smem_b = (size_t(tfi::dev::padded_size(int(BLK))) << lnb) * sizeof(float2);
+            const size_t smem_c = (size_t(NA) << lcg) * sizeof(ulonglong2);
+            const size_t smem_b = (size_t(BLK) << lnb) * sizeof(ulonglong2);
             const unsigned grid_c = unsigned(n_it * (BLK >> lcg)), grid_b = unsigned(n_it * (NA >> lnb));
             tfi::dev::big_columns<false><<<grid_c, 256, smem_c, s>>>(it, g, lcg, p->big_buf, p->twiddle, p->big_tw_hi,
                                                                     p->big_tw_lo);
             tfi::dev::big_blocks<<<grid_b, 256, smem_b, s>>>(it, int(n_it), g, lnb, p->big_buf, p->spectra, p->twiddle,
+                                                             reinterpret_cast<const ulonglong2 *>(p->twiddle_b),
                                                              p->big_tw_hi, p->big_tw_lo);
             tfi::dev::big_columns<true><<<grid_c, 256, smem_c, s>>>(it, g, lcg, p->big_buf, p->twiddle, p->big_tw_hi,
                                                                    p->big_tw_lo);
@@ -2122,8 +2125,9 @@ tfi_status tfi_stage_model(tfi_plan_t plan, int32_t d, int32_t dtype, double *by
             // two complex transforms and one complex product per channel pair
             flops[TFI_STAGE_FFT] += std::ceil(D / 2) * (2 * 5 * np * lg + 6 * np);
             // four-step tables also pass over their padded arrays in DRAM, per channel pair: the
-            // zeroed and read input half, two reads and writes of the whole, the stored output half
-            if (j.mode == 4) bytes[TFI_STAGE_FFT] += std::ceil(D / 2) * 5.5 * np * 8;
+            // zeroed and read input half, two reads and writes of the whole, the stored output half (per plane
+            // of four channels, 16 bytes a point)
+            if (j.mode == 4) bytes[TFI_STAGE_FFT] += std::ceil(D / 4) * 5.5 * np * 16;
         } else if (j.mode == 2) {
             // per term: lambda^r weighting in and out, two recurrences per backbone vertex
             bytes[TFI_STAGE_SWEEP] += nk * (2 * D * 4 + 8);
