@@ -310,8 +310,11 @@ def sweep_evaluator(a, cfg, F, G, steps=10):
 # ---------------------------------------------------------------------------
 # C2's other shapes, widths and kernels at the same N (fwd+bwd, L2 flushed)
 # ---------------------------------------------------------------------------
-C2_CASES = [("binary", 16, "exp"), ("caterpillar", 16, "exp"), ("rrt", 1, "exp"), ("rrt", 64, "exp"),
-            ("rrt", 16, "cauchy"), ("rrt", 16, "gauss")]
+# (shape, d, kernel, log2 N or None for the headline's N)
+C2_CASES = [("binary", 16, "exp", None), ("caterpillar", 16, "exp", None), ("caterpillar", 16, "cauchy", None),
+            ("caterpillar", 16, "gauss", None), ("binary", 16, "cauchy", None), ("rrt", 1, "exp", None),
+            ("rrt", 64, "exp", None), ("rrt", 16, "cauchy", None), ("rrt", 16, "gauss", None),
+            ("rrt", 16, "exp", 14), ("rrt", 16, "exp", 16), ("rrt", 16, "exp", 18)]
 
 
 def c2_sweep(a, steps=5):
@@ -322,8 +325,8 @@ def c2_sweep(a, steps=5):
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     rows = []
-    for shape, d, kern in C2_CASES:
-        cfg = W.configs.sweep(shape=shape, n=a.n, d=d, kernel=kern)
+    for shape, d, kern, lg in C2_CASES:
+        cfg = W.configs.sweep(shape=shape, n=a.n if lg is None else 1 << lg, d=d, kernel=kern)
         n = cfg["tree"].n
         t0 = time.perf_counter()
         plan = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=a.policy, leaf_max=a.leaf_max,
@@ -353,7 +356,8 @@ def c2_sweep(a, steps=5):
         rows.append({"workload": f"sweep_{shape}_n{n}_d{d}_{kern}_delta1/64", "shape": shape, "n": n, "d": d,
                      "kernel": kern, "value": n * d / (ms / 1e3), "ms_per_step": ms, "fwd_ms": fwd / steps,
                      "plan_seconds": round(plan_s, 3), "calls": info["n_calls"], "centroid_calls": info["n_centroid"],
-                     "jobs_fft": info["n_jobs_fft"], "jobs_direct": info["n_jobs_direct"],
+                     "jobs_fft": info["n_jobs_fft"], "jobs_fft_big": info["n_jobs_fft_big"],
+                     "jobs_direct": info["n_jobs_direct"], "trunc_len": info["trunc_len"],
                      "levels": info["n_levels"]})
         plan.close()
         del F, G, out, gF
