@@ -1,11 +1,14 @@
 """Sinkhorn workload: 50,000 points on a torus (R=1, r=0.3), symmetrised kNN
 (k=8) MST with Euclidean lengths on a 1/256 grid, 8 Dirichlet(1) marginal
 pairs (d = 8), f(x) = exp(-x/0.05), 200 iterations of two applies each, on
-the device (one captured iteration replayed). Reports time per iteration and
-checks the operator at full size on sampled targets against the FP64 oracle.
-Prints one JSON line.
+the device (one captured iteration replayed). Every table is summed directly
+(TFI_PLAN_DIRECT_ALL, tables cut at the kernel's FP32 support), which keeps each
+entry of K v accurate relative to itself, as the iteration at this eps needs;
+--fft lets the cost model pick FFT tables instead. Reports time per iteration,
+the marginal residuals and the transport costs, and checks the operator at full
+size on sampled targets against the FP64 oracle. Prints one JSON line.
 
-    python bench_sinkhorn.py [--n 50000] [--iters 200]
+    python bench_sinkhorn.py [--n 50000] [--iters 200] [--fft | --sweep]
 """
 from __future__ import annotations
 
@@ -27,6 +30,9 @@ def main():
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sweep", action="store_true", help="Algorithm 7 sweeps instead of FFT tables")
+    ap.add_argument("--fft", action="store_true",
+                    help="let the cost model pick FFT tables (faster per iteration; at eps = 0.05 the FFT's "
+                         "normwise accuracy does not carry the iteration)")
     a = ap.parse_args()
     import torch
 
@@ -41,7 +47,9 @@ def main():
     am, bm = W.dirichlet_pairs(t.n, 8, seed=1)
     A, B = torch.from_numpy(am).cuda(), torch.from_numpy(bm).cuda()
     t0 = time.perf_counter()
-    plan = tfi.Plan.from_spec(t, delta, cfg["kernel"], leaf_max=256, max_channels=8, sweep=a.sweep)
+    direct = not a.fft and not a.sweep
+    plan = tfi.Plan.from_spec(t, delta, cfg["kernel"], leaf_max=256, max_channels=8, sweep=a.sweep,
+                              direct_all=direct)
     plan_s = time.perf_counter() - t0
     plan.sinkhorn(A, B, iters=2)
     times = []
@@ -61,13 +69,16 @@ def main():
     op_err = float((np.abs(kvs - ref).max(0) / np.abs(ref).max(0)).max())
     res_a = float((u * kv - A).abs().max() / A.abs().max())
     res_b = float((v * ku - B).abs().max() / B.abs().max())
-    plan2 = tfi.Plan.from_spec(t, delta, W.KernelSpec.powexp(1.0 / eps), leaf_max=256, max_channels=8)
+    plan2 = tfi.Plan.from_spec(t, delta, W.KernelSpec.powexp(1.0 / eps), leaf_max=256, max_channels=8,
+                               direct_all=direct)
     cost = (u.double() * plan2.apply(v).double()).sum(0).cpu().numpy()
     info = plan.info()
     line = {"metric": "Sinkhorn iterations/s (2 applies each), d=8 marginal pairs", "value": a.iters / best,
             "unit": "iterations/s", "ms_per_iteration": 1e3 * best / a.iters, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"torus_sinkhorn_n{t.n}", "n": t.n, "pairs": 8, "delta": delta, "eps": eps,
-                       "iters": a.iters, "leaf_max": 256, "evaluator": "sweep" if a.sweep else "fft/direct",
+                       "iters": a.iters, "leaf_max": 256,
+                       "evaluator": "sweep" if a.sweep else ("fft/direct" if a.fft else "direct"),
+                       "trunc_len": plan.info()["trunc_len"],
                        "plan_seconds": round(plan_s, 3),
                        "plan_calls": info["n_calls"], "plan_leaves": info["n_leaves"]},
             "vertex_channel_per_s": 2 * a.iters * t.n * 8 / best,

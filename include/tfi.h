@@ -121,6 +121,12 @@ typedef struct {
                                    out of their tables and their table values set to zero: exact for the
                                    sampled kernel, and the tables shrink to depths below T. Not applied
                                    with TFI_PLAN_SWEEP / TFI_PLAN_SWEEP_AUTO */
+#define TFI_PLAN_DIRECT_ALL 256 /* evaluate every table by direct summation (no FFT; Hankel and sweeps only if
+                                   their flags ask). Its sums are of the field's terms themselves, so for a
+                                   positive field and a decreasing kernel every output keeps a small error
+                                   relative to itself, where an FFT's error is relative to its whole table:
+                                   what Sinkhorn iterations at a small eps need (with the support truncation
+                                   keeping those tables short) */
 #define TFI_PLAN_LEAF_ALU   16  /* dense leaves on the FP32 ALUs for every d (by default BF16 applies
                                    with d >= 64 sum leaves as f(D) x F products on the tensor cores:
                                    tcgen05 kind::tf32, f(D) split into hi + lo; FP32 applies always
@@ -259,7 +265,9 @@ tfi_status tfi_graph_destroy(tfi_graph_t graph);
  * n x d FP32, one marginal pair per channel; u, v are overwritten with the
  * scalings (the plan is diag(u) K diag(v) per channel). One iteration is
  * captured once as a CUDA graph and replayed; the call synchronises `stream`.
- * The first call allocates an n x max_channels buffer for K x. */
+ * The first call allocates an n x max_channels buffer for K x. At a small eps the
+ * iteration divides by entries of K v far below their maximum; plan with
+ * TFI_PLAN_DIRECT_ALL then (FFT tables are accurate to their table's norm only). */
 tfi_status tfi_sinkhorn(tfi_plan_t plan, const float *a, const float *b, float *u, float *v, int32_t d, int32_t iters,
                         double delta_reg, tfi_stream_t stream);
 

@@ -819,12 +819,13 @@ int flatten(HostPlan &hp, const std::vector<int32_t> &roots, std::string &err) {
             const int lg = jb.lp1 + jb.lp2;
             const double np = std::ldexp(1.0, lg);
             const double cost_fft = kFftCostPerPointLog * np * std::max(1, lg) + kFftCostPerKey * nk;
-            const bool fft_ok = lg <= kFftMaxLog;
+            const bool fft_ok = lg <= kFftMaxLog && !(hp.flags & TFI_PLAN_DIRECT_ALL);
             jb.mode = (fft_ok && cost_fft < nk * nk) ? 0 : 1;
             double best = jb.mode == 0 ? cost_fft : nk * nk;
             // tables beyond shared memory: the four-step FFT through global memory, which also
             // pays for its passes over the whole padded table in DRAM
-            if (!fft_ok && lg <= kBigMaxLog && jb.lp2 <= kBigMaxInnerLog && jb.lp1 >= 1) {
+            if (!fft_ok && !(hp.flags & TFI_PLAN_DIRECT_ALL) && lg <= kBigMaxLog && jb.lp2 <= kBigMaxInnerLog &&
+                jb.lp1 >= 1) {
                 const double cost_big = kFftCostPerPointLog * np * lg + kBigCostPerPoint * np + kFftCostPerKey * nk;
                 if (cost_big < best || (hp.flags & TFI_PLAN_FFT_BIG_ALL)) {
                     jb.mode = 4;
