@@ -127,10 +127,15 @@ typedef struct {
                                    relative to itself, where an FFT's error is relative to its whole table:
                                    what Sinkhorn iterations at a small eps need (with the support truncation
                                    keeping those tables short) */
-#define TFI_PLAN_LEAF_ALU   16  /* dense leaves on the FP32 ALUs for every d (by default BF16 applies
-                                   with d >= 64 sum leaves as f(D) x F products on the tensor cores:
-                                   tcgen05 kind::tf32, f(D) split into hi + lo; FP32 applies always
-                                   use the FP32 ALUs, whose summation holds the 1e-4 bound) */
+#define TFI_PLAN_LEAF_ALU   16  /* dense leaves on the FP32 ALUs for every d. By default the leaves of
+                                   >= 64 vertices are f(D) x F products on the tensor cores (tcgen05
+                                   kind::tf32, f(D) split into hi + lo) for BF16 fields with d >= 64
+                                   and for FP32 fields with d >= 16 (F split too, three products, a
+                                   fresh accumulator for every 32 sources, added in FP32 registers:
+                                   within the 1e-4 bound); the rest on the FP32 ALUs */
+#define TFI_PLAN_LEAF_TC    512 /* FP32 fields: the tensor-core leaves for every d (by default only
+                                   from d = 16, below which the FP32 ALUs are faster). Ignored when
+                                   TFI_PLAN_LEAF_ALU is set. */
 
 typedef struct {
     double delta;           /* grid step > 0 */

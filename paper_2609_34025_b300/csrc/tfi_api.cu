@@ -20,6 +20,7 @@
 #include "grad.cuh"
 #include "hankel_tc.cuh"
 #include "leaf_tc.cuh"
+#include "leaf_tc32.cuh"
 #include "kernels.cuh"
 #include "fft_x2.cuh"
 #include "fft_big.cuh"
@@ -145,6 +146,8 @@ struct tfi_plan_s {
                                     // [2]: the last tfi_selftest_wait gave up
     tfi::tc::LeafTile *leaf_tiles = nullptr;  // 128-row tiles of the leaf groups (tensor-core leaves)
     int32_t n_leaf_tiles = 0;
+    int2 *leaf32 = nullptr;                 // leaves of >= kLeafWarpMin vertices as [lo, hi), largest first
+    int32_t n_leaf32 = 0, max_leaf32 = 1;   // (the FP32 tensor-core leaf kernel)
     std::map<int, WorkLists> work;  // per channel count d
     int32_t fft_cta_points = 1 << 13;  // tfi_options.fft_cta_points (0 there: this default)
     // tfi_apply_static: its work lists without per-call host copies. Direct items do not depend
@@ -471,11 +474,12 @@ void pack_big_leaves(const std::vector<int32_t> &lo, const std::vector<int32_t> 
 
 constexpr int kLeafFtabSmemMax = 12288;  // f samples staged in shared memory up to this many
 
+// big = false: only the small leaves (the big ones go to the tensor cores)
 template <int CH, typename T>
-void launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s) {
+void launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s, bool big = true) {
     // leaves look f up at their own pair distances only: stage that prefix of the samples
     const int fts = p->hp.leaf_ftab_len <= kLeafFtabSmemMax ? int(p->hp.leaf_ftab_len) : 0;
-    if (p->n_big > 0) {
+    if (big && p->n_big > 0) {
         const size_t smem = tfi::dev::leaf_warp_smem_bytes(p->max_big, CH, fts);
         dim3 grid(p->n_big, (d + CH - 1) / CH);
         auto k = fts > 0 ? tfi::dev::leaf_warp_kernel<T, CH, true> : tfi::dev::leaf_warp_kernel<T, CH, false>;
@@ -522,6 +526,31 @@ void launch_leaf_tc(tfi_plan_t p, const __nv_bfloat16 *F, float *lbuf, int d, cu
     else launch_leaf_tc_nb<B, 64>(p, F, lbuf, d, s);
 }
 
+// FP32 leaves of >= kLeafWarpMin vertices on the tensor cores: NB channels per CTA
+constexpr int kLeafTc32MinChannels = 16;  // FP32 fields: tensor-core big leaves from this d
+constexpr size_t kLeaf32SmemMax = 110 * 1024;  // two CTAs per SM (with the static and reserved bytes)
+
+template <int NB>
+void launch_leaf_tc32_nb(tfi_plan_t p, const float *F, float *lbuf, int d, cudaStream_t s) {
+    int fts = int(p->hp.leaf_ftab_len);
+    if (tfi::tc::leaf_tc32_layout(NB, p->max_leaf32, fts).bytes > kLeaf32SmemMax) fts = 0;
+    // at least a third of an SM's shared memory: the two CTAs that its tensor memory holds
+    // are all that share an SM, so none waits in tcgen05.alloc
+    const size_t smem = std::max(size_t(tfi::tc::leaf_tc32_layout(NB, p->max_leaf32, fts).bytes), size_t(80 * 1024));
+    // persistent: two CTAs per SM (their tensor memory), each over every gridDim.x-th leaf
+    dim3 grid(unsigned(std::min(p->n_leaf32, 2 * device_sms())), unsigned((d + NB - 1) / NB));
+    auto k = fts > 0 ? tfi::tc::leaf_tc32_kernel<NB, true> : tfi::tc::leaf_tc32_kernel<NB, false>;
+    k<<<grid, tfi::tc::kL32Threads, smem, s>>>(p->leaf32, p->n_leaf32, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, F, d, p->ftab, fts,
+                              p->max_leaf32, lbuf, p->hk_err + 1);
+}
+
+void launch_leaf_tc32(tfi_plan_t p, const float *F, float *lbuf, int d, cudaStream_t s) {
+    if (p->n_leaf32 == 0) return;
+    if (d <= 16) launch_leaf_tc32_nb<16>(p, F, lbuf, d, s);
+    else if (d <= 32) launch_leaf_tc32_nb<32>(p, F, lbuf, d, s);
+    else launch_leaf_tc32_nb<64>(p, F, lbuf, d, s);
+}
+
 // (a3) bin sums -> kbuf: segments, then the multi-segment bins' partial rows in order
 template <typename T>
 void launch_bucket(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
@@ -540,20 +569,32 @@ void launch_bucket(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
     }
 }
 
-// (a7) dense leaves -> lbuf: tensor cores for wide BF16 fields, else the FP32-ALU kernel
+// (a7) dense leaves -> lbuf: tensor cores for wide BF16 fields and for the big leaves of FP32
+// fields with d >= 16 (any d with TFI_PLAN_LEAF_TC), the FP32-ALU kernels for the rest. Below 16
+// channels the FP32 ALUs are faster: the f(D) operand costs the same at any d, the ALU sum
+// d FMAs per pair (measured at N = 2^20, s0 = 512: 0.34 against 0.21 ms at d = 1, 0.47 against
+// 0.48 ms at d = 16, 1.18 against 1.96 ms at d = 64).
 template <typename T>
 void launch_leaves(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
+    const bool alu = (p->hp.flags & TFI_PLAN_LEAF_ALU) != 0;
     if constexpr (sizeof(T) == 2) {
-        if (d >= kLeafTcMinChannels && !(p->hp.flags & TFI_PLAN_LEAF_ALU)) {
+        if (d >= kLeafTcMinChannels && !alu) {
             launch_leaf_tc(p, F, p->lbuf, d, s);
             return;
         }
     }
-    if (d >= 16) launch_leaf<16>(p, F, p->lbuf, d, s);
-    else if (d > 4) launch_leaf<8>(p, F, p->lbuf, d, s);
-    else if (d > 2) launch_leaf<4>(p, F, p->lbuf, d, s);
-    else if (d == 2) launch_leaf<2>(p, F, p->lbuf, d, s);
-    else launch_leaf<1>(p, F, p->lbuf, d, s);
+    bool big = true;
+    if constexpr (sizeof(T) == 4) {
+        if (!alu && (d >= kLeafTc32MinChannels || (p->hp.flags & TFI_PLAN_LEAF_TC)) && p->n_leaf32 > 0) {
+            launch_leaf_tc32(p, F, p->lbuf, d, s);
+            big = false;
+        }
+    }
+    if (d >= 16) launch_leaf<16>(p, F, p->lbuf, d, s, big);
+    else if (d > 4) launch_leaf<8>(p, F, p->lbuf, d, s, big);
+    else if (d > 2) launch_leaf<4>(p, F, p->lbuf, d, s, big);
+    else if (d == 2) launch_leaf<2>(p, F, p->lbuf, d, s, big);
+    else launch_leaf<1>(p, F, p->lbuf, d, s, big);
 }
 
 template <int CH>
@@ -593,6 +634,13 @@ tfi_status set_attributes() {
                                   227 * 1024));
     LEAF_TC_ATTR(__nv_bfloat16, 64) LEAF_TC_ATTR(__nv_bfloat16, 128) LEAF_TC_ATTR(__nv_bfloat16, 256)
 #undef LEAF_TC_ATTR
+#define LEAF_TC32_ATTR(NB)                                                                                         \
+    TFI_CUDA(cudaFuncSetAttribute(tfi::tc::leaf_tc32_kernel<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  int(kLeaf32SmemMax)));                                                             \
+    TFI_CUDA(cudaFuncSetAttribute(tfi::tc::leaf_tc32_kernel<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  int(kLeaf32SmemMax)));
+    LEAF_TC32_ATTR(16) LEAF_TC32_ATTR(32) LEAF_TC32_ATTR(64)
+#undef LEAF_TC32_ATTR
 #define LEAF_ATTR(T, CH, FS)                                                                                    \
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::leaf_kernel<T, CH, FS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   200 * 1024));
@@ -981,6 +1029,15 @@ tfi_status upload_plan(tfi_plan_t p) {
         if (tfi_status rc = p->upload(&p->sgrp_ptr, sgrp)) return rc;
         if (tfi_status rc = p->upload(&p->big_lo, blo)) return rc;
         if (tfi_status rc = p->upload(&p->big_hi, bhi)) return rc;
+        // FP32 tensor-core leaves: every big leaf, largest first
+        std::vector<int2> l32;
+        for (size_t q = 0; q < leaf_lo_big.size(); ++q) {
+            l32.push_back(make_int2(leaf_lo_big[q], leaf_hi_big[q]));
+            p->max_leaf32 = std::max(p->max_leaf32, leaf_hi_big[q] - leaf_lo_big[q]);
+        }
+        std::stable_sort(l32.begin(), l32.end(), [](int2 a, int2 b) { return a.y - a.x > b.y - b.x; });
+        if (tfi_status rc = p->upload(&p->leaf32, l32)) return rc;
+        p->n_leaf32 = int32_t(l32.size());
     }
 
     {

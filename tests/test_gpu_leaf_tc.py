@@ -1,8 +1,10 @@
 """GPU parity of the tensor-core dense leaves (tcgen05 kind::tf32) against the
 FP64 oracle and against the FP32-ALU leaf kernel.
 
-BF16 applies with d >= 64 sum leaves on the tensor cores (TFI_PLAN_LEAF_ALU
-forces the FP32-ALU kernel); FP32 applies always use the FP32-ALU kernel. With
+BF16 applies with d >= 64 and FP32 applies with d >= 16 sum leaves of >= 64
+vertices on the tensor cores (the FP32 kernel: hi/lo TF32 splits of f(D) and of
+the field, a fresh accumulator per 32 sources); TFI_PLAN_LEAF_TC extends the
+FP32 kernel to every d and TFI_PLAN_LEAF_ALU forces the FP32-ALU kernels. With
 a large leaf cutoff s0 most of the operator is dense leaf work: every pair of a
 leaf contributes f(D(i) + D(j) - 2 min parent distance) F[j]. The cases cover
 leaves of up to 1024 vertices (8 row tiles, off-diagonal chunks on both sides),
@@ -95,8 +97,53 @@ def test_paths_and_stars():
 
 
 def test_fp32_large_leaves_hold_the_fp32_bound():
-    # FP32 fields sum leaves on the FP32 ALUs in a fixed order: 1024-vertex leaves with a slowly
-    # decaying kernel (heavy cancellation) stay within 1e-4
+    # FP32 fields, d = 96: tensor-core leaves by default, the FP32 ALUs when forced; 1024-vertex
+    # leaves with a slowly decaying kernel (heavy cancellation) stay within 1e-4 either way
     for t in (W.path(1024), W.star(700), _rrt(2000, 23)):
-        e, _, _ = _run(t, 1.0, W.KernelSpec.exp(0.01), 96, 1024, dtype="f32")
+        e, e_alu, _ = _run(t, 1.0, W.KernelSpec.exp(0.01), 96, 1024, dtype="f32")
+        assert e <= TOL["f32"] and e_alu <= TOL["f32"]
+
+
+def _run32(t, delta, spec, d, leaf_max, seed=3):
+    """FP32 fields: (error of the tensor-core leaves, error of the FP32-ALU leaves) against the oracle."""
+    F = torch.from_numpy(W.normal_field(t.n, d, seed=seed)).cuda()
+    tc = tfi.Plan.from_spec(t, delta, spec, leaf_max=leaf_max, max_channels=d, leaf_tc=True)
+    alu = tfi.Plan.from_spec(t, delta, spec, leaf_max=leaf_max, max_channels=d, leaf_alu=True)
+    y, y2, y_alu = tc.apply(F), tc.apply(F), alu.apply(F)
+    torch.cuda.synchronize()
+    assert tc.info()["device_errors"] == 0
+    assert torch.equal(y, y2)   # fixed summation order
+    ref = brute.integrate(t, delta, spec, F.cpu().numpy().astype(np.float64))
+    return _err(y.cpu().numpy(), ref), _err(y_alu.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("leaf_max", [64, 100, 256, 512, 1024])
+@pytest.mark.parametrize("d", [1, 3, 16, 17, 33, 64, 100])
+def test_fp32_tensor_core_leaves(leaf_max, d):
+    # leaves of 64 .. 1024 vertices (one to eight row tiles, ragged last chunks and tiles), channel
+    # blocks of 16 / 32 / 64 with ragged ends, odd d (scalar field loads)
+    t = _rrt(3000, 24)
+    e, e_alu = _run32(t, 1.0, W.KernelSpec.exp(0.05), d, leaf_max)
+    assert e <= TOL["f32"] and e_alu <= TOL["f32"]
+
+
+def test_fp32_tensor_core_leaves_heavy_cancellation():
+    # the case where one accumulator chained over a whole 1024-vertex leaf missed the bound
+    # (6.5e-4): a slowly decaying kernel on paths, stars and random trees
+    for t in (W.path(1024), W.star(700), _rrt(2000, 23), W.spider(5, 150), W.caterpillar_leaves(200)):
+        e, e_alu = _run32(t, 1.0, W.KernelSpec.exp(0.01), 16, 1024)
+        assert e <= 3e-5 and e_alu <= TOL["f32"]
+
+
+def test_fp32_tensor_core_leaves_global_f_samples_and_forests():
+    # delta = 1/64: leaf diameters of ~64,000 samples, too many to stage (f read from global memory);
+    # a forest whose trees are single leaves of 1 .. 300 vertices (small ones on the ALU kernel)
+    for t in (W.path(1000), W.spider(4, 200)):
+        e, _ = _run32(t, 1 / 64, W.KernelSpec.exp(0.2), 16, 1024)
+        assert e <= TOL["f32"]
+    cfg = W.configs.uneven_batch(count=60, lo=1, hi=300, d=16)
+    e, _ = _run32(cfg["tree"], cfg["delta"], cfg["kernel"], 16, 300)
+    assert e <= TOL["f32"]
+    for kern in (W.KernelSpec.rational(0.3, e=1.5), W.KernelSpec.gauss(0.05)):
+        e, _ = _run32(_rrt(2500, 25), 0.25, kern, 16, 512)
         assert e <= TOL["f32"]

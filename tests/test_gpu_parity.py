@@ -142,13 +142,13 @@ def _stratified_targets(p, n, seed, per=96, n_random=128):
     return t[t >= 0].astype(np.int32), len(classes)
 
 
-def _full_size_case(shape, n, leaf_max, per, n_random, min_targets):
+def _full_size_case(shape, n, leaf_max, per, n_random, min_targets, **flags):
     # a full-size tree at the benchmark's leaf cutoff, checked on stratified outputs the oracle
     # computes one by one
     cfg = W.configs.sweep(shape=shape, n=n, d=16, kernel="exp")
     t = cfg["tree"]
     F = W.normal_field(t.n, 16, seed=123)
-    p = tfi.Plan.from_spec(t, cfg["delta"], cfg["kernel"], leaf_max=leaf_max, max_channels=16)
+    p = tfi.Plan.from_spec(t, cfg["delta"], cfg["kernel"], leaf_max=leaf_max, max_channels=16, **flags)
     targets, n_classes = _stratified_targets(p, t.n, seed=1, per=per, n_random=n_random)
     assert len(targets) >= min_targets
     x = torch.from_numpy(F).cuda()
@@ -169,6 +169,12 @@ def test_full_size_stratified_rrt_2p20_bench_config():
 @pytest.mark.parametrize("shape", ["binary", "caterpillar"])
 def test_full_size_stratified_other_shapes_2p18(shape):
     _full_size_case(shape, 1 << 18, 512, per=48, n_random=96, min_targets=200)
+
+
+def test_full_size_stratified_rrt_2p18_tensor_core_leaves():
+    # the FP32 tensor-core leaf kernel (TFI_PLAN_LEAF_TC) at the benchmark's leaf cutoff
+    p, _ = _full_size_case("rrt", 1 << 18, 512, per=64, n_random=128, min_targets=256, leaf_tc=True)
+    assert p.info()["device_errors"] == 0
 
 
 def test_full_size_sampled_rrt_2p20_small_leaves():
