@@ -34,6 +34,8 @@
 // keep the FP32 bound.
 #pragma once
 
+#include <type_traits>
+
 #include "leaf_tc.cuh"
 
 namespace tfi {
@@ -199,6 +201,9 @@ __global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *_
         else return __ldg(reinterpret_cast<const float *>(reinterpret_cast<const char *>(ftab) + off));
     };
     uint32_t g = 0;   // the CTA's chunk counter (the same sequence in both roles)
+    int st = 0;        // its stage, g % STAGES
+    uint32_t par = 0;  // the parity of its use of that stage, (g / STAGES) & 1
+    bool warm = false; // g >= STAGES
     // a leaf's raw inputs are copied in asynchronously while the previous leaf runs
     auto fetch_raw = [&](int L) {
         if (L >= n_leaves) return;
@@ -257,8 +262,11 @@ __global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *_
             if (lane == 0) {
                 const uint32_t idesc = idesc_tf32(kL32Tile, NB);
                 for (int q = 0; q < n_tiles * nc; ++q, ++g) {
-                    const int stage = int(g % STAGES);
-                    if (!bar_wait(full + stage, (g / STAGES) & 1u)) {
+                    const int stage = st;
+                    if (++st == STAGES) st = 0;
+                    const uint32_t ph = par;
+                    if (st == 0) par ^= 1u;
+                    if (!bar_wait(full + stage, ph)) {
                         atomicExch(err, 1);
                         s_abort = 1;
                         break;
@@ -374,16 +382,14 @@ __global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *_
 #pragma unroll
                 for (int e = 0; e < HC; ++e) acc[e] = 0.f;
                 const uint32_t g0 = g;
-                for (int c = 0; c < nc; ++c, ++g) {
-                    const int stage = int(g % STAGES);
-                    if (g >= uint32_t(STAGES)) {
+                // one chunk; KIND 0: before the warp's block, 1: the block itself, 2: after it
+                auto chunk = [&](int c, auto kind_tag) -> bool {
+                    constexpr int KIND = decltype(kind_tag)::value;
+                    if (warm) {
                         // this stage's operands and accumulator were used by chunk g - STAGES
-                        if (!bar_wait(done + stage, (g / STAGES - 1) & 1u)) {
-                            ok = false;
-                            break;
-                        }
+                        if (!bar_wait(done + st, par ^ 1u)) return false;
                         fence_after_sync();
-                        if (c >= STAGES) read_back(stage);
+                        if (c >= STAGES) read_back(st);
                     }
                     float2 cur[PER];
 #pragma unroll
@@ -392,11 +398,11 @@ __global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *_
                     // A: f(dhat) for this thread's row and sources 16 h .. 16 h + 15 of the chunk
                     const int jb = c * kL32Chunk + h * 16;
                     int off[16];
-                    if (c != bc) {
-                        const int mid = __shfl_sync(0xffffffffu, c > bc ? mR : mL, c);
-                        const int r = min(min(c > bc ? Qi : Pi, mid), di);
+                    if constexpr (KIND != 1) {
+                        const int mid = __shfl_sync(0xffffffffu, KIND == 2 ? mR : mL, c);
+                        const int r = min(min(KIND == 2 ? Qi : Pi, mid), di);
                         const int A4 = 4 * (di - 2 * r) + fb;
-                        const int32_t *U = c > bc ? sur : sul;
+                        const int32_t *U = KIND == 2 ? sur : sul;
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int4 s4 = *reinterpret_cast<const int4 *>(ssd + jb + 4 * q);
@@ -438,9 +444,9 @@ __global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *_
                     uint32_t av[32];
 #pragma unroll
                     for (int e = 0; e < 16; ++e) split_tf32_rz(fetch(off[e]), av[e], av[16 + e]);
-                    tmem_st32(tmem + lane_base + A_COL + uint32_t(stage) * 2 * kL32Chunk + uint32_t(h * 32), av);
+                    tmem_st32(tmem + lane_base + A_COL + uint32_t(st) * 2 * kL32Chunk + uint32_t(h * 32), av);
                     // B: the chunk's field rows, transposed (row = channel, K = source), hi and lo
-                    uint8_t *Bhi = smem + lay.b_off + uint32_t(stage) * 2 * lay.b_bytes, *Blo = Bhi + lay.b_bytes;
+                    uint8_t *Bhi = smem + lay.b_off + uint32_t(st) * 2 * lay.b_bytes, *Blo = Bhi + lay.b_bytes;
 #pragma unroll
                     for (int u = 0; u < PER; ++u) {
                         const int q = tid + u * kL32Producers;
@@ -458,8 +464,19 @@ __global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *_
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     fence_async_smem();
                     fence_before_sync();
-                    bar_arrive(full + stage);
-                }
+                    bar_arrive(full + st);
+                    ++g;
+                    if (++st == STAGES) {
+                        st = 0;
+                        par ^= 1u;
+                        warm = true;
+                    }
+                    return true;
+                };
+                // the chunks before the warp's block, the block, the chunks after it (warp-uniform code)
+                for (int c = 0; c < min(bc, nc) && ok; ++c) ok = chunk(c, std::integral_constant<int, 0>());
+                if (ok && bc < nc) ok = chunk(bc, std::integral_constant<int, 1>());
+                for (int c = bc + 1; c < nc && ok; ++c) ok = chunk(c, std::integral_constant<int, 2>());
                 // the tile's last min(nc, STAGES) chunks remain (each committed by the thread
                 // that issued it, so each is waited for)
                 for (int c = max(0, nc - STAGES); c < nc && ok; ++c) {
