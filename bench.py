@@ -124,7 +124,8 @@ def measured_peaks():
 STAGE_SOURCE = {
     "fft": [("kernels.cuh", "// FFT job kernel", "// direct job kernel"), ("fft_x2.cuh", None, None)],
     "leaf": [("kernels.cuh", "// dense leaves of fewer than kLeafWarpMin", "// Exponential-sum sweeps"),
-             ("tfi_api.cu", "constexpr int kLeafWarpThreads", "constexpr int kLeafTcFtabSmem")],
+             ("leaf_tc32.cuh", None, None),
+             ("tfi_api.cu", "constexpr int kLeafWarpThreads", "void launch_direct(")],
 }
 
 
