@@ -136,6 +136,11 @@ typedef struct {
 #define TFI_PLAN_LEAF_TC    512 /* FP32 fields: the tensor-core leaves for every d (by default only
                                    from d = 16, below which the FP32 ALUs are faster). Ignored when
                                    TFI_PLAN_LEAF_ALU is set. */
+#define TFI_PLAN_TABLES_ALU 1024 /* tables evaluated by direct summation on the FP32 ALUs for every d.
+                                   By default, for d > 16, a direct table of 64 .. 2048 bins is an
+                                   f(r_i + r_j + |x_i - x_j|) x S product on the tensor cores
+                                   (tcgen05 kind::tf32, both operands split into hi + lo, a fresh
+                                   accumulator for every 32 source bins, added in FP32 registers) */
 
 typedef struct {
     double delta;           /* grid step > 0 */

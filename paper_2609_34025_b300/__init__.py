@@ -134,7 +134,8 @@ class Plan:
 
     def __init__(self, n, u, v, w, delta=1.0, kernel=("expsum", [1.0, 1.0]), table=None, policy="adaptive",
                  leaf_max=64, max_channels=16, host_only=False, sweep=False, hankel=None, leaf_alu=False,
-                 fft_big_all=False, fft_cta_points=0, truncate=True, direct_all=False, leaf_tc=False):
+                 fft_big_all=False, fft_cta_points=0, truncate=True, direct_all=False, leaf_tc=False,
+                 tables_alu=False):
         u = np.ascontiguousarray(u, dtype=np.int32)
         v = np.ascontiguousarray(v, dtype=np.int32)
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -147,7 +148,7 @@ class Plan:
         opt = _Options(float(delta), POLICIES[policy], int(leaf_max), int(max_channels),
                        (1 if host_only else 0) | SWEEP_MODES[sweep] | HANKEL_MODES[hankel] | (16 if leaf_alu else 0)
                        | (64 if fft_big_all else 0) | (0 if truncate else 128) | (256 if direct_all else 0)
-                       | (512 if leaf_tc else 0),
+                       | (512 if leaf_tc else 0) | (1024 if tables_alu else 0),
                        int(fft_cta_points))
         h = ctypes.c_void_p()
         _check(lib().tfi_plan(ctypes.byref(tree), ctypes.byref(ker), ctypes.byref(opt), ctypes.byref(h)))
@@ -174,7 +175,7 @@ class Plan:
         mc = int(max_channels or d)
         fl = SWEEP_MODES[flags.get("sweep", False)] | HANKEL_MODES[flags.get("hankel", None)] | \
             (16 if flags.get("leaf_alu") else 0) | (64 if flags.get("fft_big_all") else 0) | \
-            (512 if flags.get("leaf_tc") else 0)
+            (512 if flags.get("leaf_tc") else 0) | (1024 if flags.get("tables_alu") else 0)
         opt = _Options(float(delta), POLICIES[policy], 64, mc, fl, 0)
         cand = None if leaf_candidates is None else np.ascontiguousarray(leaf_candidates, dtype=np.int32)
         tuned = _Options()

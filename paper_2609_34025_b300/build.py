@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtfi.so")
 SOURCES = ["planner.cpp", "tfi_api.cu"]
-HEADERS = ["planner.hpp", "kernels.cuh", "dense_tc.cuh", "grad.cuh", "hankel_tc.cuh", "hankel_layout.hpp", "leaf_tc.cuh", "leaf_tc32.cuh", "fft_x2.cuh", "fft_big.cuh"]
+HEADERS = ["planner.hpp", "kernels.cuh", "dense_tc.cuh", "grad.cuh", "hankel_tc.cuh", "hankel_layout.hpp", "leaf_tc.cuh", "leaf_tc32.cuh", "table_tc32.cuh", "fft_x2.cuh", "fft_big.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

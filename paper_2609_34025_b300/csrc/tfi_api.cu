@@ -21,6 +21,7 @@
 #include "hankel_tc.cuh"
 #include "leaf_tc.cuh"
 #include "leaf_tc32.cuh"
+#include "table_tc32.cuh"
 #include "kernels.cuh"
 #include "fft_x2.cuh"
 #include "fft_big.cuh"
@@ -52,6 +53,9 @@ struct WorkLists {
     tfi::dev::FftItem *d_fft = nullptr;
     tfi::dev::DirItem *d_dir = nullptr;
     int n_dir = 0;
+    // direct jobs on the tensor cores (d > 16): (kb, ke, two-dimensional, 0), largest first
+    int4 *d_tab = nullptr;
+    int n_tab = 0, tab_max_keys = 1, tab_fts = 1;
     // Hankel-matrix jobs: one item per (job, 128-channel block), one launch
     tfi::tc::HankelItem *d_hk = nullptr;
     int n_hk = 0;
@@ -68,6 +72,14 @@ struct WorkLists {
 };
 
 constexpr int64_t kBigBatchBytes = int64_t(4) << 30;  // four-step FFT buffer of a plan, at most
+constexpr int kLeafTc32MinChannels = 16;       // FP32 fields: tensor-core big leaves from this d
+constexpr int kTable32MinChannels = 17;        // direct tables on the tensor cores from this d: one
+                                               // f operand for all channels where the ALU kernel
+                                               // needs two or more 16-channel passes (N = 2^20:
+                                               // 0.66 against 0.96 ms at d = 64, 0.25 against
+                                               // 0.24 ms at d = 16)
+constexpr size_t kLeaf32SmemMax = 110 * 1024;  // tensor-core leaf / table CTAs: two per SM (with the
+                                               // static and reserved bytes)
 
 }  // namespace
 
@@ -222,6 +234,7 @@ struct tfi_plan_s {
         for (auto &kv : work) {
             cudaFree(kv.second.d_fft);
             cudaFree(kv.second.d_dir);
+            cudaFree(kv.second.d_tab);
             cudaFree(kv.second.d_hk);
             cudaFree(kv.second.d_big);
         }
@@ -252,9 +265,11 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
     const int pairs = (d + 1) / 2;
     std::map<int, std::vector<tfi::dev::FftItem>> by_class;
     std::vector<tfi::dev::DirItem> dir;
+    std::vector<int4> tab;
     std::vector<tfi::tc::HankelItem> hk;
     uint32_t hk_cols = 32;
     const auto &jobs = p->hp.jobs;
+    const bool tab_tc = d >= kTable32MinChannels && !(p->hp.flags & TFI_PLAN_TABLES_ALU);
     for (size_t j = 0; j < jobs.size(); ++j) {
         const tfi::Job &jb = jobs[j];
         if (jb.ke == jb.kb || jb.mode == 2 || jb.mode == 4) continue;
@@ -269,9 +284,19 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
             const int np = fft_pairs_per_cta(lnp, pairs, p->fft_cta_points);
             for (int p0 = 0; p0 < pairs; p0 += np)
                 by_class[lnp].push_back(tfi::dev::FftItem{int32_t(j), p0, std::min(np, pairs - p0)});
+        } else if (tab_tc && jb.ke - jb.kb >= tfi::tc::kTab32MinKeys && jb.ke - jb.kb <= tfi::tc::kTab32MaxKeys) {
+            tab.push_back(make_int4(int32_t(jb.kb), int32_t(jb.ke), jb.maxx > 0 ? 1 : 0, 0));
+            wl.tab_max_keys = std::max(wl.tab_max_keys, int(jb.ke - jb.kb));
+            wl.tab_fts = std::max(wl.tab_fts, 2 * jb.maxr + jb.maxx + 1);
         } else {
             for (int64_t q = jb.kb; q < jb.ke; q += 64) dir.push_back(tfi::dev::DirItem{int32_t(j), int32_t(q)});
         }
+    }
+    std::stable_sort(tab.begin(), tab.end(), [](int4 a, int4 b) { return a.y - a.x > b.y - b.x; });
+    wl.n_tab = int(tab.size());
+    if (!tab.empty()) {
+        TFI_CUDA(cudaMalloc(&wl.d_tab, tab.size() * sizeof(tab[0])));
+        TFI_CUDA(cudaMemcpy(wl.d_tab, tab.data(), tab.size() * sizeof(tab[0]), cudaMemcpyHostToDevice));
     }
     std::vector<tfi::dev::FftItem> all;
     for (auto &kv : by_class) {
@@ -527,8 +552,7 @@ void launch_leaf_tc(tfi_plan_t p, const __nv_bfloat16 *F, float *lbuf, int d, cu
 }
 
 // FP32 leaves of >= kLeafWarpMin vertices on the tensor cores: NB channels per CTA
-constexpr int kLeafTc32MinChannels = 16;  // FP32 fields: tensor-core big leaves from this d
-constexpr size_t kLeaf32SmemMax = 110 * 1024;  // two CTAs per SM (with the static and reserved bytes)
+
 
 template <int NB>
 void launch_leaf_tc32_nb(tfi_plan_t p, const float *F, float *lbuf, int d, cudaStream_t s) {
@@ -597,8 +621,32 @@ void launch_leaves(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
     else launch_leaf<1>(p, F, p->lbuf, d, s, big);
 }
 
+// direct jobs of 64 .. 2048 bins on the tensor cores for d > 16: NB channels per CTA
+template <int NB>
+void launch_table_tc32_nb(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
+    int fts = wl.tab_fts;
+    if (fts > int(p->hp.ftab.size()) ||
+        tfi::tc::table_tc32_layout(NB, wl.tab_max_keys, fts).bytes > kLeaf32SmemMax)
+        fts = 0;
+    // at least a third of an SM's shared memory: two CTAs (their tensor memory) per SM
+    const size_t smem =
+        std::max(size_t(tfi::tc::table_tc32_layout(NB, wl.tab_max_keys, fts).bytes), size_t(80 * 1024));
+    dim3 grid(unsigned(std::min(wl.n_tab, 2 * device_sms())), unsigned((d + NB - 1) / NB));
+    auto k = fts > 0 ? tfi::tc::table_tc32_kernel<NB, true> : tfi::tc::table_tc32_kernel<NB, false>;
+    k<<<grid, tfi::tc::kL32Threads, smem, s>>>(wl.d_tab, wl.n_tab, p->key_r, p->key_x, d, p->kbuf, p->vbuf,
+                                              p->ftab, fts, wl.tab_max_keys, p->hk_err + 1);
+}
+
+void launch_table_tc32(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
+    if (wl.n_tab == 0) return;
+    if (d <= 16) launch_table_tc32_nb<16>(p, wl, d, s);
+    else if (d <= 32) launch_table_tc32_nb<32>(p, wl, d, s);
+    else launch_table_tc32_nb<64>(p, wl, d, s);
+}
+
 template <int CH>
 void launch_direct(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
+    launch_table_tc32(p, wl, d, s);
     if (wl.n_dir == 0) return;
     constexpr int WARPS = 4;
     dim3 grid((wl.n_dir + WARPS - 1) / WARPS, (d + CH - 1) / CH);
@@ -641,6 +689,13 @@ tfi_status set_attributes() {
                                   int(kLeaf32SmemMax)));
     LEAF_TC32_ATTR(16) LEAF_TC32_ATTR(32) LEAF_TC32_ATTR(64)
 #undef LEAF_TC32_ATTR
+#define TABLE_TC32_ATTR(NB)                                                                                         \
+    TFI_CUDA(cudaFuncSetAttribute(tfi::tc::table_tc32_kernel<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  int(kLeaf32SmemMax)));                                                              \
+    TFI_CUDA(cudaFuncSetAttribute(tfi::tc::table_tc32_kernel<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  int(kLeaf32SmemMax)));
+    TABLE_TC32_ATTR(16) TABLE_TC32_ATTR(32) TABLE_TC32_ATTR(64)
+#undef TABLE_TC32_ATTR
 #define LEAF_ATTR(T, CH, FS)                                                                                    \
     TFI_CUDA(cudaFuncSetAttribute(tfi::dev::leaf_kernel<T, CH, FS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   200 * 1024));
@@ -742,7 +797,7 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
         else if (d > 2) launch_direct<4>(p, *wl, d, s_dir);
         else if (d == 2) launch_direct<2>(p, *wl, d, s_dir);
         else launch_direct<1>(p, *wl, d, s_dir);
-        m_dir.done(wl->n_dir > 0 ? 1 : 0);
+        m_dir.done((wl->n_dir > 0 ? 1 : 0) + (wl->n_tab > 0 ? 1 : 0));
         if (wl->n_hk > 0) {
             StageMark m_hk(p, s_dir, TFI_STAGE_HANKEL);
             tfi::tc::hankel_kernel<<<wl->n_hk, 128, wl->hk_smem, s_dir>>>(wl->d_hk, p->key_r, p->key_x, d, p->kbuf,
@@ -1626,6 +1681,7 @@ void clear_work(tfi_plan_t p) {
     for (auto &kv : p->work) {
         cudaFree(kv.second.d_fft);
         cudaFree(kv.second.d_dir);
+        cudaFree(kv.second.d_tab);
         cudaFree(kv.second.d_hk);
         cudaFree(kv.second.d_big);
     }
