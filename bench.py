@@ -47,7 +47,8 @@ def config_block(a, extra=None):
          "kernel": {"exp": "exp(-0.1x)", "cauchy": "1/(1+x^2)", "gauss": "exp(-x^2/8)"}[a.kernel],
          "delta": 1.0 / 64, "weights": "U[0.5,2] snapped to 1/64", "policy": a.policy, "leaf_max": a.leaf_max,
          "l2": "flushed between timed steps (512 MB write)",
-         "leaf_kernel": "tensor cores (TF32 hi/lo) for leaves of >= 64 vertices" if (a.leaf_tc or a.d >= 16) else "FP32 ALU"}
+         "leaf_kernel": "tensor cores (TF32 hi/lo) for leaves of >= 64 vertices"
+                        if (a.leaf_tc or a.d >= 16) and not a.leaf_alu else "FP32 ALU"}
     if extra:
         c.update(extra)
     return c
@@ -239,7 +240,7 @@ def dense_baseline(a, n=1 << 16, reps=5):
 
     cfg = W.configs.sweep(shape=a.shape, n=n, d=a.d, kernel=a.kernel)
     plan = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=a.policy, leaf_max=a.leaf_max,
-                              max_channels=a.d, leaf_tc=a.leaf_tc, tables_alu=a.tables_alu)
+                              max_channels=a.d, leaf_tc=a.leaf_tc, tables_alu=a.tables_alu, leaf_alu=a.leaf_alu)
     x = torch.from_numpy(W.normal_field(n, a.d, seed=123)).cuda()
     out = torch.empty_like(x)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -332,7 +333,7 @@ def c2_sweep(a, steps=5):
         n = cfg["tree"].n
         t0 = time.perf_counter()
         plan = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=a.policy, leaf_max=a.leaf_max,
-                                  max_channels=d, leaf_tc=a.leaf_tc, tables_alu=a.tables_alu)
+                                  max_channels=d, leaf_tc=a.leaf_tc, tables_alu=a.tables_alu, leaf_alu=a.leaf_alu)
         plan_s = time.perf_counter() - t0
         F = torch.from_numpy(W.normal_field(n, d, seed=123)).cuda()
         G = torch.from_numpy(W.normal_field(n, d, seed=124)).cuda()
@@ -402,7 +403,7 @@ def run_ours(a):
     n, d = cfg["tree"].n, cfg["d"]
     t0 = time.perf_counter()
     plan = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=a.policy, leaf_max=a.leaf_max,
-                              max_channels=d, leaf_tc=a.leaf_tc, tables_alu=a.tables_alu)
+                              max_channels=d, leaf_tc=a.leaf_tc, tables_alu=a.tables_alu, leaf_alu=a.leaf_alu)
     plan_s = time.perf_counter() - t0
     # weak scaling over ranks: each rank integrates its own block of d channels on the same tree
     F = torch.from_numpy(W.normal_field(n, d, seed=123 + 2 * rank)).cuda()
@@ -584,7 +585,7 @@ def run_profile_helper(a):
     tbuild.build()
     cfg = W.configs.sweep(**workload_args(a))
     plan = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=a.policy, leaf_max=a.leaf_max,
-                              max_channels=a.d, leaf_tc=a.leaf_tc, tables_alu=a.tables_alu)
+                              max_channels=a.d, leaf_tc=a.leaf_tc, tables_alu=a.tables_alu, leaf_alu=a.leaf_alu)
     x = torch.from_numpy(W.normal_field(cfg["tree"].n, a.d, seed=123)).cuda()
     out = torch.empty_like(x)
     for _ in range(a.profile_applies):
@@ -608,6 +609,8 @@ def main():
     ap.add_argument("--kernel", default="exp", choices=["exp", "cauchy", "gauss"])
     ap.add_argument("--policy", default="adaptive")
     ap.add_argument("--leaf-max", dest="leaf_max", type=int, default=512)
+    ap.add_argument("--leaf-alu", dest="leaf_alu", action="store_true",
+                    help="every dense leaf on the FP32 ALUs (TFI_PLAN_LEAF_ALU)")
     ap.add_argument("--tables-alu", dest="tables_alu", action="store_true",
                     help="every direct table on the FP32 ALUs (TFI_PLAN_TABLES_ALU)")
     ap.add_argument("--leaf-tc", dest="leaf_tc", action="store_true",

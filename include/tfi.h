@@ -130,11 +130,13 @@ typedef struct {
 #define TFI_PLAN_LEAF_ALU   16  /* dense leaves on the FP32 ALUs for every d. By default the leaves of
                                    >= 64 vertices are f(D) x F products on the tensor cores (tcgen05
                                    kind::tf32, f(D) split into hi + lo) for BF16 fields with d >= 64
-                                   and for FP32 fields with d >= 16 (F split too, three products, a
-                                   fresh accumulator for every 32 sources, added in FP32 registers:
-                                   within the 1e-4 bound); the rest on the FP32 ALUs */
-#define TFI_PLAN_LEAF_TC    512 /* FP32 fields: the tensor-core leaves for every d (by default only
-                                   from d = 16, below which the FP32 ALUs are faster). Ignored when
+                                   and for FP32 fields with d >= 16 when the leaves are at least a
+                                   quarter of the plan's leaf and table flops (F split too, three
+                                   products, a fresh accumulator for every 32 sources, added in FP32
+                                   registers: within the 1e-4 bound); the rest on the FP32 ALUs */
+#define TFI_PLAN_LEAF_TC    512 /* FP32 fields: the tensor-core leaves for every d and plan (by default
+                                   only from d = 16, below which the FP32 ALUs are faster, and when the
+                                   leaves are a quarter of the work or more). Ignored when
                                    TFI_PLAN_LEAF_ALU is set. */
 #define TFI_PLAN_TABLES_ALU 1024 /* tables evaluated by direct summation on the FP32 ALUs for every d.
                                    By default, for d > 16, a direct table of 64 .. 2048 bins is an

@@ -72,7 +72,13 @@ struct WorkLists {
 };
 
 constexpr int64_t kBigBatchBytes = int64_t(4) << 30;  // four-step FFT buffer of a plan, at most
-constexpr int kLeafTc32MinChannels = 16;       // FP32 fields: tensor-core big leaves from this d
+constexpr int kLeafTc32MinChannels = 16;       // FP32 fields: tensor-core big leaves from this d,
+constexpr double kLeafTc32MinShare = 0.25;     // when the leaves are at least this share of the leaf
+                                               // and table flops: its persistent CTAs hold most of
+                                               // an SM's registers, which the concurrent table
+                                               // stages then miss (N = 2^20 caterpillar, leaves 3 %
+                                               // of the flops: 63.5 against 57.1 ms per step; random
+                                               // tree, 34 %: 3.03 against 3.07-3.13 ms)
 constexpr int kTable32MinChannels = 17;        // direct tables on the tensor cores from this d: one
                                                // f operand for all channels where the ALU kernel
                                                // needs two or more 16-channel passes (N = 2^20:
@@ -160,6 +166,7 @@ struct tfi_plan_s {
     int32_t n_leaf_tiles = 0;
     int2 *leaf32 = nullptr;                 // leaves of >= kLeafWarpMin vertices as [lo, hi), largest first
     int32_t n_leaf32 = 0, max_leaf32 = 1;   // (the FP32 tensor-core leaf kernel)
+    double leaf_share = 0;                  // dense-leaf flops / all leaf and table flops (per channel)
     std::map<int, WorkLists> work;  // per channel count d
     int32_t fft_cta_points = 1 << 13;  // tfi_options.fft_cta_points (0 there: this default)
     // tfi_apply_static: its work lists without per-call host copies. Direct items do not depend
@@ -558,9 +565,10 @@ template <int NB>
 void launch_leaf_tc32_nb(tfi_plan_t p, const float *F, float *lbuf, int d, cudaStream_t s) {
     int fts = int(p->hp.leaf_ftab_len);
     if (tfi::tc::leaf_tc32_layout(NB, p->max_leaf32, fts).bytes > kLeaf32SmemMax) fts = 0;
-    // at least a third of an SM's shared memory: the two CTAs that its tensor memory holds
-    // are all that share an SM, so none waits in tcgen05.alloc
-    const size_t smem = std::max(size_t(tfi::tc::leaf_tc32_layout(NB, p->max_leaf32, fts).bytes), size_t(80 * 1024));
+    // no shared-memory padding: the registers (288 threads x 96) already keep it to two CTAs per SM,
+    // which its tensor memory holds, and the rest of the SM stays open to the kernels that run
+    // beside it (a four-step FFT CTA takes 140 KB)
+    const size_t smem = tfi::tc::leaf_tc32_layout(NB, p->max_leaf32, fts).bytes;
     // persistent: two CTAs per SM (their tensor memory), each over every gridDim.x-th leaf
     dim3 grid(unsigned(std::min(p->n_leaf32, 2 * device_sms())), unsigned((d + NB - 1) / NB));
     auto k = fts > 0 ? tfi::tc::leaf_tc32_kernel<NB, true> : tfi::tc::leaf_tc32_kernel<NB, false>;
@@ -609,7 +617,8 @@ void launch_leaves(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
     }
     bool big = true;
     if constexpr (sizeof(T) == 4) {
-        if (!alu && (d >= kLeafTc32MinChannels || (p->hp.flags & TFI_PLAN_LEAF_TC)) && p->n_leaf32 > 0) {
+        const bool by_default = d >= kLeafTc32MinChannels && p->leaf_share >= kLeafTc32MinShare;
+        if (!alu && (by_default || (p->hp.flags & TFI_PLAN_LEAF_TC)) && p->n_leaf32 > 0) {
             launch_leaf_tc32(p, F, p->lbuf, d, s);
             big = false;
         }
@@ -628,9 +637,8 @@ void launch_table_tc32_nb(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t
     if (fts > int(p->hp.ftab.size()) ||
         tfi::tc::table_tc32_layout(NB, wl.tab_max_keys, fts).bytes > kLeaf32SmemMax)
         fts = 0;
-    // at least a third of an SM's shared memory: two CTAs (their tensor memory) per SM
-    const size_t smem =
-        std::max(size_t(tfi::tc::table_tc32_layout(NB, wl.tab_max_keys, fts).bytes), size_t(80 * 1024));
+    // two CTAs per SM by their registers (as for the leaves), no shared-memory padding
+    const size_t smem = tfi::tc::table_tc32_layout(NB, wl.tab_max_keys, fts).bytes;
     dim3 grid(unsigned(std::min(wl.n_tab, 2 * device_sms())), unsigned((d + NB - 1) / NB));
     auto k = fts > 0 ? tfi::tc::table_tc32_kernel<NB, true> : tfi::tc::table_tc32_kernel<NB, false>;
     k<<<grid, tfi::tc::kL32Threads, smem, s>>>(wl.d_tab, wl.n_tab, p->key_r, p->key_x, d, p->kbuf, p->vbuf,
@@ -1093,6 +1101,15 @@ tfi_status upload_plan(tfi_plan_t p) {
         std::stable_sort(l32.begin(), l32.end(), [](int2 a, int2 b) { return a.y - a.x > b.y - b.x; });
         if (tfi_status rc = p->upload(&p->leaf32, l32)) return rc;
         p->n_leaf32 = int32_t(l32.size());
+        // per-channel flops: leaf pairs 2 n^2, FFT tables 5 P log2 P + 3 P per channel, direct 2 nk^2
+        double leaf = 0, tables = 0;
+        for (const tfi::Leaf &l : hp.leaves) leaf += 2.0 * double(l.end - l.begin) * double(l.end - l.begin);
+        for (const tfi::Job &j : hp.jobs) {
+            const double nk = double(j.ke - j.kb), np = std::ldexp(1.0, j.lp1 + j.lp2);
+            if (j.mode == 0 || j.mode == 4) tables += 5.0 * np * double(j.lp1 + j.lp2) + 3.0 * np;
+            else if (j.mode == 1) tables += 2.0 * nk * nk;
+        }
+        p->leaf_share = leaf + tables > 0 ? leaf / (leaf + tables) : 0.0;
     }
 
     {
