@@ -24,7 +24,7 @@ namespace tfi {
 namespace tc {
 
 constexpr int kTab32MinKeys = 64;     // smaller tables stay on the FP32-ALU direct kernel
-constexpr int kTab32MaxKeys = 2048;   // as do larger ones (their keys would not fit shared memory)
+constexpr int kTab32MaxKeys = 4096;   // as do larger ones (their keys would not fit shared memory)
 
 struct Tab32Layout {
     uint32_t b_off, b_bytes, r_off, x_off, rr_off, rx_off, ftab_off, bar_off, bytes;

@@ -53,7 +53,7 @@ struct WorkLists {
     tfi::dev::FftItem *d_fft = nullptr;
     tfi::dev::DirItem *d_dir = nullptr;
     int n_dir = 0;
-    // direct jobs on the tensor cores (d > 16): (kb, ke, two-dimensional, 0), largest first
+    // direct jobs on the tensor cores: (kb, ke, two-dimensional, 0), largest first
     int4 *d_tab = nullptr;
     int n_tab = 0, tab_max_keys = 1, tab_fts = 1;
     // Hankel-matrix jobs: one item per (job, 128-channel block), one launch
@@ -83,7 +83,9 @@ constexpr int kTable32MinChannels = 17;        // direct tables on the tensor co
                                                // f operand for all channels where the ALU kernel
                                                // needs two or more 16-channel passes (N = 2^20:
                                                // 0.66 against 0.96 ms at d = 64, 0.25 against
-                                               // 0.24 ms at d = 16)
+                                               // 0.24 ms at d = 16 on the random tree's tables)
+constexpr int kTable32BigKeys = 512;           // and at d = 16 for tables of this many bins or more
+                                               // (the 2^20 caterpillar: 52.1 against 57.1 ms)
 constexpr size_t kLeaf32SmemMax = 110 * 1024;  // tensor-core leaf / table CTAs: two per SM (with the
                                                // static and reserved bytes)
 
@@ -276,7 +278,7 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
     std::vector<tfi::tc::HankelItem> hk;
     uint32_t hk_cols = 32;
     const auto &jobs = p->hp.jobs;
-    const bool tab_tc = d >= kTable32MinChannels && !(p->hp.flags & TFI_PLAN_TABLES_ALU);
+    const bool tab_alu = (p->hp.flags & TFI_PLAN_TABLES_ALU) != 0;
     for (size_t j = 0; j < jobs.size(); ++j) {
         const tfi::Job &jb = jobs[j];
         if (jb.ke == jb.kb || jb.mode == 2 || jb.mode == 4) continue;
@@ -291,7 +293,8 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
             const int np = fft_pairs_per_cta(lnp, pairs, p->fft_cta_points);
             for (int p0 = 0; p0 < pairs; p0 += np)
                 by_class[lnp].push_back(tfi::dev::FftItem{int32_t(j), p0, std::min(np, pairs - p0)});
-        } else if (tab_tc && jb.ke - jb.kb >= tfi::tc::kTab32MinKeys && jb.ke - jb.kb <= tfi::tc::kTab32MaxKeys) {
+        } else if (!tab_alu && jb.ke - jb.kb >= tfi::tc::kTab32MinKeys && jb.ke - jb.kb <= tfi::tc::kTab32MaxKeys &&
+                   (d >= kTable32MinChannels || (d == 16 && jb.ke - jb.kb >= kTable32BigKeys))) {
             tab.push_back(make_int4(int32_t(jb.kb), int32_t(jb.ke), jb.maxx > 0 ? 1 : 0, 0));
             wl.tab_max_keys = std::max(wl.tab_max_keys, int(jb.ke - jb.kb));
             wl.tab_fts = std::max(wl.tab_fts, 2 * jb.maxr + jb.maxx + 1);
@@ -630,7 +633,8 @@ void launch_leaves(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
     else launch_leaf<1>(p, F, p->lbuf, d, s, big);
 }
 
-// direct jobs of 64 .. 2048 bins on the tensor cores for d > 16: NB channels per CTA
+// direct jobs of 64 .. 4096 bins on the tensor cores (d > 16, or d = 16 from 512 bins): NB channels
+// per CTA
 template <int NB>
 void launch_table_tc32_nb(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {
     int fts = wl.tab_fts;

@@ -1,13 +1,14 @@
 """GPU parity of the tensor-core direct tables (tcgen05 kind::tf32) against the
 FP64 oracle and against the FP32-ALU direct kernel, through the C ABI.
 
-For d > 16 a table evaluated by direct summation with 64 .. 2048 bins is an
-f(r_i + r_j + |x_i - x_j|) x S product on the tensor cores (both operands split
-into TF32 hi + lo, a fresh accumulator per 32 source bins); TFI_PLAN_TABLES_ALU
-keeps every table on the FP32 ALUs. The N = 4096 sweep trees at s0 = 64 have such
-tables on all three shapes (component corrections and call cross tables), the
-caterpillar up to 1991 bins; the 8192-vertex caterpillar and the diameter policy
-add tables beyond 2048 bins, which stay on the ALU kernel. Tolerance 1e-4 per
+For d > 16 (for d = 16 from 512 bins) a table evaluated by direct summation with
+64 .. 4096 bins is an f(r_i + r_j + |x_i - x_j|) x S product on the tensor cores
+(both operands split into TF32 hi + lo, a fresh accumulator per 32 source bins);
+TFI_PLAN_TABLES_ALU keeps every table on the FP32 ALUs. The N = 4096 sweep trees
+at s0 = 64 have such tables on all three shapes (component corrections and call
+cross tables), the caterpillar up to 1991 bins; the 8192-vertex caterpillar has
+tables of up to 4007 bins, and under the diameter policy with every table summed
+directly one of 8135 bins, which stays on the ALU kernel. Tolerance 1e-4 per
 channel, normwise, for FP32 fields; 1e-2 for BF16 fields.
 """
 import numpy as np
@@ -30,10 +31,12 @@ def _err(y, ref):
     return float((np.abs(y - ref).max(0) / np.maximum(np.abs(ref).max(0), 1e-300)).max())
 
 
-def _eligible(p):
+def _eligible(p, d=17):
+    # direct tables the tensor cores take at d channels
     jobs = p.export("jobs")
     nb = jobs[:, 3]
-    return int(((jobs[:, 0] == 1) & (nb >= 64) & (nb <= 2048)).sum())
+    lo = 64 if d > 16 else 512 if d == 16 else 1 << 30
+    return int(((jobs[:, 0] == 1) & (nb >= lo) & (nb <= 4096)).sum())
 
 
 def _run(t, delta, spec, d, dtype="f32", seed=5, **kw):
@@ -61,17 +64,20 @@ def test_tables_on_tensor_cores(shape, d):
 
 
 @pytest.mark.parametrize("kernel", ["cauchy", "gauss"])
-def test_two_dimensional_and_oversized_tables(kernel):
-    # every table summed directly under the diameter policy: two-dimensional call cross tables,
-    # some beyond 2048 bins (on the ALU kernel); an 8192-vertex caterpillar with 3243-bin tables
+def test_two_dimensional_and_large_tables(kernel):
+    # every table summed directly under the diameter policy: two-dimensional call cross tables of
+    # up to 2548 bins; the 8192-vertex caterpillar's tables of up to 4007 bins at d = 24 and d = 16,
+    # and under the diameter policy one of 8135 bins (on the ALU kernel)
     cfg = W.configs.sweep(shape="rrt", n=4096, d=24, kernel=kernel)
     p, _, _, e, e_alu = _run(cfg["tree"], cfg["delta"], cfg["kernel"], 24, leaf_max=16, policy="diameter",
                              direct_all=True)
     assert _eligible(p) > 0 and p.export("jobs")[:, 3].max() > 2048
     assert e <= TOL["f32"] and e_alu <= TOL["f32"]
     cfg = W.configs.sweep(shape="caterpillar", n=8192, d=24, kernel=kernel)
-    p, _, _, e, _ = _run(cfg["tree"], cfg["delta"], cfg["kernel"], 24, leaf_max=64)
-    assert e <= TOL["f32"]
+    for d, kw in ((24, {}), (16, {}), (24, {"policy": "diameter", "direct_all": True})):
+        p, y, yq, e, _ = _run(cfg["tree"], cfg["delta"], cfg["kernel"], d, leaf_max=64 if not kw else 16, **kw)
+        assert e <= TOL["f32"]
+        assert _eligible(p, d) == 0 or not torch.equal(y, yq)
 
 
 def test_bf16_fields_and_positive_sums():
