@@ -252,6 +252,172 @@ __global__ void grad_leaf_hist(const int32_t *__restrict__ leaf_ptr, const int64
     }
 }
 
+// Leaves in one pass: one CTA per leaf, eight warps, each warp a block of 32
+// targets (one per lane) against every source of the leaf, the channels in blocks
+// of 16 (the histogram is linear in the channels, so the blocks add up). The
+// pair distances follow the leaf walk of the apply: dhat(i, j) = D(i) + D(j) -
+// 2 m(i, j) with running minima m over the parent distances, the sources inside
+// the block in an ascending and a descending sweep, the sources after it
+// ascending from the block's suffix minima, those before it descending from its
+// prefix minima. The pair values <g_i, F_j> are added into one histogram of
+// 64-bit fixed-point integers in shared memory: integer addition is exact and
+// associative, so the result does not depend on the order of the atomic adds
+// (deterministic), and the scale 2^S is chosen per leaf so that no sum can
+// overflow: |<g_i, F_j>| <= max ||g|| max ||F|| = B, at most n^2 pairs, so
+// S = 61 - ceil(log2 n^2) - ceil(log2 B) keeps every partial sum below 2^61;
+// each value is rounded once to a multiple of 2^-S (<= 2^-S / 2 from exact).
+constexpr int kGradLeafWarps = 8;
+
+// the fixed-point histogram rounded up to an even count of 8-byte entries, so that the source
+// rows after it start on a 16-byte boundary (they are read as float4)
+__host__ __device__ inline int grad_leaf_hist_slots(int max_hl) { return (max_hl + 1) & ~1; }
+
+__host__ __device__ inline size_t grad_leaf_warp_smem(int max_n, int max_hl) {
+    return size_t(grad_leaf_hist_slots(max_hl)) * 8 + size_t(max_n) * 16 * 4 + size_t(2 * max_n + 2) * 4 + 64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kGradLeafWarps) grad_leaf_warp_hist(
+    const int32_t *__restrict__ leaf_ptr, const int64_t *__restrict__ hist_off, const int32_t *__restrict__ hist_len,
+    const int32_t *__restrict__ leaf_vtx, const int32_t *__restrict__ leaf_dist, const int32_t *__restrict__ leaf_pdist,
+    const T *__restrict__ G, const T *__restrict__ F, int d, int max_n, int max_hl, float *__restrict__ hist) {
+    constexpr int INF = 0x7fffffff;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned long long smh[];
+    const int lf = blockIdx.x;
+    const int lo = leaf_ptr[lf], n = leaf_ptr[lf + 1] - lo, hl = hist_len[lf];
+    unsigned long long *h64 = smh;                                       // max_hl fixed-point sums
+    float *sx = reinterpret_cast<float *>(smh + grad_leaf_hist_slots(max_hl));   // the block's source rows
+    int *sdist = reinterpret_cast<int *>(sx + max_n * 16), *spd = sdist + max_n;
+    __shared__ float s_max[2][kGradLeafWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sdist[i] = leaf_dist[lo + i];
+        spd[i] = leaf_pdist[lo + i];
+    }
+    if (threadIdx.x == 0) spd[n] = INF;
+    for (int k = threadIdx.x; k < hl; k += blockDim.x) h64[k] = 0ull;
+    // the scale: B = max ||g_i|| max ||F_j|| over the leaf (squared norms, then the root)
+    {
+        float mg = 0.f, mf = 0.f;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int64_t v = leaf_vtx[lo + i];
+            float sg = 0.f, sf = 0.f;
+            for (int c = 0; c < d; ++c) {
+                const float a = ldf<T>(G + v * d + c), b = ldf<T>(F + v * d + c);
+                sg = fmaf(a, a, sg);
+                sf = fmaf(b, b, sf);
+            }
+            mg = fmaxf(mg, sg);
+            mf = fmaxf(mf, sf);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mg = fmaxf(mg, __shfl_xor_sync(FULL, mg, o));
+            mf = fmaxf(mf, __shfl_xor_sync(FULL, mf, o));
+        }
+        if (lane == 0) {
+            s_max[0][warp] = mg;
+            s_max[1][warp] = mf;
+        }
+    }
+    __syncthreads();
+    float mg = 0.f, mf = 0.f;
+#pragma unroll
+    for (int w = 0; w < kGradLeafWarps; ++w) {
+        mg = fmaxf(mg, s_max[0][w]);
+        mf = fmaxf(mf, s_max[1][w]);
+    }
+    // B^2 = mg mf; ceil(log2 B) from the exponent of B^2 (rounded up, plus one for the rounding)
+    int S = 0;
+    if (mg > 0.f && mf > 0.f) {
+        int eg, ef;
+        frexpf(mg, &eg);   // mg < 2^eg
+        frexpf(mf, &ef);
+        const int lb = (eg + ef + 1) / 2 + 1;                           // B < 2^lb
+        const int ln2 = 2 * (32 - __clz(max(n, 1)));                    // n^2 <= 2^ln2
+        S = 61 - ln2 - lb;
+    }
+    const float sc1 = ldexpf(1.f, S / 2), sc2 = ldexpf(1.f, S - S / 2);  // 2^S in two representable factors
+    auto add = [&](int D, float v) {
+        if (D >= 0 && D < hl) atomicAdd(&h64[D], static_cast<unsigned long long>(__float2ll_rn(v * sc1 * sc2)));
+    };
+    for (int c0 = 0; c0 < d; c0 += 16) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < n * 16; q += blockDim.x) {
+            const int j = q >> 4, c = q & 15;
+            sx[q] = c0 + c < d ? ldf<T>(F + int64_t(leaf_vtx[lo + j]) * d + c0 + c) : 0.f;
+        }
+        __syncthreads();
+        for (int a = warp * 32; a < n; a += kGradLeafWarps * 32) {
+            const int bend = min(a + 32, n);
+            const int ti = a + lane;
+            const bool act = ti < n;
+            const int Di = act ? sdist[ti] : 0;
+            float g[16];
+            {
+                const int64_t vi = act ? leaf_vtx[lo + ti] : 0;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) g[c] = (act && c0 + c < d) ? ldf<T>(G + vi * d + c0 + c) : 0.f;
+            }
+            auto dot = [&](int j) {
+                const float4 *x = reinterpret_cast<const float4 *>(sx + j * 16);
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 r = x[q];
+                    s0 = fmaf(g[4 * q], r.x, s0);
+                    s1 = fmaf(g[4 * q + 1], r.y, s1);
+                    s0 = fmaf(g[4 * q + 2], r.z, s0);
+                    s1 = fmaf(g[4 * q + 3], r.w, s1);
+                }
+                return s0 + s1;
+            };
+            // sources inside the block: ascending for j >= i (j = i at distance 0), descending for j < i
+            int m = INF;
+            for (int j = a; j < bend; ++j) {
+                if (j > ti) m = min(m, spd[j]);
+                add(!act || j < ti ? -1 : j == ti ? 0 : Di + sdist[j] - 2 * m, dot(j));
+            }
+            m = INF;
+            for (int j = bend - 1; j >= a; --j) {
+                if (j < ti) m = min(m, spd[j + 1]);
+                add(act && j < ti ? Di + sdist[j] - 2 * m : -1, dot(j));
+            }
+            // carries: suffix min over (i, bend - 1], prefix min over (a, i]
+            int suf = (a + lane + 1 < bend) ? spd[a + lane + 1] : INF;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_down_sync(FULL, suf, o);
+                if (lane + o < 32) suf = min(suf, u);
+            }
+            int pre = (lane > 0 && a + lane < bend) ? spd[a + lane] : INF;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(FULL, pre, o);
+                if (lane >= o) pre = min(pre, u);
+            }
+            // sources after the block, ascending
+            m = suf;
+            for (int j = bend; j < n; ++j) {
+                m = min(m, spd[j]);
+                add(act ? Di + sdist[j] - 2 * m : -1, dot(j));
+            }
+            // sources before the block, descending
+            m = pre;
+            for (int j = a - 1; j >= 0; --j) {
+                m = min(m, spd[j + 1]);
+                add(act ? Di + sdist[j] - 2 * m : -1, dot(j));
+            }
+        }
+    }
+    __syncthreads();
+    float *out = hist + hist_off[lf];
+    const float inv1 = ldexpf(1.f, -(S / 2)), inv2 = ldexpf(1.f, -(S - S / 2));
+    for (int k = threadIdx.x; k < hl; k += blockDim.x)
+        out[k] = float(static_cast<long long>(h64[k])) * inv1 * inv2;
+}
+
 // C[k] = sum over segments (fixed order) of sign * hist_segment[k], in FP64. One
 // warp per k: lanes take segments 32 apart, then a butterfly of shuffles (fixed
 // order) adds the lanes' partial sums.

@@ -131,6 +131,8 @@ struct tfi_plan_s {
     // kernel gradient (built on first use)
     bool grad_ready = false;
     int32_t n_gjobs = 0, n_gleaves = 0, n_gseg = 0, g_max_lnp = 0, g_nblk = 1;
+    int32_t g_leaf_max_n = 1, g_leaf_max_hl = 1;   // largest leaf and leaf histogram (one-pass leaf kernel)
+    bool g_leaf_onepass = false;                    // its shared memory fits: no per-pair buffers
     int64_t *g_ditems = nullptr;
     int32_t *g_djobs = nullptr, n_gditems = 0, n_gdjobs = 0;
     float *g_M = nullptr;
@@ -586,21 +588,23 @@ void launch_leaf_tc32(tfi_plan_t p, const float *F, float *lbuf, int d, cudaStre
     else launch_leaf_tc32_nb<64>(p, F, lbuf, d, s);
 }
 
-// (a3) bin sums -> kbuf: segments, then the multi-segment bins' partial rows in order
+// (a3) bin sums -> kb (the plan's kbuf by default): segments, then the multi-segment bins'
+// partial rows in order
 template <typename T>
-void launch_bucket(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
+void launch_bucket(tfi_plan_t p, const T *F, int d, cudaStream_t s, float *kb = nullptr) {
+    if (!kb) kb = p->kbuf;
     if (d % 4 == 0 && (reinterpret_cast<uintptr_t>(F) % (4 * sizeof(T))) == 0) {
         tfi::dev::bucket_seg_kernel<T, 4><<<grid_for(p->n_segs * (d / 4), 256), 256, 0, s>>>(
-            p->n_segs, p->seg_ptr, p->seg_dst, p->key_vtx, F, d, p->kbuf, p->sbuf);
+            p->n_segs, p->seg_ptr, p->seg_dst, p->key_vtx, F, d, kb, p->sbuf);
         if (p->n_multi > 0)
             tfi::dev::bucket_combine<4><<<grid_for(p->n_multi * (d / 4), 256), 256, 0, s>>>(
-                p->n_multi, p->mb_key, p->mb_ptr, d, p->sbuf, p->kbuf);
+                p->n_multi, p->mb_key, p->mb_ptr, d, p->sbuf, kb);
     } else {
         tfi::dev::bucket_seg_kernel<T, 1><<<grid_for(p->n_segs * d, 256), 256, 0, s>>>(
-            p->n_segs, p->seg_ptr, p->seg_dst, p->key_vtx, F, d, p->kbuf, p->sbuf);
+            p->n_segs, p->seg_ptr, p->seg_dst, p->key_vtx, F, d, kb, p->sbuf);
         if (p->n_multi > 0)
             tfi::dev::bucket_combine<1><<<grid_for(p->n_multi * d, 256), 256, 0, s>>>(p->n_multi, p->mb_key,
-                                                                                     p->mb_ptr, d, p->sbuf, p->kbuf);
+                                                                                     p->mb_ptr, d, p->sbuf, kb);
     }
 }
 
@@ -1526,8 +1530,11 @@ tfi_status build_grad(tfi_plan_t p) {
     std::vector<int32_t> leaf_ptr(1, 0), hist_len;
     std::vector<int64_t> pair_off, hist_off;
     int64_t poff = 0;
+    int32_t leaf_max_n = 1, leaf_max_hl = 1;
     for (const tfi::Leaf &lf : hp.leaves) {
         const int64_t sz = lf.end - lf.begin;
+        leaf_max_n = std::max(leaf_max_n, int32_t(sz));
+        leaf_max_hl = std::max(leaf_max_hl, int32_t(lf.diam + 1));
         leaf_ptr.push_back(int32_t(lf.end));
         pair_off.push_back(poff);
         poff += sz * sz;
@@ -1549,10 +1556,16 @@ tfi_status build_grad(tfi_plan_t p) {
     void *q = nullptr;
     if (tfi_status rc = p->alloc(&q, size_t(std::max<int64_t>(hoff, 1)) * 4)) return rc;
     p->g_hist = static_cast<float *>(q);
-    if (tfi_status rc = p->alloc(&q, size_t(std::max<int64_t>(poff, 1)) * 4)) return rc;
-    p->g_pval = static_cast<float *>(q);
-    if (tfi_status rc = p->alloc(&q, size_t(std::max<int64_t>(poff, 1)) * 4)) return rc;
-    p->g_pdst = static_cast<int32_t *>(q);
+    p->g_leaf_max_n = leaf_max_n;
+    p->g_leaf_max_hl = leaf_max_hl;
+    p->g_leaf_onepass = tfi::grad::grad_leaf_warp_smem(leaf_max_n, leaf_max_hl) <= size_t(227 * 1024);
+    if (!p->g_leaf_onepass) {
+        // leaves with long histograms: pair values and distances in global memory, then binned
+        if (tfi_status rc = p->alloc(&q, size_t(std::max<int64_t>(poff, 1)) * 4)) return rc;
+        p->g_pval = static_cast<float *>(q);
+        if (tfi_status rc = p->alloc(&q, size_t(std::max<int64_t>(poff, 1)) * 4)) return rc;
+        p->g_pdst = static_cast<int32_t *>(q);
+    }
     if (tfi_status rc = p->alloc(&q, std::max<size_t>(1, hp.key_r.size()) * size_t(hp.max_channels) * 4)) return rc;
     p->g_gbuf = static_cast<float *>(q);
     if (tfi_status rc = p->alloc(&q, size_t(hp.hist_len) * 8)) return rc;
@@ -1581,10 +1594,9 @@ tfi_status kernel_grad_impl(tfi_plan_t p, const T *G, const T *F, int d, double 
     const tfi::HostPlan &hp = p->hp;
     const int64_t n_keys = int64_t(hp.key_r.size());
     if (n_keys > 0) {
-        tfi::dev::bucket_kernel<T, 1><<<grid_for(n_keys * d, 256), 256, 0, s>>>(n_keys, p->key_ptr, p->key_vtx, G, d,
-                                                                                p->g_gbuf);
-        tfi::dev::bucket_kernel<T, 1><<<grid_for(n_keys * d, 256), 256, 0, s>>>(n_keys, p->key_ptr, p->key_vtx, F, d,
-                                                                                p->kbuf);
+        // the bin sums of g and F, by the apply's segmented kernel (the same fixed summation order)
+        launch_bucket(p, G, d, s, p->g_gbuf);
+        launch_bucket(p, F, d, s, p->kbuf);
     }
     if (p->n_gjobs > 0) {
         const size_t smem = 2 * size_t(tfi::dev::padded_size(1 << p->g_max_lnp)) * sizeof(float2);
@@ -1602,7 +1614,14 @@ tfi_status kernel_grad_impl(tfi_plan_t p, const T *G, const T *F, int d, double 
                                                                    p->g_M, p->g_hist);
         }
     }
-    if (p->n_gleaves > 0) {
+    if (p->n_gleaves > 0 && p->g_leaf_onepass) {
+        const size_t smem = tfi::grad::grad_leaf_warp_smem(p->g_leaf_max_n, p->g_leaf_max_hl);
+        TFI_CUDA(cudaFuncSetAttribute(tfi::grad::grad_leaf_warp_hist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(smem)));
+        tfi::grad::grad_leaf_warp_hist<T><<<p->n_gleaves, 32 * tfi::grad::kGradLeafWarps, smem, s>>>(
+            p->g_leaf_ptr, p->g_hist_off, p->g_hist_len, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, G, F, d,
+            p->g_leaf_max_n, p->g_leaf_max_hl, p->g_hist);
+    } else if (p->n_gleaves > 0) {
         tfi::grad::grad_leaf_pairs<T><<<p->n_gleaves, 256, 0, s>>>(p->g_leaf_ptr, p->g_pair_off, p->leaf_vtx,
                                                                     p->leaf_dist, p->leaf_pdist, G, F, d, p->g_pval,
                                                                     p->g_pdst);

@@ -142,3 +142,33 @@ def test_grad_device_dtheta_on_a_side_stream():
     torch.cuda.synchronize()
     assert th1.is_cuda and np.array_equal(th1.cpu().numpy(), th0)
     assert torch.equal(C0, C1)
+
+
+@pytest.mark.parametrize("leaf_max", [512, 1024])
+def test_grad_large_leaves_deterministic(leaf_max):
+    # leaves of hundreds of vertices (the one-pass leaf histograms: 64-bit fixed-point sums, exact
+    # whatever the order of the atomic adds): oracle parity, and bit-identical repeated calls
+    cfg = W.configs.sweep(shape="rrt", n=8192, d=16, kernel="exp")
+    t = cfg["tree"]
+    p = _grad_case(t, cfg["delta"], cfg["kernel"], 16, leaf_max)
+    assert p.info()["sum_leaf_pairs"] > 1_000_000
+    G = torch.from_numpy(W.normal_field(t.n, 16, seed=31)).cuda()
+    F = torch.from_numpy(W.normal_field(t.n, 16, seed=32)).cuda()
+    C1, _ = p.kernel_grad(G, F)
+    C2, _ = p.kernel_grad(G, F)
+    assert torch.equal(C1, C2)
+
+
+@pytest.mark.parametrize("scale", [1e-18, 1e18])
+def test_grad_leaf_histograms_follow_the_field_scale(scale):
+    # the fixed-point scale adapts to each leaf's field norms: tiny and huge fields keep the bound
+    cfg = W.configs.rrt_n2000()
+    t = cfg["tree"]
+    p = tfi.Plan.from_spec(t, cfg["delta"], cfg["kernel"], leaf_max=256, max_channels=8)
+    G = torch.from_numpy((W.normal_field(t.n, 8, seed=33) * np.sqrt(scale)).astype(np.float32)).cuda()
+    F = torch.from_numpy((W.normal_field(t.n, 8, seed=34) * np.sqrt(scale)).astype(np.float32)).cuda()
+    C, _ = p.kernel_grad(G, F)
+    ref = brute.corr_hist(t, cfg["delta"], G.double().cpu().numpy(), F.double().cpu().numpy())
+    c = C.cpu().numpy()
+    ref = np.concatenate([ref, np.zeros(len(c) - len(ref))])
+    assert _nerr(c, ref) <= 1e-4
