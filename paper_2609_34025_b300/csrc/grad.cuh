@@ -252,7 +252,7 @@ __global__ void grad_leaf_hist(const int32_t *__restrict__ leaf_ptr, const int64
     }
 }
 
-// Leaves in one pass: one CTA per leaf, eight warps, each warp a block of 32
+// Leaves in one pass: one CTA per leaf (and group of channel blocks), eight warps, each warp a block of 32
 // targets (one per lane) against every source of the leaf, the channels in blocks
 // of 16 (the histogram is linear in the channels, so the blocks add up). The
 // pair distances follow the leaf walk of the apply: dhat(i, j) = D(i) + D(j) -
@@ -268,6 +268,71 @@ __global__ void grad_leaf_hist(const int32_t *__restrict__ leaf_ptr, const int64
 // each value is rounded once to a multiple of 2^-S (<= 2^-S / 2 from exact).
 constexpr int kGradLeafWarps = 8;
 
+// The scale exponent S of each leaf (above), from the largest squared row norms of g and F over
+// the leaf's vertices (all channels): one CTA per leaf.
+template <typename T>
+__global__ void grad_leaf_scale(const int32_t *__restrict__ leaf_ptr, const int32_t *__restrict__ leaf_vtx,
+                                const T *__restrict__ G, const T *__restrict__ F, int d, int32_t *__restrict__ S_out) {
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ float s_max[2][32];
+    const int lf = blockIdx.x;
+    const int lo = leaf_ptr[lf], n = leaf_ptr[lf + 1] - lo;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float mg = 0.f, mf = 0.f;
+    for (int i = warp; i < n; i += nw) {   // one warp per vertex, lanes over the channels
+        const int64_t v = leaf_vtx[lo + i];
+        float sg = 0.f, sf = 0.f;
+        for (int c = lane; c < d; c += 32) {
+            const float a = ldf<T>(G + v * d + c), b = ldf<T>(F + v * d + c);
+            sg = fmaf(a, a, sg);
+            sf = fmaf(b, b, sf);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sg += __shfl_xor_sync(FULL, sg, o);
+            sf += __shfl_xor_sync(FULL, sf, o);
+        }
+        mg = fmaxf(mg, sg);
+        mf = fmaxf(mf, sf);
+    }
+    if (lane == 0) {
+        s_max[0][warp] = mg;
+        s_max[1][warp] = mf;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) {
+            mg = fmaxf(mg, s_max[0][w]);
+            mf = fmaxf(mf, s_max[1][w]);
+        }
+        // B^2 = mg mf (the squared sums round up by at most a few ulps, covered by the margin)
+        int S = 0;
+        if (mg > 0.f && mf > 0.f) {
+            int eg, ef;
+            frexpf(mg, &eg);   // mg < 2^eg
+            frexpf(mf, &ef);
+            const int lb = (eg + ef + 1) / 2 + 1;          // B < 2^lb
+            const int ln2 = 2 * (32 - __clz(max(n, 1)));   // n^2 <= 2^ln2
+            S = 61 - ln2 - lb;
+        }
+        S_out[lf] = S;
+    }
+}
+
+// Leaves whose channel blocks were split over several CTAs: their exact integer sums, scaled
+// back by 2^-S, one CTA per leaf.
+// h64 holds the leaves' histograms from offset h64_base of hist (the leaves follow the jobs).
+__global__ void grad_leaf_h64_to_float(const int32_t *__restrict__ S_in, const int64_t *__restrict__ hist_off,
+                                       const int32_t *__restrict__ hist_len,
+                                       const unsigned long long *__restrict__ h64, int64_t h64_base,
+                                       float *__restrict__ hist) {
+    const int lf = blockIdx.x, S = S_in[lf];
+    const float inv1 = ldexpf(1.f, -(S / 2)), inv2 = ldexpf(1.f, -(S - S / 2));
+    const int64_t off = hist_off[lf];
+    for (int k = threadIdx.x; k < hist_len[lf]; k += blockDim.x)
+        hist[off + k] = float(static_cast<long long>(h64[off - h64_base + k])) * inv1 * inv2;
+}
+
 // the fixed-point histogram rounded up to an even count of 8-byte entries, so that the source
 // rows after it start on a 16-byte boundary (they are read as float4)
 __host__ __device__ inline int grad_leaf_hist_slots(int max_hl) { return (max_hl + 1) & ~1; }
@@ -280,7 +345,9 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kGradLeafWarps) grad_leaf_warp_hist(
     const int32_t *__restrict__ leaf_ptr, const int64_t *__restrict__ hist_off, const int32_t *__restrict__ hist_len,
     const int32_t *__restrict__ leaf_vtx, const int32_t *__restrict__ leaf_dist, const int32_t *__restrict__ leaf_pdist,
-    const T *__restrict__ G, const T *__restrict__ F, int d, int max_n, int max_hl, float *__restrict__ hist) {
+    const T *__restrict__ G, const T *__restrict__ F, int d, int max_n, int max_hl,
+    const int32_t *__restrict__ S_in, unsigned long long *__restrict__ h64_out, int64_t h64_base,
+    float *__restrict__ hist) {
     constexpr int INF = 0x7fffffff;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned long long smh[];
@@ -289,7 +356,6 @@ __global__ void __launch_bounds__(32 * kGradLeafWarps) grad_leaf_warp_hist(
     unsigned long long *h64 = smh;                                       // max_hl fixed-point sums
     float *sx = reinterpret_cast<float *>(smh + grad_leaf_hist_slots(max_hl));   // the block's source rows
     int *sdist = reinterpret_cast<int *>(sx + max_n * 16), *spd = sdist + max_n;
-    __shared__ float s_max[2][kGradLeafWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         sdist[i] = leaf_dist[lo + i];
@@ -297,52 +363,13 @@ __global__ void __launch_bounds__(32 * kGradLeafWarps) grad_leaf_warp_hist(
     }
     if (threadIdx.x == 0) spd[n] = INF;
     for (int k = threadIdx.x; k < hl; k += blockDim.x) h64[k] = 0ull;
-    // the scale: B = max ||g_i|| max ||F_j|| over the leaf (squared norms, then the root)
-    {
-        float mg = 0.f, mf = 0.f;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int64_t v = leaf_vtx[lo + i];
-            float sg = 0.f, sf = 0.f;
-            for (int c = 0; c < d; ++c) {
-                const float a = ldf<T>(G + v * d + c), b = ldf<T>(F + v * d + c);
-                sg = fmaf(a, a, sg);
-                sf = fmaf(b, b, sf);
-            }
-            mg = fmaxf(mg, sg);
-            mf = fmaxf(mf, sf);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mg = fmaxf(mg, __shfl_xor_sync(FULL, mg, o));
-            mf = fmaxf(mf, __shfl_xor_sync(FULL, mf, o));
-        }
-        if (lane == 0) {
-            s_max[0][warp] = mg;
-            s_max[1][warp] = mf;
-        }
-    }
-    __syncthreads();
-    float mg = 0.f, mf = 0.f;
-#pragma unroll
-    for (int w = 0; w < kGradLeafWarps; ++w) {
-        mg = fmaxf(mg, s_max[0][w]);
-        mf = fmaxf(mf, s_max[1][w]);
-    }
-    // B^2 = mg mf; ceil(log2 B) from the exponent of B^2 (rounded up, plus one for the rounding)
-    int S = 0;
-    if (mg > 0.f && mf > 0.f) {
-        int eg, ef;
-        frexpf(mg, &eg);   // mg < 2^eg
-        frexpf(mf, &ef);
-        const int lb = (eg + ef + 1) / 2 + 1;                           // B < 2^lb
-        const int ln2 = 2 * (32 - __clz(max(n, 1)));                    // n^2 <= 2^ln2
-        S = 61 - ln2 - lb;
-    }
+    const int S = S_in[lf];
     const float sc1 = ldexpf(1.f, S / 2), sc2 = ldexpf(1.f, S - S / 2);  // 2^S in two representable factors
     auto add = [&](int D, float v) {
         if (D >= 0 && D < hl) atomicAdd(&h64[D], static_cast<unsigned long long>(__float2ll_rn(v * sc1 * sc2)));
     };
-    for (int c0 = 0; c0 < d; c0 += 16) {
+    // this CTA's channel blocks: blockIdx.y, + gridDim.y, ...
+    for (int c0 = 16 * blockIdx.y; c0 < d; c0 += 16 * gridDim.y) {
         __syncthreads();
         for (int q = threadIdx.x; q < n * 16; q += blockDim.x) {
             const int j = q >> 4, c = q & 15;
@@ -412,10 +439,17 @@ __global__ void __launch_bounds__(32 * kGradLeafWarps) grad_leaf_warp_hist(
         }
     }
     __syncthreads();
-    float *out = hist + hist_off[lf];
-    const float inv1 = ldexpf(1.f, -(S / 2)), inv2 = ldexpf(1.f, -(S - S / 2));
-    for (int k = threadIdx.x; k < hl; k += blockDim.x)
-        out[k] = float(static_cast<long long>(h64[k])) * inv1 * inv2;
+    if (gridDim.y == 1) {
+        float *out = hist + hist_off[lf];
+        const float inv1 = ldexpf(1.f, -(S / 2)), inv2 = ldexpf(1.f, -(S - S / 2));
+        for (int k = threadIdx.x; k < hl; k += blockDim.x)
+            out[k] = float(static_cast<long long>(h64[k])) * inv1 * inv2;
+    } else {
+        // exact integer sums of the channel-block CTAs (zeroed beforehand), converted afterwards
+        unsigned long long *out = h64_out + (hist_off[lf] - h64_base);
+        for (int k = threadIdx.x; k < hl; k += blockDim.x)
+            if (h64[k]) atomicAdd(out + k, h64[k]);
+    }
 }
 
 // C[k] = sum over segments (fixed order) of sign * hist_segment[k], in FP64. One

@@ -133,6 +133,9 @@ struct tfi_plan_s {
     int32_t n_gjobs = 0, n_gleaves = 0, n_gseg = 0, g_max_lnp = 0, g_nblk = 1;
     int32_t g_leaf_max_n = 1, g_leaf_max_hl = 1;   // largest leaf and leaf histogram (one-pass leaf kernel)
     bool g_leaf_onepass = false;                    // its shared memory fits: no per-pair buffers
+    int32_t *g_leaf_S = nullptr;                    // per leaf: the fixed-point scale exponent
+    unsigned long long *g_h64 = nullptr;            // the leaves' fixed-point histograms (channel-block CTAs)
+    int64_t g_leaf_hbase = 0, g_leaf_hlen = 0;      // their range in g_hist
     int64_t *g_ditems = nullptr;
     int32_t *g_djobs = nullptr, n_gditems = 0, n_gdjobs = 0;
     float *g_M = nullptr;
@@ -1531,6 +1534,7 @@ tfi_status build_grad(tfi_plan_t p) {
     std::vector<int64_t> pair_off, hist_off;
     int64_t poff = 0;
     int32_t leaf_max_n = 1, leaf_max_hl = 1;
+    const int64_t leaf_hbase = hoff;
     for (const tfi::Leaf &lf : hp.leaves) {
         const int64_t sz = lf.end - lf.begin;
         leaf_max_n = std::max(leaf_max_n, int32_t(sz));
@@ -1559,7 +1563,14 @@ tfi_status build_grad(tfi_plan_t p) {
     p->g_leaf_max_n = leaf_max_n;
     p->g_leaf_max_hl = leaf_max_hl;
     p->g_leaf_onepass = tfi::grad::grad_leaf_warp_smem(leaf_max_n, leaf_max_hl) <= size_t(227 * 1024);
-    if (!p->g_leaf_onepass) {
+    p->g_leaf_hbase = leaf_hbase;
+    p->g_leaf_hlen = hoff - leaf_hbase;
+    if (p->g_leaf_onepass) {
+        if (tfi_status rc = p->alloc(&q, std::max<size_t>(1, hp.leaves.size()) * 4)) return rc;
+        p->g_leaf_S = static_cast<int32_t *>(q);
+        if (tfi_status rc = p->alloc(&q, size_t(std::max<int64_t>(p->g_leaf_hlen, 1)) * 8)) return rc;
+        p->g_h64 = static_cast<unsigned long long *>(q);
+    } else {
         // leaves with long histograms: pair values and distances in global memory, then binned
         if (tfi_status rc = p->alloc(&q, size_t(std::max<int64_t>(poff, 1)) * 4)) return rc;
         p->g_pval = static_cast<float *>(q);
@@ -1618,9 +1629,19 @@ tfi_status kernel_grad_impl(tfi_plan_t p, const T *G, const T *F, int d, double 
         const size_t smem = tfi::grad::grad_leaf_warp_smem(p->g_leaf_max_n, p->g_leaf_max_hl);
         TFI_CUDA(cudaFuncSetAttribute(tfi::grad::grad_leaf_warp_hist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       int(smem)));
-        tfi::grad::grad_leaf_warp_hist<T><<<p->n_gleaves, 32 * tfi::grad::kGradLeafWarps, smem, s>>>(
+        tfi::grad::grad_leaf_scale<T><<<p->n_gleaves, 256, 0, s>>>(p->g_leaf_ptr, p->leaf_vtx, G, F, d, p->g_leaf_S);
+        // few leaves with many channels: their channel blocks spread over CTAs, whose exact integer
+        // sums are merged in global memory
+        const int nblk = (d + 15) / 16;
+        const int groups = std::max(1, std::min(nblk, (2 * device_sms() + p->n_gleaves - 1) / p->n_gleaves));
+        if (groups > 1) TFI_CUDA(cudaMemsetAsync(p->g_h64, 0, size_t(p->g_leaf_hlen) * 8, s));
+        tfi::grad::grad_leaf_warp_hist<T><<<dim3(unsigned(p->n_gleaves), unsigned(groups)),
+                                            32 * tfi::grad::kGradLeafWarps, smem, s>>>(
             p->g_leaf_ptr, p->g_hist_off, p->g_hist_len, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, G, F, d,
-            p->g_leaf_max_n, p->g_leaf_max_hl, p->g_hist);
+            p->g_leaf_max_n, p->g_leaf_max_hl, p->g_leaf_S, p->g_h64, p->g_leaf_hbase, p->g_hist);
+        if (groups > 1)
+            tfi::grad::grad_leaf_h64_to_float<<<p->n_gleaves, 256, 0, s>>>(p->g_leaf_S, p->g_hist_off, p->g_hist_len,
+                                                                           p->g_h64, p->g_leaf_hbase, p->g_hist);
     } else if (p->n_gleaves > 0) {
         tfi::grad::grad_leaf_pairs<T><<<p->n_gleaves, 256, 0, s>>>(p->g_leaf_ptr, p->g_pair_off, p->leaf_vtx,
                                                                     p->leaf_dist, p->leaf_pdist, G, F, d, p->g_pval,

@@ -172,3 +172,18 @@ def test_grad_leaf_histograms_follow_the_field_scale(scale):
     c = C.cpu().numpy()
     ref = np.concatenate([ref, np.zeros(len(c) - len(ref))])
     assert _nerr(c, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 1e-4), (torch.bfloat16, 1e-4)])
+def test_grad_few_leaves_many_channels(dtype, tol):
+    # a few big leaves and many channel blocks: the blocks spread over CTAs whose exact integer sums
+    # are merged in global memory (same result whatever the split)
+    rng = np.random.default_rng(41)
+    t = W.random_recursive(700, rng)
+    t = t.with_weights(W.trees.integer_weights(t.m, 1, 4, rng))
+    for d in (48, 200):
+        p = _grad_case(t, 1.0, W.KernelSpec.exp(0.05), d, 1024, dtype=dtype, tol=tol)
+        assert p.info()["n_calls"] == 0   # the whole tree is one leaf
+        G = torch.from_numpy(W.normal_field(t.n, d, seed=31)).cuda().to(dtype)
+        F = torch.from_numpy(W.normal_field(t.n, d, seed=32)).cuda().to(dtype)
+        assert torch.equal(p.kernel_grad(G, F)[0], p.kernel_grad(G, F)[0])
