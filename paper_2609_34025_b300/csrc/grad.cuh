@@ -191,6 +191,68 @@ __global__ void grad_direct_bin(const GradJob *__restrict__ jobs, const int32_t 
     }
 }
 
+// Direct jobs, pass 2 in one sweep over the pairs: M[i][l] = sum of the ncb channel blocks'
+// partials (in block order), then every pair adds M[i][l] into a shared-memory histogram of
+// 64-bit fixed-point integers at r_i + r_l + |x_i - x_l| (exact, so the order of the atomic adds
+// does not matter), with the scale 2^S, S = 61 - ceil(log2 nk^2) - ceil(log2 max |M|), that no sum
+// can overflow. The job's keys are staged in shared memory. One CTA per job; the plan uses it when
+// its histograms and keys fit (8 K + 8 nk bytes).
+__host__ __device__ inline size_t grad_direct_bin_smem(int max_k, int max_nk) {
+    return size_t((max_k + 1) & ~1) * 8 + size_t(max_nk) * 8 + 64;
+}
+
+__global__ void __launch_bounds__(256) grad_direct_bin_fx(const GradJob *__restrict__ jobs,
+                                                          const int32_t *__restrict__ djobs, int ncb,
+                                                          const int32_t *__restrict__ key_r,
+                                                          const int32_t *__restrict__ key_x, int max_k,
+                                                          float *__restrict__ M, float *__restrict__ hist) {
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned long long shd[];
+    __shared__ float s_max[8];
+    const GradJob jb = jobs[djobs[blockIdx.x]];
+    const int nk = jb.ke - jb.kb;
+    const int K = 2 * jb.maxr + jb.maxx + 1;
+    const int64_t nn = int64_t(nk) * nk;
+    unsigned long long *h64 = shd;
+    int *sr = reinterpret_cast<int *>(shd + ((max_k + 1) & ~1)), *sx = sr + nk;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) h64[k] = 0ull;
+    for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+        sr[i] = key_r[jb.kb + i];
+        sx[i] = key_x[jb.kb + i];
+    }
+    float mx = 0.f;
+    for (int64_t q = threadIdx.x; q < nn; q += blockDim.x) {
+        float acc = M[jb.moff + q];
+        for (int b = 1; b < ncb; ++b) acc += M[jb.moff + b * nn + q];
+        M[jb.moff + q] = acc;
+        mx = fmaxf(mx, fabsf(acc));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.f;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) mx = fmaxf(mx, s_max[w]);
+    int S = 0;
+    if (mx > 0.f) {
+        int e;
+        frexpf(mx, &e);                                              // mx < 2^e
+        const int ln2 = 64 - __clzll(static_cast<unsigned long long>(nn));   // nn < 2^ln2
+        S = 61 - ln2 - e;
+    }
+    const float sc1 = ldexpf(1.f, S / 2), sc2 = ldexpf(1.f, S - S / 2);
+    for (int64_t q = threadIdx.x; q < nn; q += blockDim.x) {
+        const int i = int(q / nk), l = int(q - int64_t(i) * nk);
+        const int D = sr[i] + sr[l] + abs(sx[i] - sx[l]);
+        const float v = M[jb.moff + q];
+        if (D < K && v != 0.f) atomicAdd(&h64[D], static_cast<unsigned long long>(__float2ll_rn(v * sc1 * sc2)));
+    }
+    __syncthreads();
+    const float inv1 = ldexpf(1.f, -(S / 2)), inv2 = ldexpf(1.f, -(S - S / 2));
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        hist[jb.hoff + k] = float(static_cast<long long>(h64[k])) * inv1 * inv2;
+}
+
 template <typename T>
 __device__ __forceinline__ float ldf(const T *p);
 template <>
@@ -454,16 +516,23 @@ __global__ void __launch_bounds__(32 * kGradLeafWarps) grad_leaf_warp_hist(
 
 // C[k] = sum over segments (fixed order) of sign * hist_segment[k], in FP64. One
 // warp per k: lanes take segments 32 apart, then a butterfly of shuffles (fixed
-// order) adds the lanes' partial sums.
+// order) adds the lanes' partial sums. The segments come sorted by length, longest
+// first, so those with an entry k are a prefix, found by bisection: the work is the
+// total histogram length, not segments x lengths.
 __global__ void grad_reduce(int n_seg, const int64_t *__restrict__ seg_off, const int32_t *__restrict__ seg_len,
                             const float *__restrict__ seg_sign, const float *__restrict__ hist, int64_t len,
                             double *__restrict__ C) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
     for (int64_t k = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5); k < len; k += warps) {
+        int lo = 0, hi = n_seg;   // the segments with seg_len > k: [0, lo)
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (seg_len[mid] > k) lo = mid + 1;
+            else hi = mid;
+        }
         double acc = 0.0;
-        for (int sgm = lane; sgm < n_seg; sgm += 32)
-            if (k < seg_len[sgm]) acc += double(seg_sign[sgm]) * double(hist[seg_off[sgm] + k]);
+        for (int sgm = lane; sgm < lo; sgm += 32) acc += double(seg_sign[sgm]) * double(hist[seg_off[sgm] + k]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) C[k] = acc;

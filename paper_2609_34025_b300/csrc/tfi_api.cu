@@ -138,6 +138,7 @@ struct tfi_plan_s {
     int64_t g_leaf_hbase = 0, g_leaf_hlen = 0;      // their range in g_hist
     int64_t *g_ditems = nullptr;
     int32_t *g_djobs = nullptr, n_gditems = 0, n_gdjobs = 0;
+    int32_t g_dir_max_k = 1, g_dir_max_nk = 1;   // direct gradient jobs: largest histogram and key count
     float *g_M = nullptr;
     tfi::grad::GradJob *g_jobs = nullptr;
     int32_t *g_leaf_ptr = nullptr, *g_hist_len = nullptr, *g_seg_len = nullptr, *g_pdst = nullptr;
@@ -1522,6 +1523,8 @@ tfi_status build_grad(tfi_plan_t p) {
             for (int32_t a = 0; a < nt; ++a)
                 for (int32_t b = 0; b < nt; ++b) ditems.push_back((int64_t(gj.size() - 1) << 16) | (a << 8) | b);
             djobs.push_back(int32_t(gj.size() - 1));
+            p->g_dir_max_k = std::max(p->g_dir_max_k, 2 * j.maxr + j.maxx + 1);
+            p->g_dir_max_nk = std::max(p->g_dir_max_nk, int32_t(j.ke - j.kb));
             moff += int64_t(j.ke - j.kb) * (j.ke - j.kb) * ncb_max;  // one partial product per channel block
         }
         seg_off.push_back(hoff);
@@ -1548,6 +1551,23 @@ tfi_status build_grad(tfi_plan_t p) {
         seg_len.push_back(int32_t(lf.diam + 1));
         seg_sign.push_back(1.f);
         hoff += lf.diam + 1;
+    }
+    {
+        // segments longest first (grad_reduce's prefix search), ties in their original order
+        std::vector<size_t> ord(seg_len.size());
+        for (size_t q = 0; q < ord.size(); ++q) ord[q] = q;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return seg_len[a] > seg_len[b]; });
+        std::vector<int64_t> so(ord.size());
+        std::vector<int32_t> sl(ord.size());
+        std::vector<float> ss(ord.size());
+        for (size_t q = 0; q < ord.size(); ++q) {
+            so[q] = seg_off[ord[q]];
+            sl[q] = seg_len[ord[q]];
+            ss[q] = seg_sign[ord[q]];
+        }
+        seg_off.swap(so);
+        seg_len.swap(sl);
+        seg_sign.swap(ss);
     }
     if (tfi_status rc = p->upload(&p->g_jobs, gj)) return rc;
     if (tfi_status rc = p->upload(&p->g_leaf_ptr, leaf_ptr)) return rc;
@@ -1621,6 +1641,14 @@ tfi_status kernel_grad_impl(tfi_plan_t p, const T *G, const T *F, int d, double 
             const int ncb = (d + tfi::grad::kGradDotCB - 1) / tfi::grad::kGradDotCB;
             tfi::grad::grad_pair_dots<<<dim3(unsigned(p->n_gditems), unsigned(ncb)), 256, 0, s>>>(
                 p->g_jobs, p->g_ditems, d, p->g_gbuf, p->kbuf, p->g_M);
+            const size_t dsm = tfi::grad::grad_direct_bin_smem(p->g_dir_max_k, p->g_dir_max_nk);
+            if (dsm <= size_t(200 * 1024)) {
+                TFI_CUDA(cudaFuncSetAttribute(tfi::grad::grad_direct_bin_fx,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(dsm)));
+                tfi::grad::grad_direct_bin_fx<<<p->n_gdjobs, 256, dsm, s>>>(p->g_jobs, p->g_djobs, ncb, p->key_r,
+                                                                            p->key_x, p->g_dir_max_k, p->g_M,
+                                                                            p->g_hist);
+            } else
             tfi::grad::grad_direct_bin<<<p->n_gdjobs, 128, 0, s>>>(p->g_jobs, p->g_djobs, ncb, p->key_r, p->key_x,
                                                                    p->g_M, p->g_hist);
         }
