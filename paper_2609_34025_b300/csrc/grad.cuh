@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include "kernels.cuh"
+#include "fft_x2.cuh"
 
 namespace tfi {
 namespace grad {
@@ -49,7 +50,8 @@ __global__ void grad_fft_kernel(const GradJob *__restrict__ jobs, const int32_t 
                                 float *__restrict__ hist) {
     extern __shared__ float2 smz[];
     const GradJob jb = jobs[blockIdx.x];
-    if (jb.mode != 0) return;  // evaluated by grad_pair_dots / grad_direct_bin
+    // direct jobs: grad_pair_dots / grad_direct_bin; one-dimensional FFT jobs: grad_fft1d_x2_kernel
+    if (jb.mode != 0 || (jb.lp2 == 0 && jb.lp1 >= 1)) return;
     const int lp1 = jb.lp1, lp2 = jb.lp2, lnp = lp1 + lp2;
     const int NP = 1 << lnp, P1 = 1 << lp1, P2 = 1 << lp2;
     const int padnp = padded_size(NP);
@@ -105,6 +107,75 @@ __global__ void grad_fft_kernel(const GradJob *__restrict__ jobs, const int32_t 
         }
         hblk[jb.hoff + k] = acc * inv;
     }
+}
+
+// One-dimensional FFT jobs (lp2 = 0) on the paired-FP32 transforms of the apply: one CTA per
+// job and block of kGradCB channels, as grad_fft_kernel, but two channels per transform: the
+// element of depth r holds z_c = gsum_c + i fsum_c for channels c and c + 1 (lane pairs), and the
+// forward transform of fwd_1d_x2 gives both spectra at once. Per channel the correlation spectrum
+// is A^ B^ = (z(f)^2 - conj z(-f)^2) / 4i, summed over the block's channels (in channel order)
+// into ACC; then, as in grad_fft_kernel, the inverse transform and the binning along depth.
+// Shared memory: NP 16-byte elements and padded_size(NP) complex accumulators.
+__global__ void __launch_bounds__(256) grad_fft1d_x2_kernel(const GradJob *__restrict__ jobs,
+                                                            const int32_t *__restrict__ ids,
+                                                            const int32_t *__restrict__ key_r, int d,
+                                                            const float *__restrict__ gsum,
+                                                            const float *__restrict__ fsum,
+                                                            const float2 *__restrict__ tw,
+                                                            const ulonglong2 *__restrict__ twb,
+                                                            float *__restrict__ hist) {
+    extern __shared__ ulonglong2 gzx[];
+    const GradJob jb = jobs[ids[blockIdx.x]];
+    const int ln = jb.lp1, NP = 1 << ln;
+    const int padnp = padded_size(NP);
+    ulonglong2 *Zx = gzx;
+    float2 *ACC = reinterpret_cast<float2 *>(gzx + NP);
+    for (int i = threadIdx.x; i < padnp; i += blockDim.x) ACC[i] = make_float2(0.f, 0.f);
+    const int nk = jb.ke - jb.kb;
+    const int cb0 = blockIdx.y * kGradCB, cb1 = min(d, cb0 + kGradCB);
+    for (int c = cb0; c < cb1; c += 2) {
+        const bool two = c + 1 < cb1;
+        for (int i = threadIdx.x; i < NP; i += blockDim.x) Zx[i] = make_ulonglong2(0ull, 0ull);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nk; t += blockDim.x) {
+            const int64_t k = jb.kb + t;
+            const float g0 = gsum[k * d + c], f0 = fsum[k * d + c];
+            const float g1 = two ? gsum[k * d + c + 1] : 0.f, f1 = two ? fsum[k * d + c + 1] : 0.f;
+            Zx[dev::swz(key_r[k])] = make_ulonglong2(dev::vpack(g0, g1), dev::vpack(f0, f1));
+        }
+        __syncthreads();
+        dev::fwd_1d_x2(Zx, NP, 1, ln, tw, twb);
+        for (int e = threadIdx.x; e < NP; e += blockDim.x) {
+            const int f = brev_bits(e, ln), q = brev_bits((NP - f) & (NP - 1), ln);
+            const ulonglong2 a = Zx[dev::swz(e)], b = Zx[dev::swz(q)];
+            float zr0, zr1, zi0, zi1, wr0, wr1, wi0, wi1;
+            dev::vunpack(a.x, zr0, zr1);
+            dev::vunpack(a.y, zi0, zi1);
+            dev::vunpack(b.x, wr0, wr1);
+            dev::vunpack(b.y, wi0, wi1);
+            // z^2 - conj(w)^2 per channel: real (zr^2 - zi^2) - (wr^2 - wi^2), imaginary 2 zr zi + 2 wr wi
+            const float re0 = (zr0 * zr0 - zi0 * zi0) - (wr0 * wr0 - wi0 * wi0);
+            const float im0 = 2.f * (zr0 * zi0 + wr0 * wi0);
+            const float re1 = (zr1 * zr1 - zi1 * zi1) - (wr1 * wr1 - wi1 * wi1);
+            const float im1 = 2.f * (zr1 * zi1 + wr1 * wi1);
+            // / (4 i): (im, -re) / 4; channel c first, then c + 1
+            float2 acc = ACC[padded(e)];
+            acc.x += 0.25f * im0;
+            acc.y += -0.25f * re0;
+            if (two) {
+                acc.x += 0.25f * im1;
+                acc.y += -0.25f * re1;
+            }
+            ACC[padded(e)] = acc;
+        }
+        __syncthreads();
+    }
+    dev::fft_axis<true>(ACC, padnp, 1, ln, 1, 0, 1, true, tw, false);
+    __syncthreads();
+    const float inv = 1.f / float(NP);
+    const int K = 2 * jb.maxr + 1;
+    float *hblk = hist + int64_t(blockIdx.y) * K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) hblk[jb.hoff + k] = ACC[padded(k)].x * inv;
 }
 
 // The job's histogram (block 0's slot) = its first nblk channel blocks' histograms added in block order.

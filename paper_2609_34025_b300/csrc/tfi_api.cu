@@ -139,6 +139,9 @@ struct tfi_plan_s {
     int64_t *g_ditems = nullptr;
     int32_t *g_djobs = nullptr, n_gditems = 0, n_gdjobs = 0;
     int32_t g_dir_max_k = 1, g_dir_max_nk = 1;   // direct gradient jobs: largest histogram and key count
+    int32_t *g_fft1d = nullptr;                    // one-dimensional FFT gradient jobs (paired-FP32 kernel),
+    int32_t n_gfft1d = 0;                          // grouped by transform size: class ln holds
+    std::vector<int32_t> g_fft1d_cls;              // g_fft1d[cls[ln] .. cls[ln + 1]) (ln = 0 .. 14)
     float *g_M = nullptr;
     tfi::grad::GradJob *g_jobs = nullptr;
     int32_t *g_leaf_ptr = nullptr, *g_hist_len = nullptr, *g_seg_len = nullptr, *g_pdst = nullptr;
@@ -1504,12 +1507,12 @@ tfi_status build_grad(tfi_plan_t p) {
     for (const tfi::Job &j : gjobs) {
         if (j.ke == j.kb) continue;
         const int32_t len = 2 * j.maxr + j.maxx + 1;
-        // direct evaluation (pair dot products over the channels, then binning) when it is cheaper
+        // direct evaluation (pair dot products over the channels, then one binning pass) when it is cheaper
         // than one FFT correlation per channel at max_channels; a table beyond one shared-memory
         // transform (P1 P2 > 2^13) takes the direct evaluation whatever its size class
         const double nk = double(j.ke - j.kb), D = double(hp.max_channels);
         const double np = std::ldexp(1.0, j.lp1 + j.lp2);
-        const double cost_direct = 2 * nk * nk * D + double(len) * nk * nk;
+        const double cost_direct = 2 * nk * nk * D + 64 * nk * nk;   // pair dot products, one binning pass
         const double cost_fft = D * (5 * np * std::max(1, j.lp1 + j.lp2) + 10 * np);
         const bool fft_ok = j.lp1 + j.lp2 <= 13, direct_ok = nk <= 32 * 255;
         if (!fft_ok && !direct_ok)
@@ -1568,6 +1571,18 @@ tfi_status build_grad(tfi_plan_t p) {
         seg_off.swap(so);
         seg_len.swap(sl);
         seg_sign.swap(ss);
+    }
+    {
+        std::vector<int32_t> f1;
+        p->g_fft1d_cls.assign(16, 0);
+        for (int ln = 1; ln <= 14; ++ln) {
+            p->g_fft1d_cls[size_t(ln)] = int32_t(f1.size());
+            for (size_t q = 0; q < gj.size(); ++q)
+                if (gj[q].mode == 0 && gj[q].lp2 == 0 && gj[q].lp1 == ln) f1.push_back(int32_t(q));
+        }
+        p->g_fft1d_cls[15] = int32_t(f1.size());
+        if (tfi_status rc = p->upload(&p->g_fft1d, f1)) return rc;
+        p->n_gfft1d = int32_t(f1.size());
     }
     if (tfi_status rc = p->upload(&p->g_jobs, gj)) return rc;
     if (tfi_status rc = p->upload(&p->g_leaf_ptr, leaf_ptr)) return rc;
@@ -1636,6 +1651,17 @@ tfi_status kernel_grad_impl(tfi_plan_t p, const T *G, const T *F, int d, double 
         const int nb = (d + tfi::grad::kGradCB - 1) / tfi::grad::kGradCB;  // channel blocks with channels
         tfi::grad::grad_fft_kernel<<<dim3(unsigned(p->n_gjobs), unsigned(nb)), 256, smem, s>>>(
             p->g_jobs, p->key_r, p->key_x, d, p->g_gbuf, p->kbuf, p->twiddle, p->g_hist);
+        // one launch per transform size, each with the shared memory of its size
+        for (int ln = 1; ln <= 14 && p->n_gfft1d > 0; ++ln) {
+            const int b0 = p->g_fft1d_cls[size_t(ln)], b1 = p->g_fft1d_cls[size_t(ln) + 1];
+            if (b1 == b0) continue;
+            const size_t sm1 = size_t(1 << ln) * 16 + size_t(tfi::dev::padded_size(1 << ln)) * sizeof(float2);
+            TFI_CUDA(cudaFuncSetAttribute(tfi::grad::grad_fft1d_x2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(sm1)));
+            tfi::grad::grad_fft1d_x2_kernel<<<dim3(unsigned(b1 - b0), unsigned(nb)), 256, sm1, s>>>(
+                p->g_jobs, p->g_fft1d + b0, p->key_r, d, p->g_gbuf, p->kbuf, p->twiddle,
+                reinterpret_cast<const ulonglong2 *>(p->twiddle_b), p->g_hist);
+        }
         if (nb > 1) tfi::grad::grad_block_reduce<<<p->n_gjobs, 128, 0, s>>>(p->g_jobs, p->n_gjobs, nb, p->g_hist);
         if (p->n_gditems > 0) {
             const int ncb = (d + tfi::grad::kGradDotCB - 1) / tfi::grad::kGradDotCB;
