@@ -270,6 +270,26 @@ def dense_baseline(a, n=1 << 16, reps=5):
 # ---------------------------------------------------------------------------
 # the same exponential workload with Algorithm 7 sweeps as the table evaluator
 # ---------------------------------------------------------------------------
+def kernel_grad_timing(plan, F, G, fwd_ms, reps=5):
+    """dL/df (the pair histogram C[k]) and dL/dtheta for the learnable kernel on the headline plan,
+    the parameter gradient left on the device: CUDA events around `reps` calls after two warm-ups."""
+    import torch
+
+    for _ in range(2):
+        plan.kernel_grad(G, F, device_dtheta=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.kernel_grad(G, F, device_dtheta=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"ms_per_call": ms, "vs_forward_apply": ms / fwd_ms, "calls": reps,
+            "what": "tfi_kernel_grad(grad_out, F): C[k] = dL/df(k delta) for every grid distance and dL/dtheta, "
+                    "same tree, kernel and d as the headline"}
+
+
 def sweep_evaluator(a, cfg, F, G, steps=10):
     """Algorithm 7 (exponential sweeps) on the same tree, field and kernel: for
     every table (TFI_PLAN_SWEEP) and per table where the cost model prefers it
@@ -541,6 +561,7 @@ def run_ours(a):
     cpu = cpu_baseline(cfg, F_np, G_np, budget_s=a.cpu_budget) if a.cpu_budget > 0 else None
     dense = dense_baseline(a, n=a.dense_n) if a.dense else None
     sweep = sweep_evaluator(a, cfg, F, G) if a.kernel == "exp" else None
+    grad = kernel_grad_timing(plan, F, G, fwd_ms)
     info = plan.info()
     plan.close()
     del F, G, out, gF, flush
@@ -556,6 +577,7 @@ def run_ours(a):
                                    "plan_levels": info["n_levels"], "sms": n_sms}),
         "fwd_value": world * n * d / (fwd_ms / 1e3), "fwd_ms": fwd_ms,
         "roofline": roof, "cpu_baseline": cpu, "dense_baseline": dense, "sweep_evaluator": sweep,
+        "kernel_grad": grad,
         "c2_sweep": c2,
         "e2e": {"value": world * n * d * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * n * d * 4,
                 "d2h_bytes_per_step": 2 * n * d * 4, "ms_per_step": 1e3 * e2e_s / a.steps,
