@@ -509,7 +509,12 @@ __global__ void __launch_bounds__(32 * kGradLeafWarps) grad_leaf_warp_hist(
             sx[q] = c0 + c < d ? ldf<T>(F + int64_t(leaf_vtx[lo + j]) * d + c0 + c) : 0.f;
         }
         __syncthreads();
-        for (int a = warp * 32; a < n; a += kGradLeafWarps * 32) {
+        // work units: (target block, part), part 0 the sources inside the block and after it, part 1
+        // those before it, so that a leaf of few blocks still keeps the eight warps busy
+        const int nblk = (n + 31) / 32;
+        for (int u = warp; u < 2 * nblk; u += kGradLeafWarps) {
+            const int a = (u >> 1) * 32, part = u & 1;
+            if (part == 1 && a == 0) continue;   // nothing before the first block (warp-uniform)
             const int bend = min(a + 32, n);
             const int ti = a + lane;
             const bool act = ti < n;
@@ -520,30 +525,23 @@ __global__ void __launch_bounds__(32 * kGradLeafWarps) grad_leaf_warp_hist(
 #pragma unroll
                 for (int c = 0; c < 16; ++c) g[c] = (act && c0 + c < d) ? ldf<T>(G + vi * d + c0 + c) : 0.f;
             }
+            // <g_i, x_j> as paired FP32 FMAs: lanes (even, odd channels), added at the end
+            dev::f32x2 gp[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) gp[c] = dev::vpack(g[2 * c], g[2 * c + 1]);
             auto dot = [&](int j) {
                 const float4 *x = reinterpret_cast<const float4 *>(sx + j * 16);
-                float s0 = 0.f, s1 = 0.f;
+                dev::f32x2 s = 0ull;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float4 r = x[q];
-                    s0 = fmaf(g[4 * q], r.x, s0);
-                    s1 = fmaf(g[4 * q + 1], r.y, s1);
-                    s0 = fmaf(g[4 * q + 2], r.z, s0);
-                    s1 = fmaf(g[4 * q + 3], r.w, s1);
+                    s = dev::vfma(gp[2 * q], dev::vpack(r.x, r.y), s);
+                    s = dev::vfma(gp[2 * q + 1], dev::vpack(r.z, r.w), s);
                 }
+                float s0, s1;
+                dev::vunpack(s, s0, s1);
                 return s0 + s1;
             };
-            // sources inside the block: ascending for j >= i (j = i at distance 0), descending for j < i
-            int m = INF;
-            for (int j = a; j < bend; ++j) {
-                if (j > ti) m = min(m, spd[j]);
-                add(!act || j < ti ? -1 : j == ti ? 0 : Di + sdist[j] - 2 * m, dot(j));
-            }
-            m = INF;
-            for (int j = bend - 1; j >= a; --j) {
-                if (j < ti) m = min(m, spd[j + 1]);
-                add(act && j < ti ? Di + sdist[j] - 2 * m : -1, dot(j));
-            }
             // carries: suffix min over (i, bend - 1], prefix min over (a, i]
             int suf = (a + lane + 1 < bend) ? spd[a + lane + 1] : INF;
 #pragma unroll
@@ -557,17 +555,31 @@ __global__ void __launch_bounds__(32 * kGradLeafWarps) grad_leaf_warp_hist(
                 const int u = __shfl_up_sync(FULL, pre, o);
                 if (lane >= o) pre = min(pre, u);
             }
+            int m = INF;
+            if (part == 0) {
+            // sources inside the block: ascending for j >= i (j = i at distance 0), descending for j < i
+            for (int j = a; j < bend; ++j) {
+                if (j > ti) m = min(m, spd[j]);
+                add(!act || j < ti ? -1 : j == ti ? 0 : Di + sdist[j] - 2 * m, dot(j));
+            }
+            m = INF;
+            for (int j = bend - 1; j >= a; --j) {
+                if (j < ti) m = min(m, spd[j + 1]);
+                add(act && j < ti ? Di + sdist[j] - 2 * m : -1, dot(j));
+            }
             // sources after the block, ascending
             m = suf;
             for (int j = bend; j < n; ++j) {
                 m = min(m, spd[j]);
                 add(act ? Di + sdist[j] - 2 * m : -1, dot(j));
             }
+            } else {
             // sources before the block, descending
             m = pre;
             for (int j = a - 1; j >= 0; --j) {
                 m = min(m, spd[j + 1]);
                 add(act ? Di + sdist[j] - 2 * m : -1, dot(j));
+            }
             }
         }
     }
