@@ -458,49 +458,6 @@ __device__ __forceinline__ void fft_1d_x2(ulonglong2 *Z, int NP, int nplane, int
     }
 }
 
-// The forward half of fft_1d_x2 alone: the same passes, the span-1 pass without the
-// spectrum product and the inverse. The result is in bit-reversed order (element e
-// holds frequency brev(e) of both of its complex values).
-template <int RL>
-__device__ __forceinline__ void bottom_fwd_1d_x2(ulonglong2 *Z, int NP, int nplane, int ln) {
-    constexpr int R = 1 << RL;
-    const int glog = ln - RL;
-    const int total = nplane << glog;
-    const int gmask = (1 << glog) - 1;
-    for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        const int g = w & gmask, p = w >> glog;
-        const int e0 = g << RL;
-        ulonglong2 *Zp = Z + p * NP;
-        int adr[R];
-        slots_1d<RL, 0>(e0, adr);
-        Cx2 v[R];
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-            const ulonglong2 q = Zp[adr[t]];
-            v[t] = Cx2{q.x, q.y};
-        }
-        dft_dif_x2<RL>(v);
-#pragma unroll
-        for (int t = 0; t < R; ++t) Zp[adr[t]] = make_ulonglong2(v[t].re, v[t].im);
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ void fwd_1d_x2(ulonglong2 *Z, int NP, int nplane, int ln, const float2 *__restrict__ tw,
-                                          const ulonglong2 *__restrict__ twb) {
-    const int full = ln / 3, rem = ln - 3 * full;
-    if (full > 0) {
-        if (rem == 2) pass_1d_dispatch<false, 2>(Z, NP, nplane, ln, ln - 2, tw, twb);
-        else if (rem == 1) pass_1d_dispatch<false, 1>(Z, NP, nplane, ln, ln - 1, tw, twb);
-        for (int k = 0; k < full - 1; ++k) pass_1d_dispatch<false, 3>(Z, NP, nplane, ln, ln - rem - 3 * (k + 1), tw, twb);
-        bottom_fwd_1d_x2<3>(Z, NP, nplane, ln);
-    } else if (rem == 2) {
-        bottom_fwd_1d_x2<2>(Z, NP, nplane, ln);
-    } else {
-        bottom_fwd_1d_x2<1>(Z, NP, nplane, ln);
-    }
-}
-
 // One CTA per (job, up to 2 * nplane channel pairs starting at pair0): plane
 // p holds pairs pair0 + 2p and pair0 + 2p + 1 (channels 2 pair0 + 4p .. + 3);
 // channels at or beyond d ride as zeros.

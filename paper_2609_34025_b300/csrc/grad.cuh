@@ -109,6 +109,49 @@ __global__ void grad_fft_kernel(const GradJob *__restrict__ jobs, const int32_t 
     }
 }
 
+// The forward half of the apply's fft_1d_x2 alone: the same passes, the span-1 pass without the
+// spectrum product and the inverse. The result is in bit-reversed order (element e
+// holds frequency brev(e) of both of its complex values).
+template <int RL>
+__device__ __forceinline__ void bottom_fwd_1d_x2(ulonglong2 *Z, int NP, int nplane, int ln) {
+    constexpr int R = 1 << RL;
+    const int glog = ln - RL;
+    const int total = nplane << glog;
+    const int gmask = (1 << glog) - 1;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int g = w & gmask, p = w >> glog;
+        const int e0 = g << RL;
+        ulonglong2 *Zp = Z + p * NP;
+        int adr[R];
+        dev::slots_1d<RL, 0>(e0, adr);
+        dev::Cx2 v[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const ulonglong2 q = Zp[adr[t]];
+            v[t] = dev::Cx2{q.x, q.y};
+        }
+        dev::dft_dif_x2<RL>(v);
+#pragma unroll
+        for (int t = 0; t < R; ++t) Zp[adr[t]] = make_ulonglong2(v[t].re, v[t].im);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void fwd_1d_x2(ulonglong2 *Z, int NP, int nplane, int ln, const float2 *__restrict__ tw,
+                                          const ulonglong2 *__restrict__ twb) {
+    const int full = ln / 3, rem = ln - 3 * full;
+    if (full > 0) {
+        if (rem == 2) dev::pass_1d_dispatch<false, 2>(Z, NP, nplane, ln, ln - 2, tw, twb);
+        else if (rem == 1) dev::pass_1d_dispatch<false, 1>(Z, NP, nplane, ln, ln - 1, tw, twb);
+        for (int k = 0; k < full - 1; ++k) dev::pass_1d_dispatch<false, 3>(Z, NP, nplane, ln, ln - rem - 3 * (k + 1), tw, twb);
+        bottom_fwd_1d_x2<3>(Z, NP, nplane, ln);
+    } else if (rem == 2) {
+        bottom_fwd_1d_x2<2>(Z, NP, nplane, ln);
+    } else {
+        bottom_fwd_1d_x2<1>(Z, NP, nplane, ln);
+    }
+}
+
 // One-dimensional FFT jobs (lp2 = 0) on the paired-FP32 transforms of the apply: one CTA per
 // job and block of kGradCB channels, as grad_fft_kernel, but two channels per transform: the
 // element of depth r holds z_c = gsum_c + i fsum_c for channels c and c + 1 (lane pairs), and the
@@ -144,7 +187,7 @@ __global__ void __launch_bounds__(256) grad_fft1d_x2_kernel(const GradJob *__res
             Zx[dev::swz(key_r[k])] = make_ulonglong2(dev::vpack(g0, g1), dev::vpack(f0, f1));
         }
         __syncthreads();
-        dev::fwd_1d_x2(Zx, NP, 1, ln, tw, twb);
+        fwd_1d_x2(Zx, NP, 1, ln, tw, twb);
         for (int e = threadIdx.x; e < NP; e += blockDim.x) {
             const int f = brev_bits(e, ln), q = brev_bits((NP - f) & (NP - 1), ln);
             const ulonglong2 a = Zx[dev::swz(e)], b = Zx[dev::swz(q)];
