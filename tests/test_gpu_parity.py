@@ -321,3 +321,23 @@ def test_graph_replay_matches_apply():
         assert torch.equal(out, p.apply(F)) and torch.equal(gF, p.apply(G))
     ref = brute.integrate(t, cfg["delta"], cfg["kernel"], F.cpu().numpy().astype(np.float64))
     assert _err(out.cpu().numpy(), ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("d", [16, 17, 33, 64])
+def test_misaligned_field_pointers_match_aligned(d):
+    # F and out 4 bytes off a 16-byte boundary: every kernel takes its scalar-load path (bin sums,
+    # tensor-core leaves and tables, gather) and must give the aligned result bit for bit
+    cfg = W.configs.sweep(shape="rrt", n=4096, d=d, kernel="exp")
+    t = cfg["tree"]
+    p = tfi.Plan.from_spec(t, cfg["delta"], cfg["kernel"], leaf_max=512, max_channels=d)
+    F = torch.from_numpy(W.normal_field(t.n, d, seed=7)).cuda()
+    buf = torch.zeros(t.n * d + 1, dtype=torch.float32, device="cuda")
+    Fm = buf[1:].view(t.n, d)
+    Fm.copy_(F)
+    obuf = torch.zeros(t.n * d + 1, dtype=torch.float32, device="cuda")
+    outm = obuf[1:].view(t.n, d)
+    assert Fm.data_ptr() % 16 == 4 and outm.data_ptr() % 16 == 4
+    y = p.apply(F)
+    p.apply(Fm, outm)
+    torch.cuda.synchronize()
+    assert torch.equal(y, outm)
