@@ -146,9 +146,10 @@ def stage_source_hash(kernel_stage: str):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_stage: str):
+def ncu_traffic(kernel_stage: str, workload: str, leaf_max: int):
     """DRAM bytes per apply for a stage from a committed ncu summary, if it was
-    taken on the current source of that stage's kernels; otherwise None."""
+    taken on the current source of that stage's kernels and on this workload and
+    leaf cutoff; otherwise None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
@@ -157,6 +158,8 @@ def ncu_traffic(kernel_stage: str):
         return None
     ent = rec.get(kernel_stage)
     if not ent or ent.get("source_sha256") != stage_source_hash(kernel_stage):
+        return None
+    if ent.get("workload") != workload or ent.get("leaf_max") != leaf_max:
         return None
     return ent.get("bytes_per_apply")
 
@@ -239,8 +242,10 @@ def dense_baseline(a, n=1 << 16, reps=5):
     import workloads as W
 
     cfg = W.configs.sweep(shape=a.shape, n=n, d=a.d, kernel=a.kernel)
-    plan = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=a.policy, leaf_max=a.leaf_max,
-                              max_channels=a.d, leaf_tc=a.leaf_tc, tables_alu=a.tables_alu, leaf_alu=a.leaf_alu)
+    # StAd at this size with the library's autotuned leaf cutoff and FFT tile (as the C2 sweep lines)
+    plan, tuned = tfi.Plan.autotune(cfg["tree"], cfg["delta"], cfg["kernel"], a.d, leaf_candidates=C2_LEAF_CUTOFFS,
+                                    policy=a.policy, max_channels=a.d, leaf_tc=a.leaf_tc, tables_alu=a.tables_alu,
+                                    leaf_alu=a.leaf_alu)
     x = torch.from_numpy(W.normal_field(n, a.d, seed=123)).cuda()
     out = torch.empty_like(x)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -263,6 +268,7 @@ def dense_baseline(a, n=1 << 16, reps=5):
     stad_ms = timed(lambda: plan.apply(x, out), 20)
     dense_ms = timed(lambda: plan.dense_apply(x, out), reps)
     return {"n": n, "d": a.d, "workload": f"sweep_{a.shape}_n{n}_d{a.d}_{a.kernel}", "stad_fwd_ms": stad_ms,
+            "stad_leaf_max": tuned["leaf_max"], "stad_fft_cta_points": tuned["fft_cta_points"],
             "dense_tensor_core_fwd_ms": dense_ms, "speedup": dense_ms / stad_ms,
             "dense": "tcgen05 kind::f16, BF16 hi/lo split (3 products), FP32 accumulation in TMEM"}
 
@@ -340,6 +346,9 @@ C2_CASES = [("binary", 16, "exp", None), ("caterpillar", 16, "exp", None), ("cat
             ("rrt", 16, "exp", 14), ("rrt", 16, "exp", 16), ("rrt", 16, "exp", 18)]
 
 
+C2_LEAF_CUTOFFS = [256, 512, 768]
+
+
 def c2_sweep(a, steps=5):
     import torch
 
@@ -352,8 +361,11 @@ def c2_sweep(a, steps=5):
         cfg = W.configs.sweep(shape=shape, n=a.n if lg is None else 1 << lg, d=d, kernel=kern)
         n = cfg["tree"].n
         t0 = time.perf_counter()
-        plan = tfi.Plan.from_spec(cfg["tree"], cfg["delta"], cfg["kernel"], policy=a.policy, leaf_max=a.leaf_max,
-                                  max_channels=d, leaf_tc=a.leaf_tc, tables_alu=a.tables_alu, leaf_alu=a.leaf_alu)
+        # each case planned by the library's autotuner (leaf cutoff x shared-memory FFT tile): the best
+        # cutoff moves with N and d (at N = 2^14 a 768-vertex cutoff makes most of the tree one leaf)
+        plan, tuned = tfi.Plan.autotune(cfg["tree"], cfg["delta"], cfg["kernel"], d, leaf_candidates=C2_LEAF_CUTOFFS,
+                                        policy=a.policy, max_channels=d, leaf_tc=a.leaf_tc,
+                                        tables_alu=a.tables_alu, leaf_alu=a.leaf_alu)
         plan_s = time.perf_counter() - t0
         F = torch.from_numpy(W.normal_field(n, d, seed=123)).cuda()
         G = torch.from_numpy(W.normal_field(n, d, seed=124)).cuda()
@@ -378,7 +390,9 @@ def c2_sweep(a, steps=5):
         ms = tot / steps
         rows.append({"workload": f"sweep_{shape}_n{n}_d{d}_{kern}_delta1/64", "shape": shape, "n": n, "d": d,
                      "kernel": kern, "value": n * d / (ms / 1e3), "ms_per_step": ms, "fwd_ms": fwd / steps,
-                     "plan_seconds": round(plan_s, 3), "calls": info["n_calls"], "centroid_calls": info["n_centroid"],
+                     "autotune_and_plan_seconds": round(plan_s, 3), "leaf_max": tuned["leaf_max"],
+                     "fft_cta_points": tuned["fft_cta_points"], "calls": info["n_calls"],
+                     "centroid_calls": info["n_centroid"],
                      "jobs_fft": info["n_jobs_fft"], "jobs_fft_big": info["n_jobs_fft_big"],
                      "jobs_direct": info["n_jobs_direct"], "trunc_len": info["trunc_len"],
                      "levels": info["n_levels"]})
@@ -531,7 +545,7 @@ def run_ours(a):
     tflops = flops_dom / t_dom / 1e12
     frac_hbm = gbs / pk["hbm_gbs"]
     frac_alu = tflops / fp32_peak_tflops
-    traffic = ncu_traffic(dom)
+    traffic = ncu_traffic(dom, workload_name(a), a.leaf_max)
     if frac_hbm >= frac_alu:
         roof = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": frac_hbm,
                 "traffic": traffic, "kernel_stage": dom, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
@@ -630,7 +644,8 @@ def main():
     ap.add_argument("--d", type=int, default=16)
     ap.add_argument("--kernel", default="exp", choices=["exp", "cauchy", "gauss"])
     ap.add_argument("--policy", default="adaptive")
-    ap.add_argument("--leaf-max", dest="leaf_max", type=int, default=512)
+    ap.add_argument("--leaf-max", dest="leaf_max", type=int, default=768,
+                    help="leaf cutoff s0 (768: the fastest of a sweep over 256 .. 1024 on the default workload)")
     ap.add_argument("--leaf-alu", dest="leaf_alu", action="store_true",
                     help="every dense leaf on the FP32 ALUs (TFI_PLAN_LEAF_ALU)")
     ap.add_argument("--tables-alu", dest="tables_alu", action="store_true",

@@ -161,8 +161,9 @@ def _full_size_case(shape, n, leaf_max, per, n_random, min_targets, **flags):
 
 
 def test_full_size_stratified_rrt_2p20_bench_config():
-    # the benchmarked configuration itself: N = 2^20, s0 = 512 (packed big leaves, FFT classes)
-    p, n_classes = _full_size_case("rrt", 1 << 20, 512, per=128, n_random=256, min_targets=512)
+    # the benchmarked configuration itself: N = 2^20, s0 = 768 (bench.py's default leaf cutoff:
+    # tensor-core leaves of up to 768 vertices, FFT classes, direct tables)
+    p, n_classes = _full_size_case("rrt", 1 << 20, 768, per=128, n_random=256, min_targets=512)
     assert n_classes >= 2 and p.info()["n_jobs_direct"] > 0
 
 
