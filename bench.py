@@ -500,14 +500,22 @@ def run_ours(a):
     Gh = torch.from_numpy(W.normal_field(n, d, seed=124 + 2 * rank)).pin_memory()
     Oh = torch.empty_like(Fh).pin_memory()
     Qh = torch.empty_like(Fh).pin_memory()
-    # per step one call of the public host API on the step's two fields: the copies of one field
-    # overlap the apply of the other (tfi_apply_host_many); every step's copies are in the timed region
+    # the K steps' 2K host fields streamed through one call of the public host API, as a serving
+    # loop does: every field is copied in and its result copied out inside the timed region, the
+    # copies of one field overlapping the applies of its neighbours (tfi_apply_host_many)
+    fin = [Fh.data_ptr(), Gh.data_ptr()] * a.steps
+    fout = [Oh.data_ptr(), Qh.data_ptr()] * a.steps
     for _ in range(2):
         plan.apply_host_many([Fh.data_ptr(), Gh.data_ptr()], [Oh.data_ptr(), Qh.data_ptr()], d)
     e2e_t0 = time.perf_counter()
+    plan.apply_host_many(fin, fout, d)
+    e2e_s = time.perf_counter() - e2e_t0
+    # one call per step on the step's two fields (the copy-in of the first and the copy-out of the
+    # second exposed every step)
+    e2e_t2 = time.perf_counter()
     for _ in range(a.steps):
         plan.apply_host_many([Fh.data_ptr(), Gh.data_ptr()], [Oh.data_ptr(), Qh.data_ptr()], d)
-    e2e_s = time.perf_counter() - e2e_t0
+    e2e_step_s = time.perf_counter() - e2e_t2
     # the same with one synchronous call per field (no overlap), for comparison
     e2e_t1 = time.perf_counter()
     for _ in range(a.steps):
@@ -517,6 +525,7 @@ def run_ours(a):
     if dist:
         from paper_2609_34025_b300.dist import max_over_ranks
         e2e_s = max_over_ranks(e2e_s, device="cuda")
+        e2e_step_s = max_over_ranks(e2e_step_s, device="cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -595,8 +604,11 @@ def run_ours(a):
         "c2_sweep": c2,
         "e2e": {"value": world * n * d * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * n * d * 4,
                 "d2h_bytes_per_step": 2 * n * d * 4, "ms_per_step": 1e3 * e2e_s / a.steps,
-                "call": "tfi_apply_host_many on the step's two pinned host fields (copies of one field overlap "
-                        "the apply of the other)",
+                "call": "one tfi_apply_host_many call streaming the K steps' 2K pinned host fields (every "
+                        "field copied in and its result copied out inside the timed region; copies overlap the "
+                        "neighbouring applies)",
+                "per_step_call_value": world * n * d * a.steps / e2e_step_s,
+                "per_step_call": "tfi_apply_host_many once per step on the step's two fields",
                 "serial_value": world * n * d * a.steps / e2e_serial_s,
                 "serial_call": "tfi_apply_host once per field (copy in, apply, copy out, one after the other)"},
         "gpu_launches": int(round(sum(launches.values()) * 2 * a.steps)),
