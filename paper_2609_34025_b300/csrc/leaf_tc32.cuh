@@ -129,7 +129,8 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, ui
         "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
 }
 
-// Persistent: each CTA takes the leaves blockIdx.x, + gridDim.x, ... (largest first),
+// Persistent: each CTA takes its own list of leaves, cta_ptr[b] .. cta_ptr[b + 1] - 1 (the host
+// assigns them longest first to the least-loaded CTA; each list runs largest first),
 // stages a leaf's per-source tables once (its raw inputs copied in with cp.async while
 // the previous leaf runs) and runs its 128-row tiles one after another; the f samples are
 // staged once per CTA and the tensor memory is held throughout. Warps 0-7 build chunk
@@ -140,7 +141,8 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, ui
 // tile, add its accumulator to their registers; a tile ends by waiting for its last
 // chunks and adding their buffers.
 template <int NB, bool FS>
-__global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *__restrict__ leaves, int n_leaves,
+__global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *__restrict__ leaves,
+                                                                   const int32_t *__restrict__ cta_ptr,
                                                                    const int32_t *__restrict__ leaf_vtx,
                                                                    const int32_t *__restrict__ leaf_dist,
                                                                    const int32_t *__restrict__ leaf_pdist,
@@ -204,9 +206,11 @@ __global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *_
     int st = 0;        // its stage, g % STAGES
     uint32_t par = 0;  // the parity of its use of that stage, (g / STAGES) & 1
     bool warm = false; // g >= STAGES
+    // this CTA's leaves, largest first
+    const int L0 = cta_ptr[blockIdx.x], L1 = cta_ptr[blockIdx.x + 1];
     // a leaf's raw inputs are copied in asynchronously while the previous leaf runs
     auto fetch_raw = [&](int L) {
-        if (L >= n_leaves) return;
+        if (L >= L1) return;
         const int2 lf = leaves[L];
         for (int j = tid; j < lf.y - lf.x; j += kL32Threads) {
             cp_async4(rdist + j, leaf_dist + lf.x + j);
@@ -214,9 +218,9 @@ __global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *_
             cp_async4(rvtx + j, leaf_vtx + lf.x + j);
         }
     };
-    fetch_raw(blockIdx.x);
+    fetch_raw(L0);
 
-    for (int L = blockIdx.x; L < n_leaves; L += gridDim.x) {
+    for (int L = L0; L < L1; ++L) {
         const int2 lf = leaves[L];
         const int n = lf.y - lf.x, nc = (n + kL32Chunk - 1) / kL32Chunk;
         cp_async_wait_all();
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *_
         }
         if (tid < kL32Chunk) spd[nc * kL32Chunk + tid] = INF;
         __syncthreads();
-        fetch_raw(L + gridDim.x);
+        fetch_raw(L + 1);
         const int n_tiles = (n + kL32Tile - 1) / kL32Tile;
 
         if (warp == kL32Producers / 32) {

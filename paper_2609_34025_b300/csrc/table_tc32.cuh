@@ -14,8 +14,9 @@
 // shared memory, 12 MMAs per chunk issued by a ninth warp into one of three
 // accumulator buffers, each chunk's result added in FP32 registers. The bin sums
 // of a job are consecutive rows of the bin-sum array, so the B operand loads are
-// coalesced. Persistent CTAs take the jobs blockIdx.x, + gridDim.x, ... (largest
-// first) and copy the next job's keys in with cp.async while a job runs.
+// coalesced. Persistent CTAs each take their own list of jobs (assigned on the host
+// longest first to the least-loaded CTA; each list runs largest first) and copy the
+// next job's keys in with cp.async while a job runs.
 #pragma once
 
 #include "leaf_tc32.cuh"
@@ -48,9 +49,11 @@ __host__ __device__ inline Tab32Layout table_tc32_layout(int nb, int max_keys, i
     return o;
 }
 
-// jobs[q] = (kb, ke, two-dimensional, 0), ke - kb in [1, max_keys]
+// jobs[q] = (kb, ke, two-dimensional, 0), ke - kb in [1, max_keys]; CTA b takes jobs
+// cta_ptr[b] .. cta_ptr[b + 1] - 1
 template <int NB, bool FS>
-__global__ void __launch_bounds__(kL32Threads, 2) table_tc32_kernel(const int4 *__restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(kL32Threads, 2) table_tc32_kernel(const int4 *__restrict__ jobs,
+                                                                    const int32_t *__restrict__ cta_ptr,
                                                                     const int32_t *__restrict__ key_r,
                                                                     const int32_t *__restrict__ key_x, int d,
                                                                     const float *__restrict__ kbuf,
@@ -104,17 +107,18 @@ __global__ void __launch_bounds__(kL32Threads, 2) table_tc32_kernel(const int4 *
     int st = 0;         // its stage, g % STAGES
     uint32_t par = 0;   // the parity of its use of that stage, (g / STAGES) & 1
     bool warm = false;  // g >= STAGES
+    const int q0 = cta_ptr[blockIdx.x], q1 = cta_ptr[blockIdx.x + 1];
     auto fetch_keys = [&](int q) {
-        if (q >= n_jobs) return;
+        if (q >= q1) return;
         const int4 jb = jobs[q];
         for (int j = tid; j < jb.y - jb.x; j += kL32Threads) {
             cp_async4(rr + j, key_r + jb.x + j);
             cp_async4(rx + j, key_x + jb.x + j);
         }
     };
-    fetch_keys(blockIdx.x);
+    fetch_keys(q0);
 
-    for (int q = blockIdx.x; q < n_jobs; q += gridDim.x) {
+    for (int q = q0; q < q1; ++q) {
         const int4 jb = jobs[q];
         const int kb = jb.x, n = jb.y - jb.x, nc = (n + kL32Chunk - 1) / kL32Chunk;
         const bool two_d = jb.z != 0;
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(kL32Threads, 2) table_tc32_kernel(const int4 *
             sx[j] = j < n ? rx[j] : 0;
         }
         __syncthreads();
-        fetch_keys(q + gridDim.x);
+        fetch_keys(q + 1);
         const int n_tiles = (n + kL32Tile - 1) / kL32Tile;
 
         if (warp == kL32Producers / 32) {

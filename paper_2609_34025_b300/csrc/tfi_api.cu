@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <queue>
 #include <cstdint>
 #include <memory>
 #include <mutex>
@@ -54,8 +55,9 @@ struct WorkLists {
     tfi::dev::DirItem *d_dir = nullptr;
     int n_dir = 0;
     // direct jobs on the tensor cores: (kb, ke, two-dimensional, 0), largest first
-    int4 *d_tab = nullptr;
-    int n_tab = 0, tab_max_keys = 1, tab_fts = 1;
+    int4 *d_tab = nullptr;       // tensor-core direct jobs, grouped by CTA
+    int32_t *d_tab_ptr = nullptr;  // CTA b takes d_tab[d_tab_ptr[b] .. d_tab_ptr[b + 1])
+    int n_tab = 0, tab_grid = 0, tab_max_keys = 1, tab_fts = 1;
     // Hankel-matrix jobs: one item per (job, 128-channel block), one launch
     tfi::tc::HankelItem *d_hk = nullptr;
     int n_hk = 0;
@@ -175,8 +177,10 @@ struct tfi_plan_s {
                                     // [2]: the last tfi_selftest_wait gave up
     tfi::tc::LeafTile *leaf_tiles = nullptr;  // 128-row tiles of the leaf groups (tensor-core leaves)
     int32_t n_leaf_tiles = 0;
-    int2 *leaf32 = nullptr;                 // leaves of >= kLeafWarpMin vertices as [lo, hi), largest first
+    int2 *leaf32 = nullptr;                 // leaves of >= kLeafWarpMin vertices as [lo, hi), grouped by CTA
     int32_t n_leaf32 = 0, max_leaf32 = 1;   // (the FP32 tensor-core leaf kernel)
+    int32_t *leaf32_ptr = nullptr;          // CTA b takes leaf32[leaf32_ptr[b] .. leaf32_ptr[b + 1])
+    int32_t leaf32_grid = 0;
     double leaf_share = 0;                  // dense-leaf flops / all leaf and table flops (per channel)
     std::map<int, WorkLists> work;  // per channel count d
     int32_t fft_cta_points = 1 << 13;  // tfi_options.fft_cta_points (0 there: this default)
@@ -253,6 +257,7 @@ struct tfi_plan_s {
             cudaFree(kv.second.d_fft);
             cudaFree(kv.second.d_dir);
             cudaFree(kv.second.d_tab);
+            cudaFree(kv.second.d_tab_ptr);
             cudaFree(kv.second.d_hk);
             cudaFree(kv.second.d_big);
         }
@@ -271,6 +276,38 @@ constexpr int kFftSmemPairPoints = 1 << 13;  // default points x pairs per CTA (
 int fft_pairs_per_cta(int lnp, int pairs, int cta_points) {
     const int cap = lnp >= 13 ? 1 : std::max(1, cta_points >> lnp);
     return std::max(1, std::min(pairs, cap));
+}
+
+int device_sms();
+
+// Work of one leaf or direct job in the persistent tensor-core kernels: its 128-row tiles x
+// 32-source chunks, plus a few chunks' worth of per-item staging.
+double tc32_cost(int n) { return std::ceil(n / 128.0) * std::ceil(n / 32.0) + 4.0; }
+
+// Longest-processing-time-first assignment of items (sorted largest first) to `ctas` persistent
+// CTAs: each item goes to the CTA with the least work so far (the lowest index among equals).
+// `grouped` receives the items CTA by CTA (each CTA's in the original, descending order) and
+// `ptr` the ctas + 1 offsets into it. Within a few percent of the optimum where round-robin
+// over the sorted list leaves the first CTAs 10-20 % above the mean.
+template <typename Item, typename Size>
+void lpt_schedule(const std::vector<Item> &items, int ctas, Size size, std::vector<Item> &grouped,
+                  std::vector<int32_t> &ptr) {
+    std::vector<std::vector<int32_t>> per(size_t(std::max(ctas, 0)));
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int b = 0; b < ctas; ++b) heap.push({0.0, b});
+    for (size_t i = 0; i < items.size() && ctas > 0; ++i) {
+        const Load l = heap.top();
+        heap.pop();
+        per[size_t(l.second)].push_back(int32_t(i));
+        heap.push({l.first + tc32_cost(size(items[i])), l.second});
+    }
+    grouped.clear();
+    ptr.assign(1, 0);
+    for (int b = 0; b < ctas; ++b) {
+        for (int32_t i : per[size_t(b)]) grouped.push_back(items[size_t(i)]);
+        ptr.push_back(int32_t(grouped.size()));
+    }
 }
 
 tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
@@ -314,8 +351,15 @@ tfi_status build_work(tfi_plan_t p, int d, WorkLists **out) {
     std::stable_sort(tab.begin(), tab.end(), [](int4 a, int4 b) { return a.y - a.x > b.y - b.x; });
     wl.n_tab = int(tab.size());
     if (!tab.empty()) {
-        TFI_CUDA(cudaMalloc(&wl.d_tab, tab.size() * sizeof(tab[0])));
-        TFI_CUDA(cudaMemcpy(wl.d_tab, tab.data(), tab.size() * sizeof(tab[0]), cudaMemcpyHostToDevice));
+        // persistent: two CTAs per SM (their tensor memory), jobs assigned longest first
+        wl.tab_grid = std::min(wl.n_tab, 2 * device_sms());
+        std::vector<int4> grouped;
+        std::vector<int32_t> ptr;
+        lpt_schedule(tab, wl.tab_grid, [](int4 a) { return a.y - a.x; }, grouped, ptr);
+        TFI_CUDA(cudaMalloc(&wl.d_tab, grouped.size() * sizeof(grouped[0])));
+        TFI_CUDA(cudaMemcpy(wl.d_tab, grouped.data(), grouped.size() * sizeof(grouped[0]), cudaMemcpyHostToDevice));
+        TFI_CUDA(cudaMalloc(&wl.d_tab_ptr, ptr.size() * sizeof(ptr[0])));
+        TFI_CUDA(cudaMemcpy(wl.d_tab_ptr, ptr.data(), ptr.size() * sizeof(ptr[0]), cudaMemcpyHostToDevice));
     }
     std::vector<tfi::dev::FftItem> all;
     for (auto &kv : by_class) {
@@ -581,11 +625,11 @@ void launch_leaf_tc32_nb(tfi_plan_t p, const float *F, float *lbuf, int d, cudaS
     // which its tensor memory holds, and the rest of the SM stays open to the kernels that run
     // beside it (a four-step FFT CTA takes 140 KB)
     const size_t smem = tfi::tc::leaf_tc32_layout(NB, p->max_leaf32, fts).bytes;
-    // persistent: two CTAs per SM (their tensor memory), each over every gridDim.x-th leaf
-    dim3 grid(unsigned(std::min(p->n_leaf32, 2 * device_sms())), unsigned((d + NB - 1) / NB));
+    // persistent: the plan's CTAs, each over its own list of leaves
+    dim3 grid(unsigned(p->leaf32_grid), unsigned((d + NB - 1) / NB));
     auto k = fts > 0 ? tfi::tc::leaf_tc32_kernel<NB, true> : tfi::tc::leaf_tc32_kernel<NB, false>;
-    k<<<grid, tfi::tc::kL32Threads, smem, s>>>(p->leaf32, p->n_leaf32, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, F, d, p->ftab, fts,
-                              p->max_leaf32, lbuf, p->hk_err + 1);
+    k<<<grid, tfi::tc::kL32Threads, smem, s>>>(p->leaf32, p->leaf32_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, F, d,
+                                              p->ftab, fts, p->max_leaf32, lbuf, p->hk_err + 1);
 }
 
 void launch_leaf_tc32(tfi_plan_t p, const float *F, float *lbuf, int d, cudaStream_t s) {
@@ -654,9 +698,9 @@ void launch_table_tc32_nb(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t
         fts = 0;
     // two CTAs per SM by their registers (as for the leaves), no shared-memory padding
     const size_t smem = tfi::tc::table_tc32_layout(NB, wl.tab_max_keys, fts).bytes;
-    dim3 grid(unsigned(std::min(wl.n_tab, 2 * device_sms())), unsigned((d + NB - 1) / NB));
+    dim3 grid(unsigned(wl.tab_grid), unsigned((d + NB - 1) / NB));
     auto k = fts > 0 ? tfi::tc::table_tc32_kernel<NB, true> : tfi::tc::table_tc32_kernel<NB, false>;
-    k<<<grid, tfi::tc::kL32Threads, smem, s>>>(wl.d_tab, wl.n_tab, p->key_r, p->key_x, d, p->kbuf, p->vbuf,
+    k<<<grid, tfi::tc::kL32Threads, smem, s>>>(wl.d_tab, wl.d_tab_ptr, p->key_r, p->key_x, d, p->kbuf, p->vbuf,
                                               p->ftab, fts, wl.tab_max_keys, p->hk_err + 1);
 }
 
@@ -1114,8 +1158,14 @@ tfi_status upload_plan(tfi_plan_t p) {
             p->max_leaf32 = std::max(p->max_leaf32, leaf_hi_big[q] - leaf_lo_big[q]);
         }
         std::stable_sort(l32.begin(), l32.end(), [](int2 a, int2 b) { return a.y - a.x > b.y - b.x; });
-        if (tfi_status rc = p->upload(&p->leaf32, l32)) return rc;
         p->n_leaf32 = int32_t(l32.size());
+        // persistent: two CTAs per SM (their tensor memory), leaves assigned longest first
+        p->leaf32_grid = std::min(p->n_leaf32, 2 * device_sms());
+        std::vector<int2> grouped;
+        std::vector<int32_t> ptr;
+        lpt_schedule(l32, p->leaf32_grid, [](int2 a) { return a.y - a.x; }, grouped, ptr);
+        if (tfi_status rc = p->upload(&p->leaf32, grouped)) return rc;
+        if (tfi_status rc = p->upload(&p->leaf32_ptr, ptr)) return rc;
         // per-channel flops: leaf pairs 2 n^2, FFT tables 5 P log2 P + 3 P per channel, direct 2 nk^2
         double leaf = 0, tables = 0;
         for (const tfi::Leaf &l : hp.leaves) leaf += 2.0 * double(l.end - l.begin) * double(l.end - l.begin);
@@ -1797,6 +1847,7 @@ void clear_work(tfi_plan_t p) {
         cudaFree(kv.second.d_fft);
         cudaFree(kv.second.d_dir);
         cudaFree(kv.second.d_tab);
+        cudaFree(kv.second.d_tab_ptr);
         cudaFree(kv.second.d_hk);
         cudaFree(kv.second.d_big);
     }
