@@ -4,6 +4,8 @@ Tolerance (per channel, normwise): max_u |y_gpu - y| / max_u |y| <= 1e-4 for
 FP32 fields and <= 1e-2 for BF16 fields (the bf16 case compares against the
 oracle applied to the bf16-rounded input).
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -342,3 +344,21 @@ def test_misaligned_field_pointers_match_aligned(d):
     p.apply(Fm, outm)
     torch.cuda.synchronize()
     assert torch.equal(y, outm)
+
+
+def test_apply_rejects_bad_arguments():
+    """Host-side validation of tfi_apply on a device plan: every bad argument returns
+    TFI_ERR_ARG (1) before anything is launched, and the plan stays usable."""
+    t = _rrt(600, 11)
+    p = tfi.Plan.from_spec(t, 1.0, W.KernelSpec.exp(0.3), leaf_max=64, max_channels=8)
+    F = torch.from_numpy(W.normal_field(t.n, 8, seed=5)).cuda()
+    out = torch.empty_like(F)
+    fn = tfi.lib().tfi_apply
+    ptr = lambda x: ctypes.c_void_p(x.data_ptr())
+    for d, dtype, a, b in [(0, 0, F, out), (9, 0, F, out), (-1, 0, F, out), (8, 7, F, out), (8, 0, F, F)]:
+        assert fn(p._h, ptr(a), ptr(b), d, dtype, None) == 1, (d, dtype)
+    assert fn(p._h, None, ptr(out), 8, 0, None) == 1
+    assert fn(p._h, ptr(F), None, 8, 0, None) == 1
+    ref = brute.integrate(t, 1.0, W.KernelSpec.exp(0.3), F.cpu().numpy().astype(np.float64))
+    assert _err(p.apply(F).cpu().numpy(), ref) <= TOL["f32"]
+    assert p.info()["device_errors"] == 0
