@@ -54,8 +54,9 @@ struct WorkLists {
     tfi::dev::FftItem *d_fft = nullptr;
     tfi::dev::DirItem *d_dir = nullptr;
     int n_dir = 0;
-    // direct jobs on the tensor cores: (kb, ke, two-dimensional, 0), largest first
-    int4 *d_tab = nullptr;       // tensor-core direct jobs, grouped by CTA
+    // direct jobs on the tensor cores: (kb, ke, two-dimensional, 0), grouped by CTA (each
+    // CTA's largest first)
+    int4 *d_tab = nullptr;
     int32_t *d_tab_ptr = nullptr;  // CTA b takes d_tab[d_tab_ptr[b] .. d_tab_ptr[b + 1])
     int n_tab = 0, tab_grid = 0, tab_max_keys = 1, tab_fts = 1;
     // Hankel-matrix jobs: one item per (job, 128-channel block), one launch
@@ -1151,7 +1152,7 @@ tfi_status upload_plan(tfi_plan_t p) {
         if (tfi_status rc = p->upload(&p->sgrp_ptr, sgrp)) return rc;
         if (tfi_status rc = p->upload(&p->big_lo, blo)) return rc;
         if (tfi_status rc = p->upload(&p->big_hi, bhi)) return rc;
-        // FP32 tensor-core leaves: every big leaf, largest first
+        // FP32 tensor-core leaves: every big leaf, sorted largest first, then dealt to the CTAs
         std::vector<int2> l32;
         for (size_t q = 0; q < leaf_lo_big.size(); ++q) {
             l32.push_back(make_int2(leaf_lo_big[q], leaf_hi_big[q]));
