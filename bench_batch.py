@@ -70,6 +70,17 @@ def main():
     out, gF = torch.empty_like(F), torch.empty_like(F)
     graph = tfi.Graph(plan, F, out, G, gF)
     step_ms = timed(graph.launch, a.steps, a.warmup)
+    # the step against HBM: the hot-path byte model and the stage model's bytes (bin-sum and table
+    # rows written and read between stages too), two applies per step
+    from bench import measured_peaks, step_bytes_8d
+    pk, pk_src = measured_peaks()
+    b8d = step_bytes_8d(plan, n, d)
+    b_stages = sum(b for b, _ in plan.stage_model(d).values())
+    t_step = step_ms / 1e3
+    hbm = {"bytes_per_apply_model": b8d, "bytes_per_apply_stages": b_stages,
+           "achieved_gbs": 2 * b8d / t_step / 1e9, "frac": 2 * b8d / t_step / 1e9 / pk["hbm_gbs"],
+           "frac_stage_bytes": 2 * b_stages / t_step / 1e9 / pk["hbm_gbs"], "peak": pk["hbm_gbs"],
+           "unit": "GB/s", "peak_source": f"{pk_src} (MEASURED_PEAKS.json hbm_gbs)"}
     # spot check against the oracle
     from oracle import brute
     rng = np.random.default_rng(0)
@@ -110,6 +121,7 @@ def main():
                           "value": loop_n * d / (loop_ms / 1e3), "plan_seconds": round(loop_plan_s, 2)},
         "speedup_vs_loop": (loop_n * d / (loop_ms / 1e3)) and (n * d / (step_ms / 1e3)) / (loop_n * d / (loop_ms / 1e3)),
         "parity": {"sampled_targets": 64, "max_normwise_err": err},
+        "hbm": hbm,
     }
     print(json.dumps(line), flush=True)
 
