@@ -564,8 +564,10 @@ void pack_big_leaves(const std::vector<int32_t> &lo, const std::vector<int32_t> 
 constexpr int kLeafFtabSmemMax = 12288;  // f samples staged in shared memory up to this many
 
 // big = false: only the small leaves (the big ones go to the tensor cores)
+// returns the number of kernels launched
 template <int CH, typename T>
-void launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s, bool big = true) {
+int launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s, bool big = true) {
+    int launched = 0;
     // leaves look f up at their own pair distances only: stage that prefix of the samples
     const int fts = p->hp.leaf_ftab_len <= kLeafFtabSmemMax ? int(p->hp.leaf_ftab_len) : 0;
     if (big && p->n_big > 0) {
@@ -574,6 +576,7 @@ void launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s, b
         auto k = fts > 0 ? tfi::dev::leaf_warp_kernel<T, CH, true> : tfi::dev::leaf_warp_kernel<T, CH, false>;
         k<<<grid, kLeafWarpThreads, smem, s>>>(p->big_ptr, p->big_lo, p->big_hi, p->leaf_vtx, p->leaf_dist,
                                                p->leaf_pdist, F, d, p->ftab, fts, lbuf, p->max_big);
+        ++launched;
     }
     if (p->n_sgroups > 0) {
         const size_t smem = tfi::dev::leaf_smem_bytes(p->max_sgs, CH, fts);
@@ -581,7 +584,9 @@ void launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s, b
         auto k = fts > 0 ? tfi::dev::leaf_kernel<T, CH, true> : tfi::dev::leaf_kernel<T, CH, false>;
         k<<<grid, 256, smem, s>>>(p->sgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, p->leaf_lo, p->leaf_hi, F, d,
                                   p->ftab, fts, lbuf, p->max_sgs);
+        ++launched;
     }
+    return launched;
 }
 
 constexpr int kLeafTcFtabSmem = 4096;  // f samples staged in shared memory by the tensor-core leaf kernel
@@ -604,15 +609,17 @@ void launch_leaf_tc_nb(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_
 }
 
 // Tensor-core leaves for BF16 fields: NB = channels per CTA (TMEM columns), the next power of two
-// >= d, from 64 to 256. FP32 fields stay on the FP32-ALU leaf kernel: the tensor cores' FP32
-// accumulation over the ~1000 chained MMAs of a large leaf measured 6.5e-4 normwise on a slowly
-// decaying kernel, beyond the FP32 bound of 1e-4.
-void launch_leaf_tc(tfi_plan_t p, const __nv_bfloat16 *F, float *lbuf, int d, cudaStream_t s) {
-    if (p->n_leaf_tiles == 0) return;
+// >= d, from 64 to 256; one chained FP32 accumulator per tile (within the BF16 bound). FP32 fields
+// use leaf_tc32_kernel instead: this kernel's accumulation over the ~1000 chained MMAs of a large
+// leaf measured 6.5e-4 normwise on a slowly decaying kernel, beyond the FP32 bound of 1e-4.
+// Returns the number of kernels launched.
+int launch_leaf_tc(tfi_plan_t p, const __nv_bfloat16 *F, float *lbuf, int d, cudaStream_t s) {
+    if (p->n_leaf_tiles == 0) return 0;
     using B = __nv_bfloat16;
     if (d > 128) launch_leaf_tc_nb<B, 256>(p, F, lbuf, d, s);
     else if (d > 64) launch_leaf_tc_nb<B, 128>(p, F, lbuf, d, s);
     else launch_leaf_tc_nb<B, 64>(p, F, lbuf, d, s);
+    return 1;
 }
 
 // FP32 leaves of >= kLeafWarpMin vertices on the tensor cores: NB channels per CTA
@@ -633,11 +640,13 @@ void launch_leaf_tc32_nb(tfi_plan_t p, const float *F, float *lbuf, int d, cudaS
                                               p->ftab, fts, p->max_leaf32, lbuf, p->hk_err + 1);
 }
 
-void launch_leaf_tc32(tfi_plan_t p, const float *F, float *lbuf, int d, cudaStream_t s) {
-    if (p->n_leaf32 == 0) return;
+// returns the number of kernels launched
+int launch_leaf_tc32(tfi_plan_t p, const float *F, float *lbuf, int d, cudaStream_t s) {
+    if (p->n_leaf32 == 0) return 0;
     if (d <= 16) launch_leaf_tc32_nb<16>(p, F, lbuf, d, s);
     else if (d <= 32) launch_leaf_tc32_nb<32>(p, F, lbuf, d, s);
     else launch_leaf_tc32_nb<64>(p, F, lbuf, d, s);
+    return 1;
 }
 
 // (a3) bin sums -> kb (the plan's kbuf by default): segments, then the multi-segment bins'
@@ -665,28 +674,28 @@ void launch_bucket(tfi_plan_t p, const T *F, int d, cudaStream_t s, float *kb = 
 // channels the FP32 ALUs are faster: the f(D) operand costs the same at any d, the ALU sum
 // d FMAs per pair (measured at N = 2^20, s0 = 512: 0.34 against 0.21 ms at d = 1, 0.47 against
 // 0.48 ms at d = 16, 1.18 against 1.96 ms at d = 64).
+// returns the number of kernels launched
 template <typename T>
-void launch_leaves(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
+int launch_leaves(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
     const bool alu = (p->hp.flags & TFI_PLAN_LEAF_ALU) != 0;
     if constexpr (sizeof(T) == 2) {
-        if (d >= kLeafTcMinChannels && !alu) {
-            launch_leaf_tc(p, F, p->lbuf, d, s);
-            return;
-        }
+        if (d >= kLeafTcMinChannels && !alu) return launch_leaf_tc(p, F, p->lbuf, d, s);
     }
     bool big = true;
+    int launched = 0;
     if constexpr (sizeof(T) == 4) {
         const bool by_default = d >= kLeafTc32MinChannels && p->leaf_share >= kLeafTc32MinShare;
         if (!alu && (by_default || (p->hp.flags & TFI_PLAN_LEAF_TC)) && p->n_leaf32 > 0) {
-            launch_leaf_tc32(p, F, p->lbuf, d, s);
+            launched += launch_leaf_tc32(p, F, p->lbuf, d, s);
             big = false;
         }
     }
-    if (d >= 16) launch_leaf<16>(p, F, p->lbuf, d, s, big);
-    else if (d > 4) launch_leaf<8>(p, F, p->lbuf, d, s, big);
-    else if (d > 2) launch_leaf<4>(p, F, p->lbuf, d, s, big);
-    else if (d == 2) launch_leaf<2>(p, F, p->lbuf, d, s, big);
-    else launch_leaf<1>(p, F, p->lbuf, d, s, big);
+    if (d >= 16) launched += launch_leaf<16>(p, F, p->lbuf, d, s, big);
+    else if (d > 4) launched += launch_leaf<8>(p, F, p->lbuf, d, s, big);
+    else if (d > 2) launched += launch_leaf<4>(p, F, p->lbuf, d, s, big);
+    else if (d == 2) launched += launch_leaf<2>(p, F, p->lbuf, d, s, big);
+    else launched += launch_leaf<1>(p, F, p->lbuf, d, s, big);
+    return launched;
 }
 
 // direct jobs of 64 .. 4096 bins on the tensor cores (d > 16, or d = 16 from 512 bins): NB channels
@@ -852,8 +861,7 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
     if (p->n_zero_ranges > 0) launch_zero_rows(p, p->vbuf, d, s_leaf);
     // (a7) dense leaves -> lbuf, on the low-priority leaf stream
     StageMark m_leaf(p, s_leaf, TFI_STAGE_LEAF);
-    launch_leaves(p, F, d, s_leaf);
-    m_leaf.done(p->n_groups > 0 ? 1 : 0);
+    m_leaf.done(launch_leaves(p, F, d, s_leaf));
     TFI_CUDA(cudaEventRecord(p->ev_leaf, s_leaf));
     if (n_keys > 0) {
         TFI_CUDA(cudaStreamWaitEvent(s_dir, p->ev_bucket, 0));
