@@ -857,11 +857,16 @@ tfi_status apply_impl(tfi_plan_t p, const T *F, T *out, int d, cudaStream_t s) {
         m_bucket.done(p->n_multi > 0 ? 2 : 1);
         TFI_CUDA(cudaEventRecord(p->ev_bucket, s_crit));
     }
-    // bins cut from their tables by the support truncation: zero values (no inputs needed)
-    if (p->n_zero_ranges > 0) launch_zero_rows(p, p->vbuf, d, s_leaf);
-    // (a7) dense leaves -> lbuf, on the low-priority leaf stream
+    // (a7) dense leaves -> lbuf, on the leaf stream; ahead of them, the bins cut from their tables
+    // by the support truncation get zero values (no inputs needed; timed with the leaves)
     StageMark m_leaf(p, s_leaf, TFI_STAGE_LEAF);
-    m_leaf.done(launch_leaves(p, F, d, s_leaf));
+    int leaf_launches = 0;
+    if (p->n_zero_ranges > 0) {
+        launch_zero_rows(p, p->vbuf, d, s_leaf);
+        ++leaf_launches;
+    }
+    leaf_launches += launch_leaves(p, F, d, s_leaf);
+    m_leaf.done(leaf_launches);
     TFI_CUDA(cudaEventRecord(p->ev_leaf, s_leaf));
     if (n_keys > 0) {
         TFI_CUDA(cudaStreamWaitEvent(s_dir, p->ev_bucket, 0));
