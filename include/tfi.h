@@ -383,6 +383,12 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
  *                       ceil(size / 64) of them, a CTA holds leaves while their warps fit in 8 and
  *                       their vertices in the capacity (largest leaf first). The paper has no
  *                       counterpart: this is a launch layout (base case of Algorithm 5).
+ *   TFI_EXPORT_LEAF_CTAS 4 per dense leaf of at least 64 vertices, CTA by CTA, for the FP32
+ *                       tensor-core leaf kernel: its persistent CTA, the leaf's [begin, end) range of
+ *                       leaf positions, and the number of CTAs (two per SM, at most one per leaf).
+ *                       Leaves are sorted largest first and each goes to the CTA with the least
+ *                       work so far (work: ceil(size / 128) x ceil(size / 32) + 4); each CTA runs its
+ *                       list in that order. A launch layout, with no counterpart in the paper.
  *   TFI_EXPORT_GATHER_ORDER the n vertices in the order the output gather takes them: a
  *                       depth-first preorder of the forest, tree by tree. Launch layout only.
  *   TFI_EXPORT_JOBS     7 per table job (a call's cross table or a component's correction), in plan
@@ -401,6 +407,7 @@ tfi_status tfi_plan_get_info(tfi_plan_t plan, tfi_plan_info *info);
 #define TFI_EXPORT_LEAF_PACKS  5
 #define TFI_EXPORT_GATHER_ORDER 6
 #define TFI_EXPORT_JOBS         7
+#define TFI_EXPORT_LEAF_CTAS    8
 tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t cap, int64_t *len);
 
 /* Stages of an apply, in launch order, for profiling and the roofline model:

@@ -26,7 +26,7 @@ KERNEL_KINDS = {"table": 0, "expsum": 1, "gauss": 2, "rational": 3, "powexp": 4}
 POLICIES = {"adaptive": 0, "diameter": 1, "centroid": 2}
 DTYPE_F32, DTYPE_BF16 = 0, 1
 EXPORTS = {"calls": (0, 7), "backbone": (1, 1), "records": (2, 5), "leaves": (3, 3), "device_keys": (4, 4),
-           "leaf_packs": (5, 4), "gather_order": (6, 1), "jobs": (7, 7)}
+           "leaf_packs": (5, 4), "gather_order": (6, 1), "jobs": (7, 7), "leaf_ctas": (8, 4)}
 
 
 class TfiError(RuntimeError):
@@ -352,8 +352,9 @@ class Plan:
         "records" (call, vertex, depth, coordinate, component), "leaves" (level, min vertex, size),
         "device_keys" (call, vertex, device depth, device coordinate; device plans only),
         "leaf_packs" (CTA, leaf begin, leaf end, CTA vertex capacity), "gather_order"
-        (vertices in the gather's order) and "jobs" (evaluator, log2 FFT points, is correction,
-        bins, first member vertex, last member vertex, largest depth)."""
+        (vertices in the gather's order), "jobs" (evaluator, log2 FFT points, is correction,
+        bins, first member vertex, last member vertex, largest depth) and "leaf_ctas" (CTA, leaf
+        begin, leaf end, CTA count of the FP32 tensor-core leaf kernel)."""
         code, width = EXPORTS[what]
         ln = ctypes.c_int64()
         _check(lib().tfi_plan_export(self._h, code, None, 0, ctypes.byref(ln)))

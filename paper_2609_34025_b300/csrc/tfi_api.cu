@@ -1040,6 +1040,22 @@ void split_leaves(const tfi::HostPlan &hp, std::vector<int32_t> &sgrp, std::vect
     if (gb >= 0) sgrp.insert(sgrp.end(), {gb, nl});
 }
 
+// FP32 tensor-core leaves: every leaf of >= kLeafWarpMin vertices as [lo, hi) (from split_leaves),
+// sorted largest first, then dealt to min(leaves, ctas_cap) persistent CTAs longest first
+// (lpt_schedule): `grouped` CTA by CTA, `ptr` the CTA offsets; returns the CTA count.
+int leaf32_schedule(const std::vector<int32_t> &big_lo, const std::vector<int32_t> &big_hi, int ctas_cap,
+                    std::vector<int2> &grouped, std::vector<int32_t> &ptr, int32_t *max_leaf) {
+    std::vector<int2> l32;
+    for (size_t q = 0; q < big_lo.size(); ++q) {
+        l32.push_back(make_int2(big_lo[q], big_hi[q]));
+        *max_leaf = std::max(*max_leaf, big_hi[q] - big_lo[q]);
+    }
+    std::stable_sort(l32.begin(), l32.end(), [](int2 a, int2 b) { return a.y - a.x > b.y - b.x; });
+    const int ctas = std::min(int(l32.size()), ctas_cap);
+    lpt_schedule(l32, ctas, [](int2 a) { return a.y - a.x; }, grouped, ptr);
+    return ctas;
+}
+
 // Depth-first preorder of the forest, tree by tree from the smallest unvisited
 // vertex: the order in which the gather takes the vertices.
 std::vector<int32_t> depth_first_order(const tfi::HostPlan &hp) {
@@ -1165,19 +1181,12 @@ tfi_status upload_plan(tfi_plan_t p) {
         if (tfi_status rc = p->upload(&p->sgrp_ptr, sgrp)) return rc;
         if (tfi_status rc = p->upload(&p->big_lo, blo)) return rc;
         if (tfi_status rc = p->upload(&p->big_hi, bhi)) return rc;
-        // FP32 tensor-core leaves: every big leaf, sorted largest first, then dealt to the CTAs
-        std::vector<int2> l32;
-        for (size_t q = 0; q < leaf_lo_big.size(); ++q) {
-            l32.push_back(make_int2(leaf_lo_big[q], leaf_hi_big[q]));
-            p->max_leaf32 = std::max(p->max_leaf32, leaf_hi_big[q] - leaf_lo_big[q]);
-        }
-        std::stable_sort(l32.begin(), l32.end(), [](int2 a, int2 b) { return a.y - a.x > b.y - b.x; });
-        p->n_leaf32 = int32_t(l32.size());
-        // persistent: two CTAs per SM (their tensor memory), leaves assigned longest first
-        p->leaf32_grid = std::min(p->n_leaf32, 2 * device_sms());
+        // FP32 tensor-core leaves: every big leaf, dealt longest first to persistent CTAs, two per
+        // SM (their tensor memory)
         std::vector<int2> grouped;
         std::vector<int32_t> ptr;
-        lpt_schedule(l32, p->leaf32_grid, [](int2 a) { return a.y - a.x; }, grouped, ptr);
+        p->leaf32_grid = leaf32_schedule(leaf_lo_big, leaf_hi_big, 2 * device_sms(), grouped, ptr, &p->max_leaf32);
+        p->n_leaf32 = int32_t(grouped.size());
         if (tfi_status rc = p->upload(&p->leaf32, grouped)) return rc;
         if (tfi_status rc = p->upload(&p->leaf32_ptr, ptr)) return rc;
         // per-channel flops: leaf pairs 2 n^2, FFT tables 5 P log2 P + 3 P per channel, direct 2 nk^2
@@ -2492,6 +2501,19 @@ tfi_status tfi_plan_export(tfi_plan_t plan, int32_t what, int64_t *dst, int64_t 
             for (size_t b = 0; b + 1 < bptr.size(); ++b)
                 for (int32_t q = bptr[b]; q < bptr[b + 1]; ++q) {
                     const int64_t row[4] = {int64_t(b), blo[size_t(q)], bhi[size_t(q)], cap};
+                    v.insert(v.end(), row, row + 4);
+                }
+            break;
+        }
+        case TFI_EXPORT_LEAF_CTAS: {
+            std::vector<int32_t> sgrp, lo, hi, ptr;
+            split_leaves(hp, sgrp, lo, hi);
+            std::vector<int2> grouped;
+            int32_t max_leaf = 1;
+            const int ctas = leaf32_schedule(lo, hi, 2 * device_sms(), grouped, ptr, &max_leaf);
+            for (int b = 0; b < ctas; ++b)
+                for (int32_t q = ptr[size_t(b)]; q < ptr[size_t(b) + 1]; ++q) {
+                    const int64_t row[4] = {int64_t(b), grouped[size_t(q)].x, grouped[size_t(q)].y, ctas};
                     v.insert(v.end(), row, row + 4);
                 }
             break;

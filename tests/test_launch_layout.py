@@ -55,6 +55,41 @@ def test_big_leaves_packed_once_within_limits(name, tree, delta, spec, s0):
     assert all(a >= b for a, b in zip(first, first[1:]))
 
 
+def _tc_cost(n):
+    # work of one leaf in the persistent tensor-core leaf kernel: 128-row tiles x 32-source chunks + 4
+    return -(-n // 128) * -(-n // 32) + 4
+
+
+@pytest.mark.parametrize("name,tree,delta,spec,s0", PLANS, ids=[p[0] for p in PLANS])
+def test_tensor_core_leaves_dealt_longest_first(name, tree, delta, spec, s0):
+    """Every big leaf goes to exactly one persistent CTA; each CTA's list runs largest first; the
+    greedy longest-first assignment keeps every CTA within one leaf's work of the least-loaded one
+    and within 4/3 of the lower bound on the best makespan."""
+    p = tfi.Plan.from_spec(tree, delta, spec, leaf_max=s0, host_only=True)
+    sizes = p.export("leaves")[:, 2]
+    ends = np.cumsum(sizes)
+    ranges = sorted((int(e - s), int(e)) for s, e in zip(sizes, ends) if s >= BIG)
+    rows = p.export("leaf_ctas")
+    if not ranges:
+        assert rows.size == 0
+        return
+    got = sorted((int(b), int(e)) for b, e in rows[:, 1:3])
+    assert got == ranges
+    n_ctas = int(rows[0, 3])
+    assert (rows[:, 3] == n_ctas).all() and 1 <= n_ctas <= len(ranges)
+    cta = rows[:, 0]
+    assert (np.diff(cta) >= 0).all() and set(cta.tolist()) == set(range(n_ctas))
+    load = np.zeros(n_ctas)
+    for c in range(n_ctas):
+        n = rows[cta == c, 2] - rows[cta == c, 1]
+        assert (np.diff(n) <= 0).all()
+        load[c] = sum(_tc_cost(int(x)) for x in n)
+    costs = [_tc_cost(e - b) for b, e in ranges]
+    assert load.max() - load.min() <= max(costs) + 1e-9
+    bound = max(sum(costs) / n_ctas, max(costs))
+    assert load.max() <= 4.0 / 3.0 * bound + 1e-9
+
+
 def _is_dfs_preorder(order, n, u, v):
     adj = [[] for _ in range(n)]
     for a, b in zip(u, v):
