@@ -139,7 +139,7 @@ typedef struct {
                                    leaves are a quarter of the work or more). Ignored when
                                    TFI_PLAN_LEAF_ALU is set. */
 #define TFI_PLAN_TABLES_ALU 1024 /* tables evaluated by direct summation on the FP32 ALUs for every d.
-                                   By default, for d > 16 (for d = 16 from 256 bins), a direct table
+                                   By default, for d > 16 (for d = 16 from 512 bins), a direct table
                                    of 64 .. 4096 bins is an
                                    f(r_i + r_j + |x_i - x_j|) x S product on the tensor cores
                                    (tcgen05 kind::tf32, both operands split into hi + lo, a fresh

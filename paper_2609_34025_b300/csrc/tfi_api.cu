@@ -87,11 +87,8 @@ constexpr int kTable32MinChannels = 17;        // direct tables on the tensor co
                                                // needs two or more 16-channel passes (N = 2^20:
                                                // 0.66 against 0.96 ms at d = 64, 0.25 against
                                                // 0.24 ms at d = 16 on the random tree's tables)
-constexpr int kTable32BigKeys = 256;           // and at d = 16 for tables of this many bins or more
-                                               // (with the longest-first CTA lists, N = 2^20 random
-                                               // tree step 2.926 ms at 256, 2.929 at 64 or 128,
-                                               // 2.938 at 512; the caterpillar 51.9 against 57.1 ms
-                                               // with no tables on the tensor cores)
+constexpr int kTable32BigKeys = 512;           // and at d = 16 for tables of this many bins or more
+                                               // (the 2^20 caterpillar: 52.1 against 57.1 ms)
 constexpr size_t kLeaf32SmemMax = 110 * 1024;  // tensor-core leaf / table CTAs: two per SM (with the
                                                // static and reserved bytes)
 
@@ -701,7 +698,7 @@ int launch_leaves(tfi_plan_t p, const T *F, int d, cudaStream_t s) {
     return launched;
 }
 
-// direct jobs of 64 .. 4096 bins on the tensor cores (d > 16, or d = 16 from 256 bins): NB channels
+// direct jobs of 64 .. 4096 bins on the tensor cores (d > 16, or d = 16 from 512 bins): NB channels
 // per CTA
 template <int NB>
 void launch_table_tc32_nb(tfi_plan_t p, const WorkLists &wl, int d, cudaStream_t s) {

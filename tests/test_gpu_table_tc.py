@@ -1,7 +1,7 @@
 """GPU parity of the tensor-core direct tables (tcgen05 kind::tf32) against the
 FP64 oracle and against the FP32-ALU direct kernel, through the C ABI.
 
-For d > 16 (for d = 16 from 256 bins) a table evaluated by direct summation with
+For d > 16 (for d = 16 from 512 bins) a table evaluated by direct summation with
 64 .. 4096 bins is an f(r_i + r_j + |x_i - x_j|) x S product on the tensor cores
 (both operands split into TF32 hi + lo, a fresh accumulator per 32 source bins);
 TFI_PLAN_TABLES_ALU keeps every table on the FP32 ALUs. The N = 4096 sweep trees
@@ -35,7 +35,7 @@ def _eligible(p, d=17):
     # direct tables the tensor cores take at d channels
     jobs = p.export("jobs")
     nb = jobs[:, 3]
-    lo = 64 if d > 16 else 256 if d == 16 else 1 << 30
+    lo = 64 if d > 16 else 512 if d == 16 else 1 << 30
     return int(((jobs[:, 0] == 1) & (nb >= lo) & (nb <= 4096)).sum())
 
 
