@@ -616,10 +616,11 @@ __global__ void direct_kernel(const DirItem *__restrict__ items, int n_items, co
 
 // ---------------------------------------------------------------------------
 // gather: out[u] = leaf[u] + sum_calls (val[A-bin] - val[b-bin]), vertices taken
-// in a depth-first order of the tree
+// in a depth-first order of the tree; rec_ptr, akey and bkey are indexed by that
+// order's positions (u = order[i] has records rec_ptr[i] .. rec_ptr[i + 1] - 1)
 // ---------------------------------------------------------------------------
 template <typename T, int V>
-__global__ void gather_kernel(int n, const int32_t *__restrict__ order, const int32_t *__restrict__ vrec_ptr,
+__global__ void gather_kernel(int n, const int32_t *__restrict__ order, const int32_t *__restrict__ rec_ptr,
                               const int32_t *__restrict__ akey, const int32_t *__restrict__ bkey,
                               const float *__restrict__ vbuf, const float *__restrict__ leaf,
                               const uint8_t *__restrict__ in_leaf, int d, T *__restrict__ out) {
@@ -638,10 +639,10 @@ __global__ void gather_kernel(int n, const int32_t *__restrict__ order, const in
 #pragma unroll
             for (int i = 0; i < V; ++i) acc[i] = 0.f;
         }
-        const int e1 = vrec_ptr[u + 1];
+        const int e1 = rec_ptr[i + 1];
         // up to four records at a time: their key and row loads are in flight together;
         // the sum still runs in record order
-        for (int e = vrec_ptr[u]; e < e1; e += 4) {
+        for (int e = rec_ptr[i]; e < e1; e += 4) {
             int ka[4], kb[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {

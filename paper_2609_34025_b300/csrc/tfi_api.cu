@@ -103,6 +103,7 @@ struct tfi_plan_s {
     // device arrays
     int32_t *key_r = nullptr, *key_x = nullptr, *key_ptr = nullptr, *key_vtx = nullptr;
     tfi::dev::JobDev *jobs = nullptr;
+    // per gather position i (vertex gorder[i]): its (A-key, b-key) pairs, one per non-leaf call
     int32_t *vrec_ptr = nullptr, *vrec_akey = nullptr, *vrec_bkey = nullptr;
     int32_t *lgrp_ptr = nullptr, *leaf_vtx = nullptr, *leaf_dist = nullptr, *leaf_pdist = nullptr;
     int32_t *leaf_lo = nullptr, *leaf_hi = nullptr;
@@ -1154,9 +1155,6 @@ tfi_status upload_plan(tfi_plan_t p) {
         p->hk_err = static_cast<int32_t *>(q);
         TFI_CUDA(cudaMemset(p->hk_err, 0, 16));
     }
-    if (tfi_status rc = p->upload(&p->vrec_ptr, hp.vrec_ptr)) return rc;
-    if (tfi_status rc = p->upload(&p->vrec_akey, hp.vrec_akey)) return rc;
-    if (tfi_status rc = p->upload(&p->vrec_bkey, hp.vrec_bkey)) return rc;
     if (tfi_status rc = p->upload(&p->lgrp_ptr, hp.lgrp_ptr)) return rc;
     if (tfi_status rc = p->upload(&p->leaf_vtx, hp.leaf_vtx)) return rc;
     if (tfi_status rc = p->upload(&p->leaf_dist, hp.leaf_dist)) return rc;
@@ -1167,6 +1165,22 @@ tfi_status upload_plan(tfi_plan_t p) {
     {
         const std::vector<int32_t> order = depth_first_order(hp);
         if (tfi_status rc = p->upload(&p->gorder, order)) return rc;
+        // the gather's record lists in its own vertex order: the threads of a warp, at
+        // consecutive positions, read consecutive (A-key, b-key) entries
+        std::vector<int32_t> gptr(size_t(hp.n) + 1, 0), gak, gbk;
+        gak.reserve(hp.vrec_akey.size());
+        gbk.reserve(hp.vrec_bkey.size());
+        for (size_t i = 0; i < order.size(); ++i) {
+            const size_t u = size_t(order[i]);
+            for (int32_t e = hp.vrec_ptr[u]; e < hp.vrec_ptr[u + 1]; ++e) {
+                gak.push_back(hp.vrec_akey[size_t(e)]);
+                gbk.push_back(hp.vrec_bkey[size_t(e)]);
+            }
+            gptr[i + 1] = int32_t(gak.size());
+        }
+        if (tfi_status rc = p->upload(&p->vrec_ptr, gptr)) return rc;
+        if (tfi_status rc = p->upload(&p->vrec_akey, gak)) return rc;
+        if (tfi_status rc = p->upload(&p->vrec_bkey, gbk)) return rc;
     }
     p->n_groups = int32_t(hp.lgrp_ptr.size()) - 1;
     {
