@@ -616,8 +616,9 @@ __global__ void direct_kernel(const DirItem *__restrict__ items, int n_items, co
 
 // ---------------------------------------------------------------------------
 // gather: out[u] = leaf[u] + sum_calls (val[A-bin] - val[b-bin]), vertices taken
-// in a depth-first order of the tree; rec_ptr, akey and bkey are indexed by that
-// order's positions (u = order[i] has records rec_ptr[i] .. rec_ptr[i + 1] - 1)
+// in a depth-first order of the tree; rec_ptr, akey, bkey, the leaf rows and
+// in_leaf are indexed by that order's positions (u = order[i] has records
+// rec_ptr[i] .. rec_ptr[i + 1] - 1 and its leaf term in row i)
 // ---------------------------------------------------------------------------
 template <typename T, int V>
 __global__ void gather_kernel(int n, const int32_t *__restrict__ order, const int32_t *__restrict__ rec_ptr,
@@ -633,8 +634,8 @@ __global__ void gather_kernel(int n, const int32_t *__restrict__ order, const in
         // calls' table rows, which then come from L2 rather than DRAM
         const int64_t u = order[i];
         float acc[V];
-        if (in_leaf[u] != 0) {
-            load_row<float, V>(leaf + u * d + c, acc);
+        if (in_leaf[i] != 0) {
+            load_row<float, V>(leaf + i * d + c, acc);
         } else {
 #pragma unroll
             for (int i = 0; i < V; ++i) acc[i] = 0.f;
@@ -711,7 +712,7 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
                             const int32_t *__restrict__ leaf_dist, const int32_t *__restrict__ leaf_pdist,
                             const int32_t *__restrict__ leaf_lo, const int32_t *__restrict__ leaf_hi,
                             const T *__restrict__ F, int d, const float *__restrict__ ftab, int ftab_smem,
-                            float *__restrict__ leaf_out, int max_gs) {
+                            float *__restrict__ leaf_out, const int32_t *__restrict__ leaf_row, int max_gs) {
     constexpr int SV = LeafStride<CH>::v;
     extern __shared__ __align__(16) int smem_i[];
     const int gb = gptr[2 * blockIdx.x], ge = gptr[2 * blockIdx.x + 1], gs = ge - gb;  // [begin, end) pairs
@@ -765,7 +766,7 @@ __global__ void leaf_kernel(const int32_t *__restrict__ gptr, const int32_t *__r
                 for (int c = 0; c < CH; ++c) acc[c] = fmaf(f, sx[j * SV + c], acc[c]);
             }
         }
-        const int64_t v = leaf_vtx[gb + i];
+        const int64_t v = leaf_row[gb + i];
 #pragma unroll
         for (int c = 0; c < CH; ++c)
             if (c0 + c < d) leaf_out[v * d + c0 + c] = acc[c];
@@ -810,7 +811,8 @@ __global__ void __launch_bounds__(256, 3) leaf_warp_kernel(const int32_t *__rest
                                                            const int32_t *__restrict__ leaf_dist,
                                                            const int32_t *__restrict__ leaf_pdist, const T *__restrict__ F,
                                                            int d, const float *__restrict__ ftab, int ftab_smem,
-                                                           float *__restrict__ leaf_out, int max_leaf) {
+                                                           float *__restrict__ leaf_out,
+                                                           const int32_t *__restrict__ leaf_row, int max_leaf) {
     constexpr int SV = CH;
     constexpr int INF = 0x7fffffff;
     constexpr int TT = kLeafWarpTargets;  // targets per lane, 32 apart
@@ -1024,7 +1026,7 @@ __global__ void __launch_bounds__(256, 3) leaf_warp_kernel(const int32_t *__rest
 #pragma unroll
         for (int k = 0; k < TT; ++k) {
             if (act[k]) {
-                float *dst = leaf_out + int64_t(leaf_vtx[lb + ti[k]]) * d;
+                float *dst = leaf_out + int64_t(leaf_row[lb + ti[k]]) * d;
 #pragma unroll
                 for (int c = 0; c < CH; ++c)
                     if (c0 + c < d) dst[c0 + c] = acc[k][c];

@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(256) leaf_tc_kernel(const LeafTile *__restrict
                                                       const int32_t *__restrict__ leaf_lo,
                                                       const int32_t *__restrict__ leaf_hi, const T *__restrict__ F,
                                                       int d, const float *__restrict__ ftab, int ftab_smem,
-                                                      float *__restrict__ leaf_out, int32_t *__restrict__ err) {
+                                                      float *__restrict__ leaf_out,
+                                                      const int32_t *__restrict__ leaf_row, int32_t *__restrict__ err) {
     constexpr bool F32 = sizeof(T) == 4;
     constexpr int NSPLIT = F32 ? 2 : 1;
     constexpr uint32_t TCOLS = NB <= 32 ? 32u : uint32_t(NB);
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(256) leaf_tc_kernel(const LeafTile *__restrict
         const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
         const int trow = tl.i0 + (warp & 3) * 32 + (tid & 31);
         const bool wr = trow < tl.ge;
-        float *dst = wr ? leaf_out + int64_t(leaf_vtx[trow]) * d : nullptr;
+        float *dst = wr ? leaf_out + int64_t(leaf_row[trow]) * d : nullptr;
         constexpr int HALF_COLS = NB >= 32 ? NB / 2 : NB;
         const int cb = NB >= 32 ? half * HALF_COLS : 0;
         if (NB >= 32 || half == 0) {

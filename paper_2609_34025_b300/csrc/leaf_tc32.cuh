@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *_
                                                                    const float *__restrict__ F, int d,
                                                                    const float *__restrict__ ftab, int fts,
                                                                    int max_leaf, float *__restrict__ leaf_out,
+                                                                   const int32_t *__restrict__ leaf_row,
                                                                    int32_t *__restrict__ err) {
     static_assert(NB == 16 || NB == 32 || NB == 64, "channel block");
     constexpr int STAGES = leaf_tc32_stages(NB);
@@ -493,7 +494,7 @@ __global__ void __launch_bounds__(kL32Threads, 2) leaf_tc32_kernel(const int2 *_
                     }
                 }
                 if (ok && row_ok) {
-                    float *dst = leaf_out + int64_t(svtx[ri]) * d + c0 + h * HC;
+                    float *dst = leaf_out + int64_t(leaf_row[lf.x + ri]) * d + c0 + h * HC;
 #pragma unroll
                     for (int e = 0; e < HC; ++e)
                         if (c0 + h * HC + e < d) dst[e] = acc[e];

@@ -107,7 +107,8 @@ struct tfi_plan_s {
     int32_t *vrec_ptr = nullptr, *vrec_akey = nullptr, *vrec_bkey = nullptr;
     int32_t *lgrp_ptr = nullptr, *leaf_vtx = nullptr, *leaf_dist = nullptr, *leaf_pdist = nullptr;
     int32_t *leaf_lo = nullptr, *leaf_hi = nullptr;
-    uint8_t *in_leaf = nullptr;
+    uint8_t *in_leaf = nullptr;   // per gather position: the vertex has a leaf term
+    int32_t *leaf_row = nullptr;  // per leaf slot: the lbuf row of its vertex (its gather position)
     int32_t *gorder = nullptr;  // vertices in depth-first preorder of the forest (gather order)
     int32_t max_gs = 0, n_groups = 0;
     // FP32-ALU leaves: groups of consecutive small leaves (one thread per target) and big leaves of
@@ -576,7 +577,7 @@ int launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s, bo
         dim3 grid(p->n_big, (d + CH - 1) / CH);
         auto k = fts > 0 ? tfi::dev::leaf_warp_kernel<T, CH, true> : tfi::dev::leaf_warp_kernel<T, CH, false>;
         k<<<grid, kLeafWarpThreads, smem, s>>>(p->big_ptr, p->big_lo, p->big_hi, p->leaf_vtx, p->leaf_dist,
-                                               p->leaf_pdist, F, d, p->ftab, fts, lbuf, p->max_big);
+                                               p->leaf_pdist, F, d, p->ftab, fts, lbuf, p->leaf_row, p->max_big);
         ++launched;
     }
     if (p->n_sgroups > 0) {
@@ -584,7 +585,7 @@ int launch_leaf(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_t s, bo
         dim3 grid(p->n_sgroups, (d + CH - 1) / CH);
         auto k = fts > 0 ? tfi::dev::leaf_kernel<T, CH, true> : tfi::dev::leaf_kernel<T, CH, false>;
         k<<<grid, 256, smem, s>>>(p->sgrp_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, p->leaf_lo, p->leaf_hi, F, d,
-                                  p->ftab, fts, lbuf, p->max_sgs);
+                                  p->ftab, fts, lbuf, p->leaf_row, p->max_sgs);
         ++launched;
     }
     return launched;
@@ -606,7 +607,7 @@ void launch_leaf_tc_nb(tfi_plan_t p, const T *F, float *lbuf, int d, cudaStream_
     dim3 grid(unsigned(p->n_leaf_tiles), unsigned((d + NB - 1) / NB));
     tfi::tc::leaf_tc_kernel<T, NB><<<grid, 256, leaf_tc_smem<T, NB>(fts), s>>>(
         p->leaf_tiles, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, p->leaf_lo, p->leaf_hi, F, d, p->ftab, fts, lbuf,
-        p->hk_err + 1);
+        p->leaf_row, p->hk_err + 1);
 }
 
 // Tensor-core leaves for BF16 fields: NB = channels per CTA (TMEM columns), the next power of two
@@ -638,7 +639,7 @@ void launch_leaf_tc32_nb(tfi_plan_t p, const float *F, float *lbuf, int d, cudaS
     dim3 grid(unsigned(p->leaf32_grid), unsigned((d + NB - 1) / NB));
     auto k = fts > 0 ? tfi::tc::leaf_tc32_kernel<NB, true> : tfi::tc::leaf_tc32_kernel<NB, false>;
     k<<<grid, tfi::tc::kL32Threads, smem, s>>>(p->leaf32, p->leaf32_ptr, p->leaf_vtx, p->leaf_dist, p->leaf_pdist, F, d,
-                                              p->ftab, fts, p->max_leaf32, lbuf, p->hk_err + 1);
+                                              p->ftab, fts, p->max_leaf32, lbuf, p->leaf_row, p->hk_err + 1);
 }
 
 // returns the number of kernels launched
@@ -1161,7 +1162,6 @@ tfi_status upload_plan(tfi_plan_t p) {
     if (tfi_status rc = p->upload(&p->leaf_pdist, hp.leaf_pdist)) return rc;
     if (tfi_status rc = p->upload(&p->leaf_lo, hp.leaf_lo)) return rc;
     if (tfi_status rc = p->upload(&p->leaf_hi, hp.leaf_hi)) return rc;
-    if (tfi_status rc = p->upload(&p->in_leaf, hp.in_leaf)) return rc;
     {
         const std::vector<int32_t> order = depth_first_order(hp);
         if (tfi_status rc = p->upload(&p->gorder, order)) return rc;
@@ -1181,6 +1181,16 @@ tfi_status upload_plan(tfi_plan_t p) {
         if (tfi_status rc = p->upload(&p->vrec_ptr, gptr)) return rc;
         if (tfi_status rc = p->upload(&p->vrec_akey, gak)) return rc;
         if (tfi_status rc = p->upload(&p->vrec_bkey, gbk)) return rc;
+        // leaf terms in the same order: the leaf kernels write the row of a vertex at its gather
+        // position, so the gather reads them in sequence
+        std::vector<int32_t> pos(size_t(hp.n), 0);
+        for (size_t i = 0; i < order.size(); ++i) pos[size_t(order[i])] = int32_t(i);
+        std::vector<int32_t> lrow(hp.leaf_vtx.size());
+        for (size_t j = 0; j < lrow.size(); ++j) lrow[j] = pos[size_t(hp.leaf_vtx[j])];
+        std::vector<uint8_t> inl(size_t(hp.n), 0);
+        for (size_t i = 0; i < order.size(); ++i) inl[i] = hp.in_leaf[size_t(order[i])];
+        if (tfi_status rc = p->upload(&p->leaf_row, lrow)) return rc;
+        if (tfi_status rc = p->upload(&p->in_leaf, inl)) return rc;
     }
     p->n_groups = int32_t(hp.lgrp_ptr.size()) - 1;
     {
